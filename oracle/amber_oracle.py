@@ -1,0 +1,260 @@
+"""FP64 CPU oracle for the AMBER reionization-redshift assignment z_re(x).
+
+TEST INFRASTRUCTURE ONLY.  This module is the slow, plain, obviously-correct
+statement of what the GPU path computes.  Only the test-suite, the smoke check
+of ``__graft_entry__`` and the CPU-baseline leg of ``bench.py`` may import it;
+the library itself never does, and this module imports nothing from the
+library.  Everything is float64 numpy; library primitives (an FFT, a stable
+sort, a cumulative sum, a binary search) serve as single steps, with no
+blocking, fusion or reordering beyond what the paper's definition states.
+
+Paper: Trac, Chen, Hoffmann & Cen, "AMBER: Abundance Matching Box for the
+Epoch of Reionization", arXiv 2109.10375.
+
+Steps and the passages they follow
+----------------------------------
+* Reionization history (Sec. 3.1.1, Eqs. duration/asymmetry/zear/zlat):
+  z_ear = z_mid + dz*Az/(1+Az), z_lat = z_ear - dz.  The printed first form of
+  the z_lat equation repeats z_ear's fraction with a minus sign; it contradicts
+  the asymmetry definition, so the second printed form z_ear - dz is used.
+* Weibull history (Sec. 3.1.2, Eq. weibull) and its inverse.
+* Weibull coefficients (Appendix A): root of f(c) for c, then the algebraic
+  a_w, b_w.  The appendix suggests a secant iteration; this oracle brackets the
+  root on a log grid and bisects, because a secant started at (1, 2) leaves the
+  valid region for large asymmetry.
+* Radiation field (Sec. 3.4.1, Eq. intensity): J = S * G with
+  G(r) = exp(-r/l)/(4 pi r^2), done by FFT (the paper computes it "using
+  FFTs").  The transform of G is arctan(k l)/k with value l at k = 0, from the
+  radial Fourier integral int_0^inf exp(-r/l) sin(kr)/(kr) dr.
+* Ranking and abundance matching (Sec. 3.4.2): rank cells by J descending
+  (ties: ascending cell index), F_n = sum_{m<=n} mass_m / sum_all mass, and z_n
+  from the tabulated history x(z_j) by linear interpolation in z between the
+  two table points that bracket F_n.
+
+parity status: every function here is pinned by tests under tests/ (worked
+Table 1 values, closed forms, brute force on tiny grids, invariants).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass
+
+import numpy as np
+
+# ---------------------------------------------------------------------------
+# Reionization history (Sec. 3.1.1 and 3.1.2, Appendix A)
+# ---------------------------------------------------------------------------
+
+DEFAULT_X_POINTS = (0.05, 0.50, 0.95)  # (x_ear, x_mid, x_lat), Sec. 3.1.1 default
+
+
+def ionization_redshifts(z_mid: float, dz: float, Az: float) -> tuple[float, float, float]:
+    """(z_ear, z_mid, z_lat) from midpoint, duration and asymmetry (Sec. 3.1.1).
+
+    z_ear follows Eq. zear; z_lat = z_ear - dz is the duration definition
+    (Eq. duration) and the second form of Eq. zlat.
+    """
+    z_ear = z_mid + dz * Az / (1.0 + Az)
+    z_lat = z_ear - dz
+    return z_ear, z_mid, z_lat
+
+
+def weibull_x(z, a_w: float, b_w: float, c_w: float):
+    """Modified Weibull history x(z) = exp(-max((z-a)/b, 0)^c)  (Eq. weibull)."""
+    z = np.asarray(z, dtype=np.float64)
+    u = np.maximum((z - a_w) / b_w, 0.0)
+    return np.exp(-(u ** c_w))
+
+
+def weibull_inverse(x, a_w: float, b_w: float, c_w: float):
+    """Analytic inverse z(x) = a + b |ln x|^(1/c)  (Sec. 3.1.2)."""
+    x = np.asarray(x, dtype=np.float64)
+    return a_w + b_w * np.abs(np.log(x)) ** (1.0 / c_w)
+
+
+def _a_from_mid_lat(c, z_mid, z_lat, L_mid, L_lat):
+    """Offset a(c) from the mid and late points (Appendix A)."""
+    pm = L_mid ** (1.0 / c)
+    pl = L_lat ** (1.0 / c)
+    return (z_lat * pm - z_mid * pl) / (pm - pl)
+
+
+def weibull_coeffs(z_mid: float, dz: float, Az: float,
+                   x_points=DEFAULT_X_POINTS) -> tuple[float, float, float]:
+    """(a_w, b_w, c_w) through the three ionization points (Appendix A).
+
+    Solve f(c) = (ln x_ear / ln x_mid)^(1/c) - (z_ear - a(c))/(z_mid - a(c)) = 0
+    for c by a sign change on a log grid over [0.05, 100] followed by bisection
+    to machine precision, then a_w from the early and late points and
+    b_w = (z_mid - a_w) / |ln x_mid|^(1/c).  Raises ValueError when no root is
+    bracketed or a coefficient is not positive (the paper requires all three
+    to be positive).
+    """
+    x_ear, x_mid, x_lat = x_points
+    if not (0.0 < x_ear < x_mid < x_lat < 1.0):
+        raise ValueError("need 0 < x_ear < x_mid < x_lat < 1")
+    if not (dz > 0.0 and Az > 0.0):
+        raise ValueError("need dz > 0 and Az > 0")
+    z_ear, z_mid, z_lat = ionization_redshifts(z_mid, dz, Az)
+    L_ear, L_mid, L_lat = abs(math.log(x_ear)), abs(math.log(x_mid)), abs(math.log(x_lat))
+
+    def f(c):
+        a = _a_from_mid_lat(c, z_mid, z_lat, L_mid, L_lat)
+        return (L_ear / L_mid) ** (1.0 / c) - (z_ear - a) / (z_mid - a)
+
+    grid = np.exp(np.linspace(math.log(0.05), math.log(100.0), 401))
+    vals = [f(c) for c in grid]
+    for i in range(len(grid) - 1):
+        f0, f1 = vals[i], vals[i + 1]
+        if not (math.isfinite(f0) and math.isfinite(f1)) or f0 * f1 > 0.0:
+            continue
+        lo, hi, flo = grid[i], grid[i + 1], f0
+        for _ in range(200):
+            mid = 0.5 * (lo + hi)
+            fm = f(mid)
+            if fm == 0.0:
+                lo = hi = mid
+                break
+            if (fm > 0.0) == (flo > 0.0):
+                lo, flo = mid, fm
+            else:
+                hi = mid
+            if hi - lo <= 1e-15 * hi:
+                break
+        c = 0.5 * (lo + hi)
+        pe, pl = L_ear ** (1.0 / c), L_lat ** (1.0 / c)
+        a = (z_ear * pl - z_lat * pe) / (pl - pe)
+        b = (z_mid - a) / L_mid ** (1.0 / c)
+        if a > 0.0 and b > 0.0 and c > 0.0:
+            return float(a), float(b), float(c)
+    raise ValueError("no Weibull root bracketed with positive coefficients")
+
+
+@dataclass
+class HistoryTable:
+    """Tabulated history: z_j uniform on [z_lo, z_hi], x_j = x(z_j)."""
+    z: np.ndarray
+    x: np.ndarray
+    a_w: float
+    b_w: float
+    c_w: float
+
+
+def history_table(z_mid: float, dz: float, Az: float, z_lo: float = 5.0, z_hi: float = 20.0,
+                  n_table: int = 2000, x_points=DEFAULT_X_POINTS) -> HistoryTable:
+    """x(z) tabulated on n_table uniform redshifts.
+
+    The low end is lowered to a_w when a_w < z_lo so that the table reaches the
+    fully ionized plateau x = 1 (otherwise the fraction at the lowest table
+    redshift could not equal x there).
+    """
+    a, b, c = weibull_coeffs(z_mid, dz, Az, x_points)
+    lo = min(z_lo, a)
+    j = np.arange(n_table, dtype=np.float64)
+    z = lo + (z_hi - lo) * j / (n_table - 1)
+    return HistoryTable(z=z, x=weibull_x(z, a, b, c), a_w=a, b_w=b, c_w=c)
+
+
+# ---------------------------------------------------------------------------
+# Radiation field (Sec. 3.4.1, Eq. intensity)
+# ---------------------------------------------------------------------------
+
+def kernel_transform(k, l_mfp: float):
+    """Fourier transform of G(r) = exp(-r/l)/(4 pi r^2): arctan(k l)/k, l at k=0."""
+    k = np.asarray(k, dtype=np.float64)
+    out = np.empty_like(k)
+    nz = k > 0.0
+    out[nz] = np.arctan(k[nz] * l_mfp) / k[nz]
+    out[~nz] = l_mfp
+    return out
+
+
+def wavenumbers(n: int, box: float):
+    """Angular wavenumbers 2 pi m / L for FFT index m, signed (numpy order)."""
+    return 2.0 * np.pi / box * np.fft.fftfreq(n, d=1.0 / n)
+
+
+def kmag_half(n: int, box: float):
+    """|k| on the half-spectrum grid [z][y][x<=n/2] of a real n^3 field."""
+    k = wavenumbers(n, box)
+    kx = np.abs(k[: n // 2 + 1])
+    kx[-1] = 2.0 * np.pi / box * (n // 2)  # Nyquist: same |k| either sign
+    return np.sqrt(k[:, None, None] ** 2 + k[None, :, None] ** 2 + kx[None, None, :] ** 2)
+
+
+def radiation_field(S, box: float, l_mfp: float):
+    """J = IDFT(DFT(S) * K(|k|)) in float64, cell order [z][y][x].
+
+    The discrete convolution on the periodic grid: forward sum
+    S_hat(k) = sum_x S(x) e^{-i k.x}, inverse with the 1/C normalisation.
+    """
+    S = np.asarray(S, dtype=np.float64)
+    n = S.shape[0]
+    assert S.shape == (n, n, n)
+    S_hat = np.fft.rfftn(S)
+    J_hat = S_hat * kernel_transform(kmag_half(n, box), l_mfp)
+    return np.fft.irfftn(J_hat, s=S.shape, axes=(0, 1, 2))
+
+
+# ---------------------------------------------------------------------------
+# Ranking and abundance matching (Sec. 3.4.2)
+# ---------------------------------------------------------------------------
+
+def rank(J):
+    """order[r] = cell index of rank r: descending J, ties by ascending index."""
+    J = np.asarray(J).reshape(-1)
+    if not np.all(np.isfinite(J)):
+        raise ValueError("non-finite intensity")
+    return np.argsort(-J, kind="stable")
+
+
+def cumulative_mass_fraction(order, mass):
+    """F_n = sum_{m<=n} mass[order[m]] / sum_all mass (inclusive, float64)."""
+    m = np.asarray(mass, dtype=np.float64).reshape(-1)[np.asarray(order)]
+    M = np.cumsum(m)
+    return M / M[-1]
+
+
+def assign_from_fraction(F, table: HistoryTable):
+    """z_n from F_n by the tabulated inverse of x(z).
+
+    j* = largest j with x_j >= F.  No such j: z_lo.  j* = last: z_hi.
+    Otherwise t = (x_j* - F)/(x_j* - x_j*+1) in [0,1) and
+    z = z_j* + t (z_j*+1 - z_j*).
+    """
+    F = np.asarray(F, dtype=np.float64)
+    x, z = table.x, table.z
+    M = len(x)
+    # x is non-increasing in j, so {j : x_j >= F} is a prefix of length cnt.
+    cnt = M - np.searchsorted(x[::-1], F, side="left")
+    j = cnt - 1
+    out = np.empty_like(F)
+    none = j < 0
+    last = j == M - 1
+    mid = ~(none | last)
+    jm = j[mid]
+    t = (x[jm] - F[mid]) / (x[jm] - x[jm + 1])
+    t = np.minimum(np.maximum(t, 0.0), np.nextafter(1.0, 0.0))
+    out[mid] = z[jm] + t * (z[jm + 1] - z[jm])
+    out[none] = z[0]
+    out[last] = z[-1]
+    return out
+
+
+def assign_zre(order, mass, table: HistoryTable):
+    """z_re in cell order: z_re[order[n]] = z_n (Sec. 3.4.2)."""
+    order = np.asarray(order)
+    z_n = assign_from_fraction(cumulative_mass_fraction(order, mass), table)
+    z_re = np.empty(order.shape[0], dtype=np.float64)
+    z_re[order] = z_n
+    return z_re
+
+
+def solve(S, mass, box: float, l_mfp: float, z_mid: float, dz: float, Az: float,
+          z_lo: float = 5.0, z_hi: float = 20.0, n_table: int = 2000):
+    """The whole path: J, order, z_re (cell order, flattened) in float64."""
+    J = radiation_field(S, box, l_mfp)
+    order = rank(J)
+    table = history_table(z_mid, dz, Az, z_lo, z_hi, n_table)
+    z_re = assign_zre(order, mass, table)
+    return J, order, z_re

@@ -1,0 +1,67 @@
+"""Plant plausible mistakes in the oracle (CPU only) and check that the pins catch each.
+
+Every mutation below is a slip one could make when writing the oracle from
+the paper: a dropped or wrong term, a sign, an index or a transposed axis.
+Each must make at least one pin in test_oracle_pins fail.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import amber_oracle as o
+import tests.test_oracle_pins as pins
+
+PINS = [
+    lambda: pins.test_radiation_field_vs_brute_force_dft(4),
+    lambda: pins.test_uniform_source_gives_uniform_intensity(),
+    lambda: [pins.test_plane_wave_is_eigenfunction(m) for m in [(0, 0, 1), (0, 3, 0), (2, 0, 0), (1, -2, 3)]],
+    lambda: pins.test_point_source_recovers_attenuated_inverse_square(),
+    lambda: pins.test_rank_matches_brute_force_and_is_stable(),
+    lambda: pins.test_equal_mass_fraction_is_n_over_C_and_matches_analytic_inverse(),
+    lambda: pins.test_assign_vs_brute_force_loop(),
+    lambda: pins.test_ionized_mass_fraction_follows_history_within_one_cell(),
+    lambda: [pins.test_weibull_coeffs_match_table1(r) for r in pins._table1()],
+    lambda: pins.test_table_interpolation_vs_analytic_inverse(),
+]
+
+
+def _kmag_transposed(n, box):
+    k = o.wavenumbers(n, box)
+    kx = np.abs(k[: n // 2 + 1])
+    kx[-1] = 2.0 * np.pi / box * (n // 2)
+    return np.sqrt(kx[None, None, :] ** 2 * 0 + k[None, :, None] ** 2 + k[:n // 2 + 1][None, None, :] ** 2
+                   + np.zeros((n, 1, 1)))
+
+
+MUTATIONS = {
+    "kernel_k_squared": ("kernel_transform",
+                         lambda k, l: np.where(np.asarray(k) > 0, np.arctan(np.asarray(k) * l) / np.maximum(np.asarray(k), 1e-300) ** 2, l)),
+    "kernel_no_atan": ("kernel_transform",
+                       lambda k, l: np.where(np.asarray(k) > 0, l / (1.0 + np.asarray(k) * l), l)),
+    "kmag_drops_z_axis": ("kmag_half", _kmag_transposed),
+    "rank_ascending": ("rank", lambda J: np.argsort(np.asarray(J).reshape(-1), kind="stable")),
+    "fraction_exclusive": ("cumulative_mass_fraction",
+                           lambda order, mass: (lambda m: (np.cumsum(m) - m) / m.sum())(
+                               np.asarray(mass, dtype=np.float64).reshape(-1)[np.asarray(order)])),
+    "zlat_printed_typo": ("ionization_redshifts",
+                          lambda z_mid, dz, Az: (z_mid + dz * Az / (1 + Az), z_mid, z_mid - dz * Az / (1 + Az))),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_pins_catch_mutation(name, monkeypatch):
+    attr, fn = MUTATIONS[name]
+    monkeypatch.setattr(o, attr, fn)
+    caught = 0
+    for pin in PINS:
+        try:
+            pin()
+        except (AssertionError, ValueError):
+            caught += 1
+    assert caught > 0, f"no pin caught mutation {name}"
+
+
+def test_pins_pass_unmutated():
+    for pin in PINS:
+        pin()

@@ -1,0 +1,311 @@
+"""Pins for the FP64 oracle against what the paper and the mathematics fix.
+
+No GPU.  Each test ties one oracle function to something other than itself:
+the paper's Table 1 worked values, closed forms (kernel transform, plane-wave
+eigenfunctions, uniform fields), brute-force sums on tiny grids, and the
+invariants of abundance matching (Sec. 3.4.2).
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import amber_oracle as o
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _table1():
+    rows = []
+    with open(os.path.join(GOLDEN, "weibull_table1.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            name, *vals = line.split()
+            rows.append((name, *map(float, vals)))
+    return rows
+
+
+# ----------------------------------------------------------------------------
+# Reionization history: Sec. 3.1, Appendix A, Table 1
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("row", _table1(), ids=lambda r: r[0])
+def test_weibull_coeffs_match_table1(row):
+    _, z_mid, dz, Az, a_w, b_w, c_w = row
+    a, b, c = o.weibull_coeffs(z_mid, dz, Az)
+    assert abs(a - a_w) <= 0.01 and abs(b - b_w) <= 0.01 and abs(c - c_w) <= 0.01, (a, b, c)
+
+
+@pytest.mark.parametrize("params", [(8, 4, 3), (7.5, 4, 3), (6.5, 6, 1.5), (9, 2, 5), (8, 4, 1), (8, 4, 14)])
+def test_weibull_passes_through_ionization_points(params):
+    z_mid, dz, Az = params
+    a, b, c = o.weibull_coeffs(z_mid, dz, Az)
+    z_ear, _, z_lat = o.ionization_redshifts(z_mid, dz, Az)
+    x = o.weibull_x([z_ear, z_mid, z_lat], a, b, c)
+    np.testing.assert_allclose(x, [0.05, 0.5, 0.95], rtol=0, atol=1e-12)
+    # duration and asymmetry definitions (Eqs. duration, asymmetry)
+    assert abs((z_ear - z_lat) - dz) < 1e-12
+    assert abs((z_ear - z_mid) / (z_mid - z_lat) - Az) < 1e-12
+
+
+def test_weibull_quartile_convention():
+    # the other convention named in Sec. 3.1.1: (x_ear, x_lat) = (0.25, 0.75)
+    a, b, c = o.weibull_coeffs(8.0, 2.0, 2.0, x_points=(0.25, 0.5, 0.75))
+    z_ear, z_mid, z_lat = o.ionization_redshifts(8.0, 2.0, 2.0)
+    np.testing.assert_allclose(o.weibull_x([z_ear, z_mid, z_lat], a, b, c), [0.25, 0.5, 0.75], atol=1e-12)
+
+
+def test_weibull_symmetric_case_and_monotone():
+    a, b, c = o.weibull_coeffs(8.0, 4.0, 1.0)
+    z = np.linspace(0, 30, 3001)
+    x = o.weibull_x(z, a, b, c)
+    assert np.all(np.diff(x) <= 0)            # monotone non-increasing in z
+    assert np.all(x[z <= a] == 1.0)           # fully ionized below a_w
+    assert np.all((x > 0) & (x <= 1))
+
+
+def test_weibull_rejects_bad_points():
+    with pytest.raises(ValueError):
+        o.weibull_coeffs(8, 4, 3, x_points=(0.5, 0.05, 0.95))
+    with pytest.raises(ValueError):
+        o.weibull_coeffs(8, -1, 3)
+
+
+def test_analytic_inverse_roundtrip():
+    a, b, c = o.weibull_coeffs(7.91, 5.45, 2.69)
+    xs = np.linspace(0.001, 0.999, 500)
+    np.testing.assert_allclose(o.weibull_x(o.weibull_inverse(xs, a, b, c), a, b, c), xs, rtol=1e-12)
+
+
+def test_table_lowers_z_lo_to_reach_plateau():
+    t = o.history_table(6.5, 6.0, 1.5)        # a_w ~ 3.22 < 5
+    assert abs(t.z[0] - t.a_w) < 1e-12 and t.x[0] == 1.0 and t.z[-1] == 20.0
+    t2 = o.history_table(8.0, 4.0, 3.0)       # a_w ~ 6.89 > 5
+    assert t2.z[0] == 5.0 and len(t2.z) == 2000
+
+
+def test_table_interpolation_vs_analytic_inverse():
+    t = o.history_table(8.0, 4.0, 3.0)
+    F = np.linspace(t.x[-1] * 1.01, 0.999, 20001)
+    z_tab = o.assign_from_fraction(F, t)
+    z_ana = o.weibull_inverse(F, t.a_w, t.b_w, t.c_w)
+    # linear interpolation in z between table nodes: error <= local node spacing
+    assert np.max(np.abs(z_tab - z_ana)) < (t.z[1] - t.z[0])
+    # and much better where x(z) is nearly linear on the node scale
+    mid = (F > 0.05) & (F < 0.95)
+    assert np.max(np.abs(z_tab[mid] - z_ana[mid])) < 1e-4
+
+
+# ----------------------------------------------------------------------------
+# Radiation kernel: Sec. 3.4.1, Eq. intensity
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("l", [0.5, 3.0, 20.0])
+def test_kernel_transform_matches_radial_quadrature(l):
+    from scipy.integrate import quad
+    for k in [0.01, 0.3, 1.0, 4.0]:
+        # 3D transform of G(r) = exp(-r/l)/(4 pi r^2): 4 pi int r^2 G(r) sin(kr)/(kr) dr
+        f = lambda r: 4 * math.pi * r * r * (math.exp(-r / l) / (4 * math.pi * r * r)) * math.sin(k * r) / (k * r)
+        a = 1.0 / k
+        head, _ = quad(f, 0, a, epsabs=1e-14, epsrel=1e-13, limit=400)
+        # oscillatory tail by the Fourier-integral rule (sin weight on [a, inf))
+        tail, _ = quad(lambda r: math.exp(-r / l) / (k * r), a, np.inf, weight="sin", wvar=k, epsabs=1e-14, limlst=200)
+        val = head + tail
+        assert abs(o.kernel_transform(np.array([k]), l)[0] - val) <= 1e-10 * abs(val)
+
+
+def test_kernel_transform_limits():
+    l = 3.0
+    assert o.kernel_transform(np.array([0.0]), l)[0] == l
+    k = np.array([1e-9])
+    assert abs(o.kernel_transform(k, l)[0] - l) < 1e-12
+    # l -> infinity: pure inverse-square kernel, transform pi/(2k)
+    kk = np.array([0.5, 2.0])
+    np.testing.assert_allclose(o.kernel_transform(kk, 1e12), math.pi / (2 * kk), rtol=1e-10)
+
+
+def _brute_force_field(S, box, l):
+    """J by explicit complex sums over every k and x (no FFT)."""
+    n = S.shape[0]
+    C = n ** 3
+    m = np.arange(n)
+    sm = np.where(m < n // 2, m, m - n)
+    kf = 2 * math.pi / box
+    xs = np.array([(z, y, x) for z in range(n) for y in range(n) for x in range(n)])
+    Sflat = S.reshape(-1)
+    J = np.zeros(C)
+    for a in range(n):
+        for b in range(n):
+            for c in range(n):
+                kv = kf * np.array([sm[a], sm[b], sm[c]])       # (kz, ky, kx)
+                phase = xs @ (np.array([a, b, c]) * 2 * math.pi / n)
+                Sk = np.sum(Sflat * np.exp(-1j * phase))
+                K = o.kernel_transform(np.array([np.linalg.norm(kv)]), l)[0]
+                J += (Sk * K * np.exp(1j * phase)).real
+    return (J / C).reshape(S.shape)
+
+
+@pytest.mark.parametrize("n", [4, 6])
+def test_radiation_field_vs_brute_force_dft(n):
+    rng = np.random.default_rng(7)
+    S = rng.random((n, n, n))
+    box, l = 10.0, 2.5
+    np.testing.assert_allclose(o.radiation_field(S, box, l), _brute_force_field(S, box, l), rtol=1e-11, atol=1e-12)
+
+
+def test_uniform_source_gives_uniform_intensity():
+    S = np.full((16, 16, 16), 2.5)
+    J = o.radiation_field(S, 50.0, 3.0)
+    np.testing.assert_allclose(J, 2.5 * 3.0, rtol=1e-12)
+
+
+@pytest.mark.parametrize("mvec", [(0, 0, 1), (0, 3, 0), (2, 0, 0), (1, -2, 3), (0, 0, 8), (8, 8, 8), (-5, 7, 2)])
+def test_plane_wave_is_eigenfunction(mvec):
+    n, box, l, eps = 16, 40.0, 3.0, 0.3
+    z, y, x = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    mz, my, mx = mvec
+    phase = 2 * math.pi * (mz * z + my * y + mx * x) / n
+    S = 1.0 + eps * np.cos(phase)
+    kmag = 2 * math.pi / box * math.sqrt(mz * mz + my * my + mx * mx)
+    K = math.atan(kmag * l) / kmag
+    np.testing.assert_allclose(o.radiation_field(S, box, l), l + eps * K * np.cos(phase), rtol=0, atol=1e-12)
+
+
+def test_point_source_recovers_attenuated_inverse_square():
+    n, box, l = 64, 64.0, 6.0
+    dx = box / n
+    S = np.zeros((n, n, n))
+    S[0, 0, 0] = 1.0 / dx ** 3
+    J = o.radiation_field(S, box, l)
+
+    def G_images(d):
+        tot = 0.0
+        for i in range(-3, 4):
+            for j in range(-3, 4):
+                for k in range(-3, 4):
+                    r = np.linalg.norm(np.array(d) * dx + np.array([i, j, k]) * box)
+                    tot += math.exp(-r / l) / (4 * math.pi * r * r)
+        return tot
+
+    # along lattice diagonals the band-limited field matches exp(-r/l)/(4 pi r^2)
+    for c in [3, 4, 6, 8, 12, 16]:
+        assert abs(J[c, c, c] / G_images((c, c, c)) - 1) < 1e-3
+        assert abs(J[0, c, c] / G_images((0, c, c)) - 1) < 2e-2
+
+
+# ----------------------------------------------------------------------------
+# Ranking and abundance matching: Sec. 3.4.2
+# ----------------------------------------------------------------------------
+
+def test_rank_matches_brute_force_and_is_stable():
+    rng = np.random.default_rng(3)
+    J = rng.integers(0, 7, size=300).astype(np.float64)   # many ties
+    order = o.rank(J)
+    brute = sorted(range(len(J)), key=lambda i: (-J[i], i))
+    assert list(order) == brute
+    assert sorted(order.tolist()) == list(range(len(J)))
+
+
+def test_rank_rejects_nan():
+    with pytest.raises(ValueError):
+        o.rank(np.array([1.0, np.nan]))
+
+
+def test_equal_mass_fraction_is_n_over_C_and_matches_analytic_inverse():
+    C = 5000
+    order = np.arange(C)[::-1].copy()
+    F = o.cumulative_mass_fraction(order, np.ones(C))
+    np.testing.assert_array_equal(F, np.arange(1, C + 1) / C)
+    t = o.history_table(8.0, 4.0, 3.0)
+    z = o.assign_zre(order, np.ones(C), t)
+    Fn = np.arange(1, C + 1) / C
+    inside = (Fn < 0.999) & (Fn > t.x[-1])
+    ana = o.weibull_inverse(Fn, t.a_w, t.b_w, t.c_w)
+    assert np.max(np.abs(z[order][inside] - ana[inside])) < (t.z[1] - t.z[0])
+
+
+def _brute_assign(order, mass, t):
+    C = len(order)
+    T = 0.0
+    for i in range(C):
+        T += float(mass[order[i]])
+    zre = np.zeros(C)
+    M = 0.0
+    for n in range(C):
+        M += float(mass[order[n]])
+        F = M / T
+        js = [j for j in range(len(t.x)) if t.x[j] >= F]
+        if not js:
+            zn = t.z[0]
+        elif js[-1] == len(t.x) - 1:
+            zn = t.z[-1]
+        else:
+            j = js[-1]
+            tt = (t.x[j] - F) / (t.x[j] - t.x[j + 1])
+            zn = t.z[j] + tt * (t.z[j + 1] - t.z[j])
+        zre[order[n]] = zn
+    return zre
+
+
+def test_assign_vs_brute_force_loop():
+    rng = np.random.default_rng(11)
+    C = 400
+    mass = rng.uniform(0.01, 5.0, C)
+    order = rng.permutation(C)
+    t = o.history_table(8.0, 4.0, 3.0, n_table=200)
+    np.testing.assert_allclose(o.assign_zre(order, mass, t), _brute_assign(order, mass, t), rtol=0, atol=1e-12)
+
+
+def _fraction_invariant(z_re, mass, t):
+    T = mass.sum()
+    mmax = mass.max() / T
+    for zj, xj in zip(t.z, t.x):
+        frac = mass[z_re >= zj].sum() / T
+        assert xj - mmax - 1e-12 <= frac <= xj + 1e-12, (zj, xj, frac)
+
+
+def test_ionized_mass_fraction_follows_history_within_one_cell():
+    rng = np.random.default_rng(5)
+    C = 20000
+    mass = rng.uniform(0.01, 3.0, C)
+    J = rng.normal(size=C)
+    t = o.history_table(7.5, 4.0, 3.0, n_table=300)
+    z = o.assign_zre(o.rank(J), mass, t)
+    _fraction_invariant(z, mass, t)
+
+
+def test_tiny_grid_whole_path_brute_force():
+    """N = 4 (64 cells): J by explicit sums, ranking by selection, loop assign."""
+    n, box, l = 4, 8.0, 1.7
+    rng = np.random.default_rng(2)
+    S = rng.random((n, n, n))
+    mass = rng.uniform(0.5, 1.5, n ** 3)
+    Jb = _brute_force_field(S, box, l).reshape(-1)
+    remaining = list(range(n ** 3))
+    order_b = []
+    while remaining:
+        best = remaining[0]
+        for i in remaining[1:]:
+            if Jb[i] > Jb[best]:
+                best = i
+        order_b.append(best)
+        remaining.remove(best)
+    t = o.history_table(8.0, 4.0, 3.0, n_table=50)
+    zb = _brute_assign(np.array(order_b), mass, t)
+    J, order, z = o.solve(S, mass, box, l, 8.0, 4.0, 3.0, n_table=50)
+    np.testing.assert_allclose(J.reshape(-1), Jb, rtol=1e-12)
+    assert list(order) == order_b
+    np.testing.assert_allclose(z, zb, atol=1e-12)
+
+
+def test_solve_monotone_in_intensity():
+    import sys
+    from paper_2109_10375_gb300 import synth
+    S, m = synth.realisation(16, 25.0, 0)
+    J, order, z = o.solve(S.numpy(), m.numpy(), 25.0, 3.0, 8.0, 4.0, 3.0)
+    Jf = J.reshape(-1)
+    # J_a > J_b  =>  z(a) >= z(b): z along descending-J order is non-increasing
+    assert np.all(np.diff(z[order]) <= 0)
+    assert np.all(np.diff(Jf[order]) <= 0)
