@@ -1,0 +1,172 @@
+/*
+ * amber.h -- C ABI of libamber: the reionization-redshift assignment z_re(x)
+ * of AMBER (Trac et al., arXiv 2109.10375) on one NVIDIA GB300 (sm_103a).
+ *
+ * The path, in the paper's order:
+ *   amber_radiation_field  J = S * exp(-r/l_mfp)/(4 pi r^2) by FFT   (Sec. 3.4.1, Eq. intensity)
+ *   amber_rank             order cells by J, descending               (Sec. 3.4.2)
+ *   amber_assign_zre       cumulative-mass abundance matching to the
+ *                          Weibull history x(z) of (z_mid, dz, Az)    (Sec. 3.4.2, Sec. 3.1, App. A)
+ *   amber_solve            all of the above in one call
+ *
+ * Conventions for every entry point:
+ *  - Fields are C-order [z][y][x] (x fastest) on a periodic n^3 grid of side
+ *    `box` (h^-1 Mpc); n is a power of two in [4, 1024].
+ *  - Pointers named d_* are DEVICE pointers owned by the caller (any CUDA
+ *    allocation on the context's device).  The library never frees them.
+ *  - `stream` is a cudaStream_t passed as void*; NULL means the legacy default
+ *    stream.  All device work is asynchronous on that stream; no call
+ *    allocates device memory after amber_create.
+ *  - Return values are amber_status codes.  Argument errors are detected on
+ *    the host and returned immediately with nothing enqueued.  Errors found by
+ *    kernels (non-finite intensity, invalid mass, a lookback wait that ran
+ *    out) latch in a device status word read by amber_sync_status.
+ *  - A context serialises its own work: calls on one context must not
+ *    overlap in time on different streams (they share one workspace).
+ *    Use one context per concurrent stream.
+ */
+#ifndef AMBER_H_
+#define AMBER_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  AMBER_OK = 0,
+  AMBER_ERR_INVALID_ARG = 1,     /* bad size, pointer, box, l_mfp or history point */
+  AMBER_ERR_NO_SOLUTION = 2,     /* no Weibull root with a_w, b_w, c_w > 0 (App. A) */
+  AMBER_ERR_NONFINITE = 4,       /* device: a NaN or Inf intensity was ranked */
+  AMBER_ERR_OOM = 8,             /* workspace allocation failed in amber_create */
+  AMBER_ERR_DEVICE_TIMEOUT = 16, /* device: a bounded lookback wait ran out */
+  AMBER_ERR_CUDA = 32,           /* a CUDA runtime call failed (no device, launch error) */
+  AMBER_ERR_INVALID_MASS = 64,   /* device: a cell mass was negative, NaN or >= 2^40 */
+  AMBER_ERR_CAPACITY = 128       /* size exceeds the context's max_cells */
+} amber_status;
+
+typedef struct amber_ctx amber_ctx;
+
+/* Reionization history (Sec. 3.1.1): midpoint, duration dz = z_ear - z_lat,
+ * asymmetry Az = (z_ear - z_mid)/(z_mid - z_lat); the ionized fractions at
+ * the three points (default 0.05, 0.50, 0.95); and the table x(z_j) on
+ * n_table uniform redshifts in [min(z_lo, a_w), z_hi] (default 5, 20, 2000). */
+typedef struct {
+  double z_mid, dz, Az;
+  double x_ear, x_mid, x_lat;
+  double z_lo, z_hi;
+  int n_table;
+} amber_history_t;
+
+/* One realisation's parameters.  precision: 32 (FP32 FFT and intensity) or
+ * 64 (FP64 FFT and intensity, n <= 256). */
+typedef struct {
+  int n;
+  double box;
+  double l_mfp;
+  amber_history_t hist;
+  int precision;
+} amber_params_t;
+
+/* Fill *h with the paper's defaults (x points 0.05/0.50/0.95, table [5,20] x 2000). */
+int amber_history_default(amber_history_t *h, double z_mid, double dz, double Az);
+
+/* Weibull coefficients (a_w, b_w, c_w) of x(z) = exp(-max((z-a)/b,0)^c) through
+ * the three ionization points (Sec. 3.1.2, Eq. weibull; App. A).  Host only, FP64,
+ * no GPU needed.  The root in c is bracketed on a log grid over [0.05, 100] and
+ * bisected (the appendix's secant iteration can leave the valid region).
+ * z_lat is taken as z_ear - dz (the duration definition).
+ * Returns AMBER_ERR_INVALID_ARG for points not 0 < x_ear < x_mid < x_lat < 1,
+ * dz <= 0 or Az <= 0; AMBER_ERR_NO_SOLUTION if no positive root exists. */
+int amber_history_coeffs(const amber_history_t *h, double out_abc[3]);
+
+/* The history table the device builds for h, computed on the host in FP64:
+ * z_out[j], x_out[j] for j < h->n_table (caller-owned host arrays).  Host only. */
+int amber_history_table(const amber_history_t *h, double *z_out, double *x_out);
+
+/* Create a context on `device` able to process up to max_cells cells
+ * (max_cells <= 2^30; the FFT needs n^3 <= max_cells).  Allocates the whole
+ * workspace once (about 21 bytes per cell plus the half spectrum, see
+ * amber_workspace_bytes).  *ctx is owned by the caller and released with
+ * amber_destroy.  Returns AMBER_ERR_CUDA when no device is usable and
+ * AMBER_ERR_OOM when the workspace does not fit. */
+int amber_create(amber_ctx **ctx, int device, int64_t max_cells);
+int amber_destroy(amber_ctx *ctx);
+
+/* Bytes of device workspace amber_create(max_cells) allocates.  Host only. */
+int amber_workspace_bytes(int64_t max_cells, size_t *out_bytes);
+
+/* Radiation intensity (Sec. 3.4.1, Eq. intensity):
+ *   J = IDFT( DFT(S) * arctan(|k| l_mfp)/|k| ),  value l_mfp at k = 0,
+ * the periodic convolution of S with exp(-r/l_mfp)/(4 pi r^2), where
+ * k = 2 pi m / box for signed FFT index m and the inverse carries 1/n^3.
+ * d_src: n^3 floats (cell order); d_J: n^3 floats out (may alias d_src).
+ * FP32 arithmetic, twiddles rounded from FP64. */
+int amber_radiation_field(amber_ctx *ctx, const float *d_src, int n, double box, double l_mfp,
+                          float *d_J, void *stream);
+/* Same in FP64 (n <= 256): d_src and d_J are n^3 doubles. */
+int amber_radiation_field_f64(amber_ctx *ctx, const double *d_src, int n, double box, double l_mfp,
+                              double *d_J, void *stream);
+
+/* Ranking (Sec. 3.4.2): d_order[r] = index of the cell with rank r, ranks in
+ * descending J, equal J ordered by ascending cell index (a stable sort; the
+ * paper's quicksort leaves ties unspecified).  -0.0 ranks equal to +0.0.
+ * A NaN intensity latches AMBER_ERR_NONFINITE.  ncells in [1, max_cells].
+ * d_J: ncells floats; d_order: ncells uint32 out. */
+int amber_rank(amber_ctx *ctx, const float *d_J, int64_t ncells, uint32_t *d_order, void *stream);
+/* Same for FP64 intensities (ncells <= 2^24). */
+int amber_rank_f64(amber_ctx *ctx, const double *d_J, int64_t ncells, uint32_t *d_order, void *stream);
+
+/* Abundance matching (Sec. 3.4.2): with M_n = sum_{m<=n} mass[order[m]] and
+ * F_n = M_n / M_{ncells-1}, the rank-n cell gets z_n from the tabulated
+ * history: j* = largest j with x(z_j) >= F_n; z_n = z_lo if there is none,
+ * z_hi if j* is the last node, otherwise the linear interpolation
+ * z_j* + (x_j* - F_n)/(x_j* - x_j*+1) (z_j*+1 - z_j*).  Writes
+ * d_zre[order[n]] = z_n (float, cell order).
+ * The cumulative mass is accumulated exactly in 128-bit fixed point
+ * (2^-64 units) and the bracket test is exact; the interpolation weight is
+ * FP32.  d_F_opt, if not NULL, receives F_n (double, rank order).
+ * Masses must be finite, >= 0 and < 2^40 (else AMBER_ERR_INVALID_MASS latches),
+ * with a positive total.  d_order must be a permutation of [0, ncells). */
+int amber_assign_zre(amber_ctx *ctx, const uint32_t *d_order, const float *d_mass, int64_t ncells,
+                     const amber_history_t *h, float *d_zre, double *d_F_opt, void *stream);
+
+/* The whole path for one realisation: radiation field -> rank -> assign.
+ * d_src, d_mass: n^3 floats; d_zre: n^3 floats out; d_J_opt: if not NULL,
+ * n^3 floats out with the intensity.  p->precision must be 32 here. */
+int amber_solve(amber_ctx *ctx, const float *d_src, const float *d_mass, const amber_params_t *p,
+                float *d_zre, float *d_J_opt, void *stream);
+/* FP64 intensity variant (p->precision == 64, n <= 256): d_src n^3 doubles,
+ * d_J_opt n^3 doubles or NULL. */
+int amber_solve_f64(amber_ctx *ctx, const double *d_src, const float *d_mass, const amber_params_t *p,
+                    float *d_zre, double *d_J_opt, void *stream);
+
+/* Synchronise `stream`, return and clear the device status word (OR of
+ * amber_status bits latched by kernels since the last call). */
+int amber_sync_status(amber_ctx *ctx, void *stream);
+
+/* Human-readable name of a status code (static string). */
+const char *amber_status_string(int code);
+
+/* Per-kernel timing with CUDA events on the launching stream.  When enabled,
+ * every kernel launch is bracketed by events and the totals accumulate until
+ * amber_profile_reset.  amber_profile_read synchronises the context's last
+ * stream and returns, for kernel kind `kind` (0 <= kind < amber_profile_kinds()),
+ * its name, total milliseconds and launch count. */
+int amber_profile_enable(amber_ctx *ctx, int on);
+int amber_profile_reset(amber_ctx *ctx);
+int amber_profile_kinds(void);
+int amber_profile_read(amber_ctx *ctx, int kind, const char **name, double *total_ms, int64_t *launches);
+
+/* Test hook for failure detection: runs the production lookback wait on a
+ * status array nothing ever publishes, with `spin_limit` iterations, and
+ * latches AMBER_ERR_DEVICE_TIMEOUT.  No fault, no trap: the kernel returns. */
+int amber_test_wait_timeout(amber_ctx *ctx, unsigned int spin_limit, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* AMBER_H_ */

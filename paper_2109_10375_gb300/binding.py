@@ -1,0 +1,226 @@
+"""ctypes binding of libamber (include/amber.h): argument marshalling only.
+
+Every step of the path runs in the CUDA library; this module only converts
+torch tensors to raw device pointers, fills the parameter structs and turns
+non-zero status codes into exceptions.  There is no fallback: if the shared
+library is missing, importing this module raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libamber.so")
+
+AMBER_OK = 0
+AMBER_ERR_INVALID_ARG = 1
+AMBER_ERR_NO_SOLUTION = 2
+AMBER_ERR_NONFINITE = 4
+AMBER_ERR_OOM = 8
+AMBER_ERR_DEVICE_TIMEOUT = 16
+AMBER_ERR_CUDA = 32
+AMBER_ERR_INVALID_MASS = 64
+AMBER_ERR_CAPACITY = 128
+
+EXPORTED = [
+    "amber_history_default", "amber_history_coeffs", "amber_history_table", "amber_create", "amber_destroy",
+    "amber_workspace_bytes", "amber_radiation_field", "amber_radiation_field_f64", "amber_rank",
+    "amber_rank_f64", "amber_assign_zre", "amber_solve", "amber_solve_f64", "amber_sync_status",
+    "amber_status_string", "amber_profile_enable", "amber_profile_reset", "amber_profile_kinds",
+    "amber_profile_read", "amber_test_wait_timeout",
+]
+
+
+class amber_history_t(C.Structure):
+    _fields_ = [("z_mid", C.c_double), ("dz", C.c_double), ("Az", C.c_double),
+                ("x_ear", C.c_double), ("x_mid", C.c_double), ("x_lat", C.c_double),
+                ("z_lo", C.c_double), ("z_hi", C.c_double), ("n_table", C.c_int)]
+
+
+class amber_params_t(C.Structure):
+    _fields_ = [("n", C.c_int), ("box", C.c_double), ("l_mfp", C.c_double),
+                ("hist", amber_history_t), ("precision", C.c_int)]
+
+
+class AmberError(RuntimeError):
+    def __init__(self, code: int, what: str = ""):
+        self.code = code
+        super().__init__(f"{what}: amber status {code} ({status_string(code)})")
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libamber.so not built at {LIB_PATH}; run __graft_entry__.build() first")
+    lib = C.CDLL(LIB_PATH)
+    vp, i64, dbl, i32 = C.c_void_p, C.c_int64, C.c_double, C.c_int
+    H = C.POINTER(amber_history_t)
+    sig = {
+        "amber_history_default": (i32, [H, dbl, dbl, dbl]),
+        "amber_history_coeffs": (i32, [H, C.POINTER(dbl)]),
+        "amber_history_table": (i32, [H, C.POINTER(dbl), C.POINTER(dbl)]),
+        "amber_create": (i32, [C.POINTER(vp), i32, i64]),
+        "amber_destroy": (i32, [vp]),
+        "amber_workspace_bytes": (i32, [i64, C.POINTER(C.c_size_t)]),
+        "amber_radiation_field": (i32, [vp, vp, i32, dbl, dbl, vp, vp]),
+        "amber_radiation_field_f64": (i32, [vp, vp, i32, dbl, dbl, vp, vp]),
+        "amber_rank": (i32, [vp, vp, i64, vp, vp]),
+        "amber_rank_f64": (i32, [vp, vp, i64, vp, vp]),
+        "amber_assign_zre": (i32, [vp, vp, vp, i64, H, vp, vp, vp]),
+        "amber_solve": (i32, [vp, vp, vp, C.POINTER(amber_params_t), vp, vp, vp]),
+        "amber_solve_f64": (i32, [vp, vp, vp, C.POINTER(amber_params_t), vp, vp, vp]),
+        "amber_sync_status": (i32, [vp, vp]),
+        "amber_status_string": (C.c_char_p, [i32]),
+        "amber_profile_enable": (i32, [vp, i32]),
+        "amber_profile_reset": (i32, [vp]),
+        "amber_profile_kinds": (i32, []),
+        "amber_profile_read": (i32, [vp, i32, C.POINTER(C.c_char_p), C.POINTER(dbl), C.POINTER(i64)]),
+        "amber_test_wait_timeout": (i32, [vp, C.c_uint, vp]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+lib = _load()
+
+
+def status_string(code: int) -> str:
+    return lib.amber_status_string(int(code)).decode()
+
+
+def _check(code: int, what: str):
+    if code != AMBER_OK:
+        raise AmberError(code, what)
+
+
+def history(z_mid: float, dz: float, Az: float, x_points=(0.05, 0.5, 0.95), z_lo: float = 5.0,
+            z_hi: float = 20.0, n_table: int = 2000) -> amber_history_t:
+    h = amber_history_t()
+    _check(lib.amber_history_default(C.byref(h), z_mid, dz, Az), "amber_history_default")
+    h.x_ear, h.x_mid, h.x_lat = x_points
+    h.z_lo, h.z_hi, h.n_table = z_lo, z_hi, n_table
+    return h
+
+
+def history_coeffs(h: amber_history_t):
+    out = (C.c_double * 3)()
+    _check(lib.amber_history_coeffs(C.byref(h), out), "amber_history_coeffs")
+    return tuple(out)
+
+
+def history_table(h: amber_history_t):
+    import numpy as np
+    z = np.zeros(h.n_table)
+    x = np.zeros(h.n_table)
+    _check(lib.amber_history_table(C.byref(h), z.ctypes.data_as(C.POINTER(C.c_double)),
+                                   x.ctypes.data_as(C.POINTER(C.c_double))), "amber_history_table")
+    return z, x
+
+
+def workspace_bytes(max_cells: int) -> int:
+    out = C.c_size_t()
+    _check(lib.amber_workspace_bytes(max_cells, C.byref(out)), "amber_workspace_bytes")
+    return out.value
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+class Context:
+    """An amber_ctx: one device, a workspace sized for max_cells cells."""
+
+    def __init__(self, max_cells: int, device: int = 0):
+        self._h = C.c_void_p()
+        self.device = device
+        self.max_cells = max_cells
+        _check(lib.amber_create(C.byref(self._h), device, max_cells), "amber_create")
+
+    def close(self):
+        if self._h:
+            lib.amber_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # --- the path -----------------------------------------------------------
+    def radiation_field(self, S, box: float, l_mfp: float, out=None, stream=None):
+        import torch
+        n = S.shape[0]
+        f64 = S.dtype == torch.float64
+        if out is None:
+            out = torch.empty_like(S)
+        fn = lib.amber_radiation_field_f64 if f64 else lib.amber_radiation_field
+        _check(fn(self._h, _ptr(S), n, box, l_mfp, _ptr(out), _stream(stream)), "amber_radiation_field")
+        return out
+
+    def rank(self, J, out=None, stream=None):
+        import torch
+        n = J.numel()
+        if out is None:
+            out = torch.empty(n, dtype=torch.int32, device=J.device)
+        fn = lib.amber_rank_f64 if J.dtype == torch.float64 else lib.amber_rank
+        _check(fn(self._h, _ptr(J), n, _ptr(out), _stream(stream)), "amber_rank")
+        return out
+
+    def assign_zre(self, order, mass, h: amber_history_t, out=None, F=None, stream=None):
+        import torch
+        n = order.numel()
+        if out is None:
+            out = torch.empty(n, dtype=torch.float32, device=order.device)
+        _check(lib.amber_assign_zre(self._h, _ptr(order), _ptr(mass), n, C.byref(h), _ptr(out), _ptr(F),
+                                    _stream(stream)), "amber_assign_zre")
+        return out
+
+    def solve(self, S, mass, box: float, l_mfp: float, h: amber_history_t, out=None, J_out=None, stream=None):
+        import torch
+        n = S.shape[0]
+        p = amber_params_t()
+        p.n, p.box, p.l_mfp, p.hist = n, box, l_mfp, h
+        f64 = S.dtype == torch.float64
+        p.precision = 64 if f64 else 32
+        if out is None:
+            out = torch.empty(S.shape, dtype=torch.float32, device=S.device)
+        fn = lib.amber_solve_f64 if f64 else lib.amber_solve
+        _check(fn(self._h, _ptr(S), _ptr(mass), C.byref(p), _ptr(out), _ptr(J_out), _stream(stream)), "amber_solve")
+        return out
+
+    def sync_status(self, stream=None) -> int:
+        return lib.amber_sync_status(self._h, _stream(stream))
+
+    # --- profiling ----------------------------------------------------------
+    def profile(self, on: bool = True):
+        _check(lib.amber_profile_enable(self._h, 1 if on else 0), "amber_profile_enable")
+
+    def profile_reset(self):
+        _check(lib.amber_profile_reset(self._h), "amber_profile_reset")
+
+    def profile_read(self) -> dict:
+        out = {}
+        for k in range(lib.amber_profile_kinds()):
+            name, ms, cnt = C.c_char_p(), C.c_double(), C.c_int64()
+            _check(lib.amber_profile_read(self._h, k, C.byref(name), C.byref(ms), C.byref(cnt)), "amber_profile_read")
+            out[name.value.decode()] = (ms.value, cnt.value)
+        return out
+
+    def test_wait_timeout(self, spin_limit: int, stream=None):
+        _check(lib.amber_test_wait_timeout(self._h, spin_limit, _stream(stream)), "amber_test_wait_timeout")

@@ -1,0 +1,552 @@
+// Host runtime of libamber: argument validation, the Weibull history solve
+// (Sec. 3.1.2, Appendix A), the context and its one-time workspace, per-
+// kernel event timing, and the extern "C" entry points declared in amber.h.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "assign.cuh"
+#include "fft.cuh"
+#include "sort.cuh"
+
+namespace amber {
+cudaError_t radiation_field_f32(int n, const float* src, float* J, void* H, const void* tw, double box, double l_mfp,
+                               unsigned int* status, cudaStream_t s, FftProfile* prof);
+cudaError_t radiation_field_f64(int n, const double* src, double* J, void* H, const void* tw, double box,
+                               double l_mfp, unsigned int* status, cudaStream_t s, FftProfile* prof);
+
+// ---------------------------------------------------------------------------
+// Per-kernel timing: a pool of events recorded around launches.
+// ---------------------------------------------------------------------------
+static const char* kProfNames[PK_COUNT] = {
+    "fft_r2c_x", "fft_y_fwd", "fft_z_conv", "fft_y_inv", "fft_c2r_x",
+    "sort_histogram", "sort_pass", "mass_reduce", "thresholds", "scan_assign"};
+
+struct FftProfile {
+  bool on = false;
+  int device = 0;
+  std::vector<cudaEvent_t> pool;
+  size_t used = 0;
+  struct Rec { int kind; size_t ev; };
+  std::vector<Rec> recs;
+  int open_kind = -1;
+  double total_ms[PK_COUNT] = {};
+  int64_t launches[PK_COUNT] = {};
+};
+
+void prof_begin(FftProfile* p, int kind, cudaStream_t s) {
+  if (!p || !p->on) return;
+  if (p->used + 2 > p->pool.size()) { p->open_kind = -1; return; }
+  cudaEventRecord(p->pool[p->used], s);
+  p->recs.push_back({kind, p->used});
+  p->used += 2;
+  p->open_kind = kind;
+}
+void prof_end(FftProfile* p, int kind, cudaStream_t s) {
+  if (!p || !p->on || p->open_kind != kind) return;
+  cudaEventRecord(p->pool[p->recs.back().ev + 1], s);
+  p->open_kind = -1;
+}
+static void prof_harvest(FftProfile* p) {
+  for (const auto& r : p->recs) {
+    cudaEventSynchronize(p->pool[r.ev + 1]);
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, p->pool[r.ev], p->pool[r.ev + 1]) == cudaSuccess) {
+      p->total_ms[r.kind] += ms;
+      p->launches[r.kind] += 1;
+    }
+  }
+  p->recs.clear();
+  p->used = 0;
+}
+
+// ---------------------------------------------------------------------------
+// Weibull history (Sec. 3.1.1, 3.1.2, Appendix A) in FP64 on the host.
+// ---------------------------------------------------------------------------
+static bool history_valid(const amber_history_t* h) {
+  if (!h) return false;
+  const double v[] = {h->z_mid, h->dz, h->Az, h->x_ear, h->x_mid, h->x_lat, h->z_lo, h->z_hi};
+  for (double x : v)
+    if (!std::isfinite(x)) return false;
+  if (!(0.0 < h->x_ear && h->x_ear < h->x_mid && h->x_mid < h->x_lat && h->x_lat < 1.0)) return false;
+  if (!(h->dz > 0.0 && h->Az > 0.0)) return false;
+  if (!(h->z_hi > h->z_lo)) return false;
+  if (h->n_table < 2 || h->n_table > kMaxTable) return false;
+  return true;
+}
+
+// Offset a through the mid and late points for power c (Appendix A).
+static double a_mid_lat(double c, double zm, double zl, double Lm, double Ll) {
+  const double pm = std::pow(Lm, 1.0 / c), pl = std::pow(Ll, 1.0 / c);
+  return (zl * pm - zm * pl) / (pm - pl);
+}
+
+static int weibull_solve(const amber_history_t* h, double* a_out, double* b_out, double* c_out) {
+  if (!history_valid(h)) return AMBER_ERR_INVALID_ARG;
+  const double ze = h->z_mid + h->dz * h->Az / (1.0 + h->Az);  // Eq. zear
+  const double zm = h->z_mid;
+  const double zl = ze - h->dz;                                 // Eq. duration
+  const double Le = std::fabs(std::log(h->x_ear)), Lm = std::fabs(std::log(h->x_mid)),
+               Ll = std::fabs(std::log(h->x_lat));
+  auto f = [&](double c) {
+    const double a = a_mid_lat(c, zm, zl, Lm, Ll);
+    return std::pow(Le / Lm, 1.0 / c) - (ze - a) / (zm - a);
+  };
+  const int G = 400;
+  const double lc0 = std::log(0.05), lc1 = std::log(100.0);
+  double cprev = std::exp(lc0), fprev = f(cprev);
+  for (int i = 1; i <= G; ++i) {
+    const double c = std::exp(lc0 + (lc1 - lc0) * i / G);
+    const double fc = f(c);
+    const bool ok = std::isfinite(fprev) && std::isfinite(fc) && !(fprev * fc > 0.0);
+    if (ok) {
+      double lo = cprev, hi = c, flo = fprev;
+      for (int it = 0; it < 200; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        const double fm = f(mid);
+        if (fm == 0.0) { lo = hi = mid; break; }
+        if ((fm > 0.0) == (flo > 0.0)) { lo = mid; flo = fm; } else { hi = mid; }
+        if (hi - lo <= 1e-15 * hi) break;
+      }
+      const double cw = 0.5 * (lo + hi);
+      const double pe = std::pow(Le, 1.0 / cw), pl = std::pow(Ll, 1.0 / cw);
+      const double aw = (ze * pl - zl * pe) / (pl - pe);
+      const double bw = (zm - aw) / std::pow(Lm, 1.0 / cw);
+      if (aw > 0.0 && bw > 0.0 && cw > 0.0) {
+        *a_out = aw; *b_out = bw; *c_out = cw;
+        return AMBER_OK;
+      }
+    }
+    cprev = c;
+    fprev = fc;
+  }
+  return AMBER_ERR_NO_SOLUTION;
+}
+
+static int history_coeffs(const amber_history_t* h, HistoryCoeffs* hc) {
+  double a, b, c;
+  const int st = weibull_solve(h, &a, &b, &c);
+  if (st != AMBER_OK) return st;
+  hc->a = a; hc->b = b; hc->c = c;
+  hc->z_lo = std::fmin(h->z_lo, a);  // reach the fully ionized plateau
+  hc->z_hi = h->z_hi;
+  hc->n_table = h->n_table;
+  return AMBER_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Workspace plan.
+// ---------------------------------------------------------------------------
+static int fft_nmax(int64_t cells) {
+  int n = 0;
+  for (int m = 4; m <= 1024; m *= 2)
+    if ((int64_t)m * m * m <= cells) n = m;
+  return n;
+}
+
+struct Plan {
+  int n32 = 0, n64 = 0;
+  int64_t cells64 = 0;
+  size_t off_spec, off_keysA, off_keysB, off_idxA, off_idxB, off_lb, off_sctrl, off_actrl, off_X, off_invdx,
+      off_state, off_status, off_tw32, off_tw64, total;
+  size_t tw32_off[11] = {}, tw64_off[11] = {};
+};
+
+static size_t align256(size_t v) { return (v + 255) / 256 * 256; }
+
+static Plan make_plan(int64_t max_cells) {
+  Plan p;
+  p.n32 = fft_nmax(max_cells);
+  p.n64 = std::min(p.n32, 256);
+  p.cells64 = std::min<int64_t>(max_cells, (int64_t)1 << 24);
+  auto spec_bytes = [](int n, size_t elem) { return n ? (size_t)n * n * (n / 2 + 2) * elem : 0; };
+  const size_t spec = std::max(spec_bytes(p.n32, 8), spec_bytes(p.n64, 16));
+  const size_t keyb = std::max((size_t)max_cells * 4, (size_t)p.cells64 * 8);
+  const size_t idxb = (size_t)max_cells * 4;
+  const size_t lb = 2 * (size_t)sort_tiles(max_cells) * kRadix * 4;
+  const size_t stt = (size_t)((max_cells + kScanTile - 1) / kScanTile) * sizeof(ScanTile);
+  size_t o = 0;
+  auto take = [&](size_t bytes) { const size_t at = o; o += align256(bytes); return at; };
+  p.off_spec = take(spec);
+  p.off_keysA = take(keyb);
+  p.off_keysB = take(keyb);
+  p.off_idxA = take(idxb);
+  p.off_idxB = take(idxb);
+  p.off_lb = take(lb);
+  p.off_sctrl = take(kSortCtrlBytes);
+  p.off_actrl = take(kAssignCtrlBytes);
+  p.off_X = take((size_t)kMaxTable * sizeof(u128));
+  p.off_invdx = take((size_t)kMaxTable * sizeof(float));
+  p.off_state = take(stt);
+  p.off_status = take(256);
+  size_t tw32 = 0, tw64 = 0;
+  for (int l = 2, n = 4; n <= 1024; ++l, n *= 2) {
+    if (n <= p.n32) { p.tw32_off[l] = tw32; tw32 += align256((size_t)n * 8); }
+    if (n <= p.n64) { p.tw64_off[l] = tw64; tw64 += align256((size_t)n * 16); }
+  }
+  p.off_tw32 = take(tw32);
+  p.off_tw64 = take(tw64);
+  p.total = o;
+  return p;
+}
+
+static int ilog2i(int n) { int l = 0; while ((1 << l) < n) ++l; return l; }
+
+}  // namespace amber
+
+using namespace amber;
+
+struct amber_ctx {
+  int device = 0;
+  int64_t max_cells = 0;
+  Plan plan;
+  unsigned char* ws = nullptr;
+  unsigned int* status = nullptr;
+  unsigned int* h_status = nullptr;  // pinned
+  SortWork sortw{};
+  AssignWork assw{};
+  int num_sms = 0;
+  FftProfile prof;
+  cudaStream_t last_stream = nullptr;
+  std::mutex mu;
+};
+
+namespace {
+
+struct DeviceGuard {
+  int prev = -1;
+  bool changed = false;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) changed = cudaSetDevice(dev) == cudaSuccess;
+  }
+  ~DeviceGuard() {
+    if (changed) cudaSetDevice(prev);
+  }
+};
+
+bool is_pow2_in(int n, int lo, int hi) { return n >= lo && n <= hi && (n & (n - 1)) == 0; }
+
+int cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return AMBER_OK;
+  return AMBER_ERR_CUDA;
+}
+
+}  // namespace
+
+extern "C" {
+
+int amber_history_default(amber_history_t* h, double z_mid, double dz, double Az) {
+  if (!h) return AMBER_ERR_INVALID_ARG;
+  h->z_mid = z_mid; h->dz = dz; h->Az = Az;
+  h->x_ear = 0.05; h->x_mid = 0.50; h->x_lat = 0.95;
+  h->z_lo = 5.0; h->z_hi = 20.0; h->n_table = 2000;
+  return AMBER_OK;
+}
+
+int amber_history_coeffs(const amber_history_t* h, double out_abc[3]) {
+  if (!h || !out_abc) return AMBER_ERR_INVALID_ARG;
+  double a, b, c;
+  const int st = weibull_solve(h, &a, &b, &c);
+  if (st != AMBER_OK) return st;
+  out_abc[0] = a; out_abc[1] = b; out_abc[2] = c;
+  return AMBER_OK;
+}
+
+int amber_history_table(const amber_history_t* h, double* z_out, double* x_out) {
+  if (!h || !z_out || !x_out) return AMBER_ERR_INVALID_ARG;
+  HistoryCoeffs hc;
+  const int st = history_coeffs(h, &hc);
+  if (st != AMBER_OK) return st;
+  for (int j = 0; j < hc.n_table; ++j) {
+    const double z = hc.z_lo + (hc.z_hi - hc.z_lo) * (double)j / (double)(hc.n_table - 1);
+    const double u = std::fmax((z - hc.a) / hc.b, 0.0);
+    z_out[j] = z;
+    x_out[j] = std::exp(-std::pow(u, hc.c));
+  }
+  return AMBER_OK;
+}
+
+int amber_workspace_bytes(int64_t max_cells, size_t* out_bytes) {
+  if (!out_bytes || max_cells < 1 || max_cells > ((int64_t)1 << 30)) return AMBER_ERR_INVALID_ARG;
+  *out_bytes = make_plan(max_cells).total;
+  return AMBER_OK;
+}
+
+int amber_create(amber_ctx** out, int device, int64_t max_cells) {
+  if (!out || max_cells < 1 || max_cells > ((int64_t)1 << 30) || device < 0) return AMBER_ERR_INVALID_ARG;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device >= ndev) {
+    cudaGetLastError();
+    return AMBER_ERR_CUDA;
+  }
+  DeviceGuard g(device);
+  amber_ctx* c = new (std::nothrow) amber_ctx();
+  if (!c) return AMBER_ERR_OOM;
+  c->device = device;
+  c->max_cells = max_cells;
+  c->plan = make_plan(max_cells);
+  cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+  if (cudaMalloc(&c->ws, c->plan.total) != cudaSuccess) {
+    cudaGetLastError();
+    delete c;
+    return AMBER_ERR_OOM;
+  }
+  if (cudaMallocHost(&c->h_status, sizeof(unsigned int)) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(c->ws);
+    delete c;
+    return AMBER_ERR_CUDA;
+  }
+  const Plan& p = c->plan;
+  c->status = reinterpret_cast<unsigned int*>(c->ws + p.off_status);
+  cudaMemset(c->ws + p.off_status, 0, 256);
+  c->sortw.keysA = c->ws + p.off_keysA;
+  c->sortw.keysB = c->ws + p.off_keysB;
+  c->sortw.idxA = reinterpret_cast<uint32_t*>(c->ws + p.off_idxA);
+  c->sortw.idxB = reinterpret_cast<uint32_t*>(c->ws + p.off_idxB);
+  c->sortw.lookback = reinterpret_cast<uint32_t*>(c->ws + p.off_lb);
+  c->sortw.ctrl = reinterpret_cast<uint32_t*>(c->ws + p.off_sctrl);
+  c->sortw.num_sms = c->num_sms;
+  c->assw.ctrl = c->ws + p.off_actrl;
+  c->assw.X = reinterpret_cast<u128*>(c->ws + p.off_X);
+  c->assw.inv_dx = reinterpret_cast<float*>(c->ws + p.off_invdx);
+  c->assw.state = reinterpret_cast<ScanTile*>(c->ws + p.off_state);
+  c->assw.num_sms = c->num_sms;
+  // twiddles w_n^m = exp(-2 pi i m / n), FP64 on the host, rounded for FP32
+  for (int l = 6, n = 64; n <= p.n32; ++l, n *= 2) {
+    std::vector<float> t32(2 * n);
+    std::vector<double> t64(2 * n);
+    for (int m = 0; m < n; ++m) {
+      const double ang = -2.0 * M_PI * (double)m / (double)n;
+      t64[2 * m] = std::cos(ang);
+      t64[2 * m + 1] = std::sin(ang);
+      t32[2 * m] = (float)t64[2 * m];
+      t32[2 * m + 1] = (float)t64[2 * m + 1];
+    }
+    cudaMemcpy(c->ws + p.off_tw32 + p.tw32_off[l], t32.data(), t32.size() * 4, cudaMemcpyHostToDevice);
+    if (n <= p.n64) cudaMemcpy(c->ws + p.off_tw64 + p.tw64_off[l], t64.data(), t64.size() * 8, cudaMemcpyHostToDevice);
+  }
+  if (cudaDeviceSynchronize() != cudaSuccess) {
+    cudaGetLastError();
+    cudaFreeHost(c->h_status);
+    cudaFree(c->ws);
+    delete c;
+    return AMBER_ERR_CUDA;
+  }
+  *out = c;
+  return AMBER_OK;
+}
+
+int amber_destroy(amber_ctx* c) {
+  if (!c) return AMBER_ERR_INVALID_ARG;
+  {
+    DeviceGuard g(c->device);
+    cudaDeviceSynchronize();
+    for (auto e : c->prof.pool) cudaEventDestroy(e);
+    if (c->h_status) cudaFreeHost(c->h_status);
+    if (c->ws) cudaFree(c->ws);
+  }
+  delete c;
+  return AMBER_OK;
+}
+
+static int rf_args_ok(amber_ctx* c, const void* src, int n, double box, double l, const void* J, int nmax) {
+  if (!c || !src || !J) return AMBER_ERR_INVALID_ARG;
+  if (!is_pow2_in(n, 4, 1024) || !(box > 0.0) || !std::isfinite(box) || !(l > 0.0) || !std::isfinite(l))
+    return AMBER_ERR_INVALID_ARG;
+  if (n > nmax) return AMBER_ERR_CAPACITY;
+  return AMBER_OK;
+}
+
+int amber_radiation_field(amber_ctx* c, const float* d_src, int n, double box, double l_mfp, float* d_J,
+                          void* stream) {
+  int st = rf_args_ok(c, d_src, n, box, l_mfp, d_J, c ? c->plan.n32 : 0);
+  if (st) return st;
+  std::lock_guard<std::mutex> lk(c->mu);
+  DeviceGuard g(c->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  c->last_stream = s;
+  const Plan& p = c->plan;
+  const int l = ilog2i(n);
+  return cuda_status(radiation_field_f32(n, d_src, d_J, c->ws + p.off_spec, c->ws + p.off_tw32 + p.tw32_off[l], box,
+                                         l_mfp, c->status, s, &c->prof));
+}
+
+int amber_radiation_field_f64(amber_ctx* c, const double* d_src, int n, double box, double l_mfp, double* d_J,
+                              void* stream) {
+  int st = rf_args_ok(c, d_src, n, box, l_mfp, d_J, c ? c->plan.n64 : 0);
+  if (st) return st;
+  std::lock_guard<std::mutex> lk(c->mu);
+  DeviceGuard g(c->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  c->last_stream = s;
+  const Plan& p = c->plan;
+  const int l = ilog2i(n);
+  return cuda_status(radiation_field_f64(n, d_src, d_J, c->ws + p.off_spec, c->ws + p.off_tw64 + p.tw64_off[l], box,
+                                         l_mfp, c->status, s, &c->prof));
+}
+
+int amber_rank(amber_ctx* c, const float* d_J, int64_t ncells, uint32_t* d_order, void* stream) {
+  if (!c || !d_J || !d_order || ncells < 1) return AMBER_ERR_INVALID_ARG;
+  if (ncells > c->max_cells) return AMBER_ERR_CAPACITY;
+  std::lock_guard<std::mutex> lk(c->mu);
+  DeviceGuard g(c->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  c->last_stream = s;
+  return cuda_status(rank_impl<float>(c->sortw, d_J, ncells, d_order, c->status, s, &c->prof, kSpinLimit));
+}
+
+int amber_rank_f64(amber_ctx* c, const double* d_J, int64_t ncells, uint32_t* d_order, void* stream) {
+  if (!c || !d_J || !d_order || ncells < 1) return AMBER_ERR_INVALID_ARG;
+  if (ncells > c->plan.cells64) return AMBER_ERR_CAPACITY;
+  std::lock_guard<std::mutex> lk(c->mu);
+  DeviceGuard g(c->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  c->last_stream = s;
+  return cuda_status(rank_impl<double>(c->sortw, d_J, ncells, d_order, c->status, s, &c->prof, kSpinLimit));
+}
+
+int amber_assign_zre(amber_ctx* c, const uint32_t* d_order, const float* d_mass, int64_t ncells,
+                     const amber_history_t* h, float* d_zre, double* d_F_opt, void* stream) {
+  if (!c || !d_order || !d_mass || !d_zre || ncells < 1) return AMBER_ERR_INVALID_ARG;
+  if (ncells > c->max_cells) return AMBER_ERR_CAPACITY;
+  HistoryCoeffs hc;
+  const int st = history_coeffs(h, &hc);
+  if (st) return st;
+  std::lock_guard<std::mutex> lk(c->mu);
+  DeviceGuard g(c->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  c->last_stream = s;
+  return cuda_status(assign_impl(c->assw, d_order, d_mass, ncells, hc, d_zre, d_F_opt, c->status, s, &c->prof,
+                                 kSpinLimit));
+}
+
+static int solve_args(amber_ctx* c, const void* src, const float* mass, const amber_params_t* p, const float* zre,
+                      int want_prec, int nmax, HistoryCoeffs* hc) {
+  if (!c || !src || !mass || !p || !zre) return AMBER_ERR_INVALID_ARG;
+  if (p->precision != want_prec) return AMBER_ERR_INVALID_ARG;
+  int st = rf_args_ok(c, src, p->n, p->box, p->l_mfp, zre, nmax);
+  if (st) return st;
+  return history_coeffs(&p->hist, hc);
+}
+
+int amber_solve(amber_ctx* c, const float* d_src, const float* d_mass, const amber_params_t* p, float* d_zre,
+                float* d_J_opt, void* stream) {
+  HistoryCoeffs hc;
+  int st = solve_args(c, d_src, d_mass, p, d_zre, 32, c ? c->plan.n32 : 0, &hc);
+  if (st) return st;
+  std::lock_guard<std::mutex> lk(c->mu);
+  DeviceGuard g(c->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  c->last_stream = s;
+  const Plan& pl = c->plan;
+  const int n = p->n;
+  const int64_t C = (int64_t)n * n * n;
+  float* J = d_J_opt ? d_J_opt : reinterpret_cast<float*>(c->sortw.keysB);
+  cudaError_t e = radiation_field_f32(n, d_src, J, c->ws + pl.off_spec, c->ws + pl.off_tw32 + pl.tw32_off[ilog2i(n)],
+                                      p->box, p->l_mfp, c->status, s, &c->prof);
+  if (e == cudaSuccess) e = rank_impl<float>(c->sortw, J, C, c->sortw.idxB, c->status, s, &c->prof, kSpinLimit);
+  if (e == cudaSuccess)
+    e = assign_impl(c->assw, c->sortw.idxB, d_mass, C, hc, d_zre, nullptr, c->status, s, &c->prof, kSpinLimit);
+  return cuda_status(e);
+}
+
+int amber_solve_f64(amber_ctx* c, const double* d_src, const float* d_mass, const amber_params_t* p, float* d_zre,
+                    double* d_J_opt, void* stream) {
+  HistoryCoeffs hc;
+  int st = solve_args(c, d_src, d_mass, p, d_zre, 64, c ? c->plan.n64 : 0, &hc);
+  if (st) return st;
+  std::lock_guard<std::mutex> lk(c->mu);
+  DeviceGuard g(c->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  c->last_stream = s;
+  const Plan& pl = c->plan;
+  const int n = p->n;
+  const int64_t C = (int64_t)n * n * n;
+  double* J = d_J_opt ? d_J_opt : reinterpret_cast<double*>(c->sortw.keysB);
+  cudaError_t e = radiation_field_f64(n, d_src, J, c->ws + pl.off_spec, c->ws + pl.off_tw64 + pl.tw64_off[ilog2i(n)],
+                                      p->box, p->l_mfp, c->status, s, &c->prof);
+  if (e == cudaSuccess) e = rank_impl<double>(c->sortw, J, C, c->sortw.idxB, c->status, s, &c->prof, kSpinLimit);
+  if (e == cudaSuccess)
+    e = assign_impl(c->assw, c->sortw.idxB, d_mass, C, hc, d_zre, nullptr, c->status, s, &c->prof, kSpinLimit);
+  return cuda_status(e);
+}
+
+int amber_sync_status(amber_ctx* c, void* stream) {
+  if (!c) return AMBER_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(c->mu);
+  DeviceGuard g(c->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (cudaMemcpyAsync(c->h_status, c->status, sizeof(unsigned int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaMemsetAsync(c->status, 0, sizeof(unsigned int), s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess) {
+    cudaGetLastError();
+    return AMBER_ERR_CUDA;
+  }
+  return (int)*c->h_status;
+}
+
+const char* amber_status_string(int code) {
+  switch (code) {
+    case AMBER_OK: return "ok";
+    case AMBER_ERR_INVALID_ARG: return "invalid argument";
+    case AMBER_ERR_NO_SOLUTION: return "no Weibull solution with positive coefficients";
+    case AMBER_ERR_NONFINITE: return "non-finite intensity";
+    case AMBER_ERR_OOM: return "device workspace allocation failed";
+    case AMBER_ERR_DEVICE_TIMEOUT: return "device wait timed out";
+    case AMBER_ERR_CUDA: return "CUDA runtime error";
+    case AMBER_ERR_INVALID_MASS: return "invalid cell mass";
+    case AMBER_ERR_CAPACITY: return "size exceeds context capacity";
+    default: return "multiple or unknown status bits";
+  }
+}
+
+int amber_profile_enable(amber_ctx* c, int on) {
+  if (!c) return AMBER_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(c->mu);
+  DeviceGuard g(c->device);
+  if (on && c->prof.pool.empty()) {
+    c->prof.pool.resize(8192);
+    for (auto& e : c->prof.pool)
+      if (cudaEventCreate(&e) != cudaSuccess) return AMBER_ERR_CUDA;
+  }
+  c->prof.on = on != 0;
+  return AMBER_OK;
+}
+
+int amber_profile_reset(amber_ctx* c) {
+  if (!c) return AMBER_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(c->mu);
+  DeviceGuard g(c->device);
+  prof_harvest(&c->prof);
+  for (int k = 0; k < PK_COUNT; ++k) { c->prof.total_ms[k] = 0.0; c->prof.launches[k] = 0; }
+  return AMBER_OK;
+}
+
+int amber_profile_kinds(void) { return PK_COUNT; }
+
+int amber_profile_read(amber_ctx* c, int kind, const char** name, double* total_ms, int64_t* launches) {
+  if (!c || kind < 0 || kind >= PK_COUNT) return AMBER_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(c->mu);
+  DeviceGuard g(c->device);
+  prof_harvest(&c->prof);
+  if (name) *name = kProfNames[kind];
+  if (total_ms) *total_ms = c->prof.total_ms[kind];
+  if (launches) *launches = c->prof.launches[kind];
+  return AMBER_OK;
+}
+
+int amber_test_wait_timeout(amber_ctx* c, unsigned int spin_limit, void* stream) {
+  if (!c || spin_limit < 1) return AMBER_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(c->mu);
+  DeviceGuard g(c->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  uint32_t* word = reinterpret_cast<uint32_t*>(c->ws + c->plan.off_status + 64);
+  return cuda_status(wait_timeout_test(word, c->status, spin_limit, s));
+}
+
+}  // extern "C"

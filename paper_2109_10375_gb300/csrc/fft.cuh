@@ -1,0 +1,448 @@
+// Radiation field J = IDFT(DFT(S) * K(|k|)) on an n^3 periodic grid
+// (Sec. 3.4.1, Eq. intensity), as five HBM passes over a half spectrum:
+//
+//   x-pass  R2C   S[z][y][x]      -> H[z][y][kx]      (two real rows per complex FFT)
+//   y-pass  fwd   H along y, in place
+//   z-pass  fwd along z, multiply by K(|k|)/n^3, inverse along z (one round trip)
+//   y-pass  inv   H along y, in place
+//   x-pass  C2R   H -> J[z][y][x]
+//
+// H is [n][n][RS] complex with RS = n/2 + 2 (rows 16-byte aligned); columns
+// kx in [0, n/2] are live.  Each CTA transforms a batch of lines held in
+// registers and shared memory with a two-stage Stockham decomposition
+// n = R0 * R1 (R0 = n for n <= 32): stage A reads its inputs straight from
+// global memory, stage B writes its outputs straight back, so every 1D
+// transform costs one read and one write of the line and one shared-memory
+// exchange.  In the z-pass the forward stage B and the inverse stage A touch
+// the same register set, so the kernel multiply happens in registers.
+#pragma once
+
+#include "common.cuh"
+
+namespace amber {
+
+template <int N> struct FftCfg;
+//                                        R0  R1   E  strided-lines  x-pairs
+template <> struct FftCfg<1024> { static constexpr int R0 = 32, R1 = 32, E = 32, SB = 8,  XP = 8;  };
+template <> struct FftCfg<512>  { static constexpr int R0 = 32, R1 = 16, E = 32, SB = 16, XP = 16; };
+template <> struct FftCfg<256>  { static constexpr int R0 = 16, R1 = 16, E = 16, SB = 16, XP = 16; };
+template <> struct FftCfg<128>  { static constexpr int R0 = 16, R1 = 8,  E = 16, SB = 32, XP = 32; };
+template <> struct FftCfg<64>   { static constexpr int R0 = 8,  R1 = 8,  E = 8,  SB = 32, XP = 32; };
+template <> struct FftCfg<32>   { static constexpr int R0 = 32, R1 = 1,  E = 32, SB = 32, XP = 32; };
+template <> struct FftCfg<16>   { static constexpr int R0 = 16, R1 = 1,  E = 16, SB = 32, XP = 32; };
+template <> struct FftCfg<8>    { static constexpr int R0 = 8,  R1 = 1,  E = 8,  SB = 32, XP = 32; };
+template <> struct FftCfg<4>    { static constexpr int R0 = 4,  R1 = 1,  E = 4,  SB = 32, XP = 32; };
+
+template <int N> constexpr int strided_threads() { return FftCfg<N>::SB * N / FftCfg<N>::E; }
+template <int N> constexpr int xpass_threads() { return FftCfg<N>::XP * N / FftCfg<N>::E; }
+
+// Shared-memory layout of a strided tile: element (n, b) of line b.  With
+// 8 float2 lines a row is 64 bytes; the pad per 32 rows puts the row groups
+// a stage-A butterfly writes (n = 32 j + r) on alternating bank halves.
+template <typename T, int N> struct StridedSmem {
+  static constexpr int SB = FftCfg<N>::SB;
+  static constexpr int PAD = (SB * (int)sizeof(cpx<T>) == 64) ? 8 : 0;
+  static constexpr int elems = N * SB + (N / 32) * PAD;
+  static __device__ __forceinline__ int pos(int n, int b) { return n * SB + b + (n >> 5) * PAD; }
+};
+
+// Shared-memory layout of x-pass lines: line p, element n.  One pad element
+// per R0 keeps stage-A writes (n = R0 j + r, lanes along j) conflict-free.
+template <typename T, int N> struct XSmem {
+  static constexpr int R0 = FftCfg<N>::R0;
+  static constexpr int LS = N + N / R0;
+  static constexpr int elems = FftCfg<N>::XP * LS;
+  static __device__ __forceinline__ int pos(int p, int n) { return p * LS + n + n / R0; }
+};
+
+template <typename T> __device__ __forceinline__ T kernel_K(T k2, T l_mfp, T kf, T norm);
+template <> __device__ __forceinline__ float kernel_K<float>(float k2, float l, float kf, float norm) {
+  if (k2 == 0.f) return l * norm;
+  const float k = kf * sqrtf(k2);
+  return atanf(k * l) / k * norm;
+}
+template <> __device__ __forceinline__ double kernel_K<double>(double k2, double l, double kf, double norm) {
+  if (k2 == 0.0) return l * norm;
+  const double k = kf * sqrt(k2);
+  return atan(k * l) / k * norm;
+}
+
+__device__ __forceinline__ int signed_freq(int m, int n) { return m < n / 2 ? m : m - n; }
+
+// ---------------------------------------------------------------------------
+// Strided passes (y forward, y inverse, z convolution).  A CTA owns SB
+// consecutive kx columns of one line family; lane mapping is column-fastest
+// so each row of the tile is one contiguous global segment.
+// ---------------------------------------------------------------------------
+enum { PASS_FWD = 0, PASS_INV = 1, PASS_CONV = 2 };
+
+template <typename T, int N, int MODE>
+__global__ void __launch_bounds__(strided_threads<N>())
+k_fft_strided(cpx<T>* __restrict__ H, int64_t elem_stride, int64_t outer_stride, int ncol,
+              int ntx, const cpx<T>* __restrict__ tw, T kf, T l_mfp, T norm) {
+  using C = FftCfg<N>;
+  using L = StridedSmem<T, N>;
+  constexpr int R0 = C::R0, R1 = C::R1, E = C::E, SB = C::SB, NT = strided_threads<N>();
+  constexpr int QA = E / R0, QB = (R1 > 1) ? E / R1 : 0;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cpx<T>* sm = reinterpret_cast<cpx<T>*>(smem_raw);
+
+  const int tid = threadIdx.x;
+  const int outer = blockIdx.x / ntx;
+  const int kx0 = (blockIdx.x - outer * ntx) * SB;
+  cpx<T>* base = H + (int64_t)outer * outer_stride + kx0;
+
+  cpx<T> v[E];
+  // ---- forward stage A: radix R0 over n = j + r N/R0, read from global
+#pragma unroll
+  for (int q = 0; q < QA; ++q) {
+    const int id = tid + q * NT;
+    const int b = id % SB, j = id / SB;
+    const bool ok = kx0 + b < ncol;
+#pragma unroll
+    for (int r = 0; r < R0; ++r) {
+      const int n = j + r * (N / R0);
+      v[q * R0 + r] = ok ? base[(int64_t)n * elem_stride + b] : mk<T>(0, 0);
+    }
+    dft<R0, MODE == PASS_INV>(v + q * R0);
+  }
+  if constexpr (R1 == 1) {
+    // single stage (n <= 32): v already holds natural order n = r for j = 0
+  } else {
+#pragma unroll
+    for (int q = 0; q < QA; ++q) {
+      const int id = tid + q * NT;
+      const int b = id % SB, j = id / SB;
+#pragma unroll
+      for (int r = 0; r < R0; ++r) sm[L::pos(j * R0 + r, b)] = v[q * R0 + r];
+    }
+    __syncthreads();
+    // ---- forward stage B: radix R1 over n = j + r R0, twiddle w_N^(j r)
+#pragma unroll
+    for (int q = 0; q < QB; ++q) {
+      const int id = tid + q * NT;
+      const int b = id % SB, j = id / SB;
+#pragma unroll
+      for (int r = 0; r < R1; ++r) {
+        cpx<T> x = sm[L::pos(j + r * R0, b)];
+        if (r > 0) {
+          const cpx<T> w = tw[j * r];
+          x = (MODE == PASS_INV) ? cmulc(x, w) : cmul(x, w);
+        }
+        v[q * R1 + r] = x;
+      }
+      dft<R1, MODE == PASS_INV>(v + q * R1);
+    }
+  }
+
+  if constexpr (MODE != PASS_CONV) {
+    // ---- write natural order n = j + r R0 (or n = r when single stage)
+    constexpr int QO = (R1 > 1) ? QB : QA;
+    constexpr int RO = (R1 > 1) ? R1 : R0;
+#pragma unroll
+    for (int q = 0; q < QO; ++q) {
+      const int id = tid + q * NT;
+      const int b = id % SB, j = id / SB;
+      if (kx0 + b < ncol) {
+#pragma unroll
+        for (int r = 0; r < RO; ++r) {
+          const int n = (R1 > 1) ? j + r * R0 : r;
+          base[(int64_t)n * elem_stride + b] = v[q * RO + r];
+        }
+      }
+    }
+  } else {
+    // ---- z-pass: multiply by K(|k|)/n^3 at kz = n, ky = outer, kx = kx0 + b
+    constexpr int QO = (R1 > 1) ? QB : QA;
+    constexpr int RO = (R1 > 1) ? R1 : R0;
+    const int ky = signed_freq(outer, N);
+#pragma unroll
+    for (int q = 0; q < QO; ++q) {
+      const int id = tid + q * NT;
+      const int b = id % SB, j = id / SB;
+      const int kx = kx0 + b;
+#pragma unroll
+      for (int r = 0; r < RO; ++r) {
+        const int n = (R1 > 1) ? j + r * R0 : r;
+        const int kz = signed_freq(n, N);
+        const T k2 = (T)(kx * kx + ky * ky + kz * kz);
+        v[q * RO + r] = scale(v[q * RO + r], kernel_K<T>(k2, l_mfp, kf, norm));
+      }
+      // inverse stage A (radix RO) on the same elements: n = j + r N/RO
+      dft<RO, true>(v + q * RO);
+    }
+    if constexpr (R1 > 1) {
+      // inverse plan is (R1, R0): stage A wrote n = j R1 + r
+      __syncthreads();  // all forward stage-B reads of sm are done
+#pragma unroll
+      for (int q = 0; q < QB; ++q) {
+        const int id = tid + q * NT;
+        const int b = id % SB, j = id / SB;
+#pragma unroll
+        for (int r = 0; r < R1; ++r) sm[L::pos(j * R1 + r, b)] = v[q * R1 + r];
+      }
+      __syncthreads();
+      // inverse stage B: radix R0 over n = j + r R1, twiddle conj(w_N^(j r))
+#pragma unroll
+      for (int q = 0; q < QA; ++q) {
+        const int id = tid + q * NT;
+        const int b = id % SB, j = id / SB;
+#pragma unroll
+        for (int r = 0; r < R0; ++r) {
+          cpx<T> x = sm[L::pos(j + r * R1, b)];
+          if (r > 0) x = cmulc(x, tw[j * r]);
+          v[q * R0 + r] = x;
+        }
+        dft<R0, true>(v + q * R0);
+        if (kx0 + b < ncol) {
+#pragma unroll
+          for (int r = 0; r < R0; ++r) base[(int64_t)(j + r * R1) * elem_stride + b] = v[q * R0 + r];
+        }
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < QA; ++q) {
+        const int id = tid + q * NT;
+        const int b = id % SB;
+        if (kx0 + b < ncol) {
+#pragma unroll
+          for (int r = 0; r < R0; ++r) base[(int64_t)r * elem_stride + b] = v[q * R0 + r];
+        }
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// x-pass R2C: rows 2p and 2p+1 form z = a + i b; after the complex FFT
+// A_k = (Z_k + conj Z_{N-k})/2 and B_k = (Z_k - conj Z_{N-k})/(2i), k <= N/2.
+// ---------------------------------------------------------------------------
+template <typename T, int N>
+__global__ void __launch_bounds__(xpass_threads<N>())
+k_fft_r2c_x(const T* __restrict__ src, cpx<T>* __restrict__ H, int64_t nrows, int RS,
+            const cpx<T>* __restrict__ tw) {
+  using C = FftCfg<N>;
+  using L = XSmem<T, N>;
+  constexpr int R0 = C::R0, R1 = C::R1, E = C::E, XP = C::XP, NT = xpass_threads<N>();
+  constexpr int QA = E / R0, QB = (R1 > 1) ? E / R1 : 0;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cpx<T>* sm = reinterpret_cast<cpx<T>*>(smem_raw);
+  const int tid = threadIdx.x;
+  const int64_t row0 = (int64_t)blockIdx.x * 2 * XP;
+
+  cpx<T> v[E];
+#pragma unroll
+  for (int q = 0; q < QA; ++q) {
+    const int id = tid + q * NT;
+    const int j = id % (N / R0), p = id / (N / R0);
+    const int64_t ra = row0 + 2 * p;
+    const bool ok = ra + 1 < nrows;
+    const T* a = src + ra * N;
+#pragma unroll
+    for (int r = 0; r < R0; ++r) {
+      const int n = j + r * (N / R0);
+      v[q * R0 + r] = ok ? mk<T>(a[n], a[N + n]) : mk<T>(0, 0);
+    }
+    dft<R0, false>(v + q * R0);
+    if constexpr (R1 == 1) {
+#pragma unroll
+      for (int r = 0; r < R0; ++r) sm[L::pos(p, r)] = v[q * R0 + r];
+    } else {
+#pragma unroll
+      for (int r = 0; r < R0; ++r) sm[L::pos(p, j * R0 + r)] = v[q * R0 + r];
+    }
+  }
+  __syncthreads();
+  if constexpr (R1 > 1) {
+#pragma unroll
+    for (int q = 0; q < QB; ++q) {
+      const int id = tid + q * NT;
+      const int j = id % R0, p = id / R0;
+#pragma unroll
+      for (int r = 0; r < R1; ++r) {
+        cpx<T> x = sm[L::pos(p, j + r * R0)];
+        if (r > 0) x = cmul(x, tw[j * r]);
+        v[q * R1 + r] = x;
+      }
+      dft<R1, false>(v + q * R1);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < QB; ++q) {
+      const int id = tid + q * NT;
+      const int j = id % R0, p = id / R0;
+#pragma unroll
+      for (int r = 0; r < R1; ++r) sm[L::pos(p, j + r * R0)] = v[q * R1 + r];
+    }
+    __syncthreads();
+  }
+  // split the two real transforms, write k in [0, N/2]
+  constexpr int NK = N / 2 + 1;
+  for (int idx = tid; idx < XP * NK; idx += NT) {
+    const int p = idx / NK, k = idx - p * NK;
+    const int64_t ra = row0 + 2 * p;
+    if (ra + 1 >= nrows) continue;
+    const cpx<T> zk = sm[L::pos(p, k)];
+    const cpx<T> zn = sm[L::pos(p, (N - k) & (N - 1))];
+    const T h = (T)0.5;
+    const cpx<T> A = mk<T>(h * (zk.x + zn.x), h * (zk.y - zn.y));
+    const cpx<T> B = mk<T>(h * (zk.y + zn.y), h * (zn.x - zk.x));
+    H[ra * RS + k] = A;
+    H[(ra + 1) * RS + k] = B;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// x-pass C2R: Z_k = A_k + i B_k (k <= N/2), Z_{N-k} = conj A_k + i conj B_k;
+// DC and Nyquist use the real parts only.  Re z -> row 2p, Im z -> row 2p+1.
+// The 1/n^3 normalisation was applied with the kernel in the z-pass.
+// ---------------------------------------------------------------------------
+template <typename T, int N>
+__global__ void __launch_bounds__(xpass_threads<N>())
+k_fft_c2r_x(const cpx<T>* __restrict__ H, T* __restrict__ J, int64_t nrows, int RS,
+            const cpx<T>* __restrict__ tw, unsigned int* __restrict__ status) {
+  using C = FftCfg<N>;
+  using L = XSmem<T, N>;
+  constexpr int R0 = C::R0, R1 = C::R1, E = C::E, XP = C::XP, NT = xpass_threads<N>();
+  constexpr int QA = E / R0, QB = (R1 > 1) ? E / R1 : 0;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cpx<T>* sm = reinterpret_cast<cpx<T>*>(smem_raw);
+  const int tid = threadIdx.x;
+  const int64_t row0 = (int64_t)blockIdx.x * 2 * XP;
+
+  constexpr int NK = N / 2 + 1;
+  for (int idx = tid; idx < XP * NK; idx += NT) {
+    const int p = idx / NK, k = idx - p * NK;
+    const int64_t ra = row0 + 2 * p;
+    cpx<T> A = mk<T>(0, 0), B = mk<T>(0, 0);
+    if (ra + 1 < nrows) { A = H[ra * RS + k]; B = H[(ra + 1) * RS + k]; }
+    if (k == 0 || k == N / 2) {
+      sm[L::pos(p, k)] = mk<T>(A.x, B.x);
+    } else {
+      sm[L::pos(p, k)] = mk<T>(A.x - B.y, A.y + B.x);
+      sm[L::pos(p, N - k)] = mk<T>(A.x + B.y, B.x - A.y);
+    }
+  }
+  __syncthreads();
+
+  cpx<T> v[E];
+#pragma unroll
+  for (int q = 0; q < QA; ++q) {
+    const int id = tid + q * NT;
+    const int j = id % (N / R0), p = id / (N / R0);
+#pragma unroll
+    for (int r = 0; r < R0; ++r) v[q * R0 + r] = sm[L::pos(p, j + r * (N / R0))];
+    dft<R0, true>(v + q * R0);
+  }
+  bool bad = false;
+  if constexpr (R1 == 1) {
+#pragma unroll
+    for (int q = 0; q < QA; ++q) {
+      const int id = tid + q * NT;
+      const int p = id / (N / R0);
+      const int64_t ra = row0 + 2 * p;
+      if (ra + 1 < nrows) {
+#pragma unroll
+        for (int r = 0; r < R0; ++r) {
+          J[ra * N + r] = v[q * R0 + r].x;
+          J[(ra + 1) * N + r] = v[q * R0 + r].y;
+          bad |= !isfinite(v[q * R0 + r].x) || !isfinite(v[q * R0 + r].y);
+        }
+      }
+    }
+  } else {
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < QA; ++q) {
+      const int id = tid + q * NT;
+      const int j = id % (N / R0), p = id / (N / R0);
+#pragma unroll
+      for (int r = 0; r < R0; ++r) sm[L::pos(p, j * R0 + r)] = v[q * R0 + r];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < QB; ++q) {
+      const int id = tid + q * NT;
+      const int j = id % R0, p = id / R0;
+#pragma unroll
+      for (int r = 0; r < R1; ++r) {
+        cpx<T> x = sm[L::pos(p, j + r * R0)];
+        if (r > 0) x = cmulc(x, tw[j * r]);
+        v[q * R1 + r] = x;
+      }
+      dft<R1, true>(v + q * R1);
+      const int64_t ra = row0 + 2 * p;
+      if (ra + 1 < nrows) {
+#pragma unroll
+        for (int r = 0; r < R1; ++r) {
+          const int n = j + r * R0;
+          J[ra * N + n] = v[q * R1 + r].x;
+          J[(ra + 1) * N + n] = v[q * R1 + r].y;
+          bad |= !isfinite(v[q * R1 + r].x) || !isfinite(v[q * R1 + r].y);
+        }
+      }
+    }
+  }
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) raise_status(status, AMBER_ERR_NONFINITE);
+}
+
+// ---------------------------------------------------------------------------
+// Host launcher for one radiation field of size N.
+// ---------------------------------------------------------------------------
+struct FftProfile;  // opaque; see host runtime
+void prof_begin(FftProfile* p, int kind, cudaStream_t s);
+void prof_end(FftProfile* p, int kind, cudaStream_t s);
+
+enum ProfKind {
+  PK_R2C_X = 0, PK_FFT_Y_FWD, PK_FFT_Z_CONV, PK_FFT_Y_INV, PK_C2R_X,
+  PK_SORT_HIST, PK_SORT_PASS, PK_MASS_REDUCE, PK_THRESHOLDS, PK_SCAN_ASSIGN, PK_COUNT
+};
+
+template <typename T, int N>
+cudaError_t radiation_field_n(const T* src, T* J, cpx<T>* H, const cpx<T>* tw, double box, double l_mfp,
+                              unsigned int* status, cudaStream_t s, FftProfile* prof) {
+  using C = FftCfg<N>;
+  const int RS = N / 2 + 2;
+  const int ncol = N / 2 + 1;
+  const int64_t nrows = (int64_t)N * N;
+  const T kf = (T)(2.0 * 3.14159265358979323846 / box);
+  const T norm = (T)(1.0 / ((double)N * N * N));
+  const size_t xs = XSmem<T, N>::elems * sizeof(cpx<T>);
+  const size_t ss = StridedSmem<T, N>::elems * sizeof(cpx<T>);
+  static bool attr_done = false;  // per instantiation; device-independent attribute
+  if (!attr_done) {
+    cudaFuncSetAttribute(k_fft_r2c_x<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xs);
+    cudaFuncSetAttribute(k_fft_c2r_x<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xs);
+    cudaFuncSetAttribute(k_fft_strided<T, N, PASS_FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss);
+    cudaFuncSetAttribute(k_fft_strided<T, N, PASS_INV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss);
+    cudaFuncSetAttribute(k_fft_strided<T, N, PASS_CONV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss);
+    attr_done = true;
+  }
+  const int xgrid = (int)((nrows / 2 + C::XP - 1) / C::XP);
+  const int ntx = (ncol + C::SB - 1) / C::SB;
+  const int sgrid = N * ntx;
+
+  prof_begin(prof, PK_R2C_X, s);
+  k_fft_r2c_x<T, N><<<xgrid, xpass_threads<N>(), xs, s>>>(src, H, nrows, RS, tw);
+  prof_end(prof, PK_R2C_X, s);
+  // y-pass: lines (z, kx); element stride RS; outer (z) stride N*RS
+  prof_begin(prof, PK_FFT_Y_FWD, s);
+  k_fft_strided<T, N, PASS_FWD><<<sgrid, strided_threads<N>(), ss, s>>>(H, RS, (int64_t)N * RS, ncol, ntx, tw,
+                                                                       kf, (T)l_mfp, norm);
+  prof_end(prof, PK_FFT_Y_FWD, s);
+  // z-pass: lines (y, kx); element stride N*RS; outer (y) stride RS
+  prof_begin(prof, PK_FFT_Z_CONV, s);
+  k_fft_strided<T, N, PASS_CONV><<<sgrid, strided_threads<N>(), ss, s>>>(H, (int64_t)N * RS, RS, ncol, ntx, tw,
+                                                                        kf, (T)l_mfp, norm);
+  prof_end(prof, PK_FFT_Z_CONV, s);
+  prof_begin(prof, PK_FFT_Y_INV, s);
+  k_fft_strided<T, N, PASS_INV><<<sgrid, strided_threads<N>(), ss, s>>>(H, RS, (int64_t)N * RS, ncol, ntx, tw,
+                                                                       kf, (T)l_mfp, norm);
+  prof_end(prof, PK_FFT_Y_INV, s);
+  prof_begin(prof, PK_C2R_X, s);
+  k_fft_c2r_x<T, N><<<xgrid, xpass_threads<N>(), xs, s>>>(H, J, nrows, RS, tw, status);
+  prof_end(prof, PK_C2R_X, s);
+  return cudaGetLastError();
+}
+
+}  // namespace amber

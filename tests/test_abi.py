@@ -1,0 +1,86 @@
+"""Host-side checks of libamber (no GPU): symbols, the Weibull solve, argument errors."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def B():
+    import __graft_entry__ as g
+    g.build()
+    from paper_2109_10375_gb300 import binding
+    return binding
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "amber.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(amber_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_symbol(B):
+    names = _declared()
+    assert len(names) >= 18
+    for name in names:
+        assert hasattr(B.lib, name), name
+    assert set(names) == set(B.EXPORTED)
+
+
+def test_host_weibull_matches_table1(B):
+    with open(os.path.join(ROOT, "tests", "golden", "weibull_table1.txt")) as f:
+        rows = [l.split() for l in f if l.strip() and not l.startswith("#")]
+    for name, *v in rows:
+        z_mid, dz, Az, a_w, b_w, c_w = map(float, v)
+        a, b, c = B.history_coeffs(B.history(z_mid, dz, Az))
+        assert abs(a - a_w) <= 0.01 and abs(b - b_w) <= 0.01 and abs(c - c_w) <= 0.01, name
+
+
+@pytest.mark.parametrize("p", [(8, 4, 3), (7.5, 4, 3), (6.5, 6, 1.5), (9, 2, 5), (8, 4, 14), (8, 2, 2)])
+def test_host_history_table_matches_oracle(B, p):
+    from oracle import amber_oracle as o
+    z, x = B.history_table(B.history(*p))
+    t = o.history_table(*p)
+    np.testing.assert_allclose(z, t.z, rtol=0, atol=1e-12)
+    np.testing.assert_allclose(x, t.x, rtol=0, atol=1e-12)
+    a, b, c = B.history_coeffs(B.history(*p))
+    assert abs(a - t.a_w) < 1e-10 and abs(b - t.b_w) < 1e-10 and abs(c - t.c_w) < 1e-10
+
+
+def test_host_history_rejects_bad_arguments(B):
+    h = B.history(8, 4, 3)
+    h.x_ear, h.x_mid = 0.6, 0.5
+    out = (C.c_double * 3)()
+    assert B.lib.amber_history_coeffs(C.byref(h), out) == B.AMBER_ERR_INVALID_ARG
+    h = B.history(8, -4, 3)
+    assert B.lib.amber_history_coeffs(C.byref(h), out) == B.AMBER_ERR_INVALID_ARG
+    h = B.history(8, 4, 3, n_table=1)
+    assert B.lib.amber_history_coeffs(C.byref(h), out) == B.AMBER_ERR_INVALID_ARG
+
+
+def test_entry_points_reject_null_context(B):
+    vp = C.c_void_p
+    assert B.lib.amber_radiation_field(None, vp(16), 64, 1.0, 1.0, vp(16), None) == B.AMBER_ERR_INVALID_ARG
+    assert B.lib.amber_rank(None, vp(16), 10, vp(16), None) == B.AMBER_ERR_INVALID_ARG
+    assert B.lib.amber_sync_status(None, None) == B.AMBER_ERR_INVALID_ARG
+    assert B.status_string(B.AMBER_ERR_NONFINITE) == "non-finite intensity"
+
+
+def test_workspace_plan(B):
+    # 1024^3: half spectrum + 4 sort buffers + look-back, all allocated once
+    wb = B.workspace_bytes(1 << 30)
+    assert 20e9 < wb < 24e9
+    with pytest.raises(B.AmberError):
+        B.workspace_bytes((1 << 30) + 1)
+
+
+def test_create_without_gpu_reports_cuda_error(B):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    h = C.c_void_p()
+    assert B.lib.amber_create(C.byref(h), 0, 4096) == B.AMBER_ERR_CUDA

@@ -1,0 +1,307 @@
+"""GPU path vs the FP64 oracle, through the C ABI (needs a GB300).
+
+Tolerances (stated for the method):
+  intensity  relative L2 <= 1e-5 and max relative <= 1e-4, the max taken with
+             denominator max(|J|, 1e-3 rms(J));
+  ranking    bit-exact against a stable sort of the same float keys;
+  z_re       |dz| > 1e-3 in at most 1e-4 of the cells;
+  history    ionized-mass fraction above every table redshift within one
+             cell's mass of x(z_j).
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import amber_oracle as O
+from paper_2109_10375_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def B():
+    import __graft_entry__ as g
+    g.build()
+    from paper_2109_10375_gb300 import binding
+    return binding
+
+
+@pytest.fixture(scope="module")
+def ctx(B):
+    c = B.Context(256 ** 3)
+    yield c
+    c.close()
+
+
+def j_errors(Jg, Jo):
+    Jg = np.asarray(Jg, dtype=np.float64).reshape(-1)
+    Jo = np.asarray(Jo, dtype=np.float64).reshape(-1)
+    rel_l2 = np.linalg.norm(Jg - Jo) / np.linalg.norm(Jo)
+    den = np.maximum(np.abs(Jo), 1e-3 * np.sqrt(np.mean(Jo * Jo)))
+    return rel_l2, np.max(np.abs(Jg - Jo) / den)
+
+
+def field(n, box, kind, seed=0):
+    if kind == "recipe":
+        S, m = synth.realisation(n, box, seed)
+        return S, m
+    g = torch.Generator().manual_seed(seed)
+    S = torch.rand((n, n, n), generator=g, dtype=torch.float32)
+    m = 0.01 + 2.0 * torch.rand((n, n, n), generator=g, dtype=torch.float32)
+    return S, m
+
+
+def check_status(ctx, B):
+    st = ctx.sync_status()
+    assert st == 0, B.status_string(st)
+
+
+# ---------------------------------------------------------------------------
+# Radiation field (Sec. 3.4.1)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n", [4, 8, 16, 32, 64, 128, 256])
+@pytest.mark.parametrize("kind", ["recipe", "uniform01"])
+def test_radiation_field_fp32_vs_oracle(ctx, B, n, kind):
+    box = 100.0 * n / 64
+    l = 3.0
+    S, _ = field(n, box, kind, seed=n)
+    J = ctx.radiation_field(S.cuda(), box, l)
+    check_status(ctx, B)
+    Jo = O.radiation_field(S.double().numpy(), box, l)
+    rel_l2, max_rel = j_errors(J.cpu().numpy(), Jo)
+    assert rel_l2 <= 1e-5 and max_rel <= 1e-4, (rel_l2, max_rel)
+
+
+@pytest.mark.parametrize("n", [4, 8, 16, 32, 64, 128, 256])
+def test_radiation_field_fp64_vs_oracle(ctx, B, n):
+    box, l = 100.0 * n / 64, 2.0
+    S, _ = field(n, box, "recipe", seed=3 + n)
+    J = ctx.radiation_field(S.double().cuda(), box, l)
+    check_status(ctx, B)
+    Jo = O.radiation_field(S.double().numpy(), box, l)
+    rel_l2, max_rel = j_errors(J.cpu().numpy(), Jo)
+    assert rel_l2 <= 1e-12 and max_rel <= 1e-11, (rel_l2, max_rel)
+
+
+@pytest.mark.parametrize("mvec", [(0, 0, 1), (0, 5, 0), (3, 0, 0), (2, -7, 31), (32, 32, 32), (-17, 9, 4)])
+def test_plane_wave_eigenfunction_fp32(ctx, B, mvec):
+    n, box, l, eps = 64, 80.0, 3.0, 0.25
+    z, y, x = torch.meshgrid(*(torch.arange(n, dtype=torch.float64),) * 3, indexing="ij")
+    mz, my, mx = mvec
+    ph = 2 * math.pi * (mz * z + my * y + mx * x) / n
+    S = (1.0 + eps * torch.cos(ph)).float()
+    J = ctx.radiation_field(S.cuda(), box, l).double().cpu()
+    k = 2 * math.pi / box * math.sqrt(mz * mz + my * my + mx * mx)
+    ref = l + eps * math.atan(k * l) / k * torch.cos(ph)
+    assert torch.max(torch.abs(J - ref)).item() < 2e-6 * l
+
+
+def test_uniform_field_gives_uniform_intensity(ctx, B):
+    n, box, l = 128, 100.0, 5.0
+    J = ctx.radiation_field(torch.full((n, n, n), 1.5, device="cuda"), box, l)
+    assert torch.max(torch.abs(J - 1.5 * l)).item() < 1e-5 * 1.5 * l
+
+
+def test_radiation_field_in_place(ctx, B):
+    n, box, l = 32, 40.0, 2.0
+    S, _ = field(n, box, "recipe", seed=9)
+    d = S.cuda()
+    ctx.radiation_field(d, box, l, out=d)
+    Jo = O.radiation_field(S.double().numpy(), box, l)
+    assert j_errors(d.cpu().numpy(), Jo)[0] <= 1e-5
+
+
+# ---------------------------------------------------------------------------
+# Ranking (Sec. 3.4.2): bit-exact against a stable sort of the same keys
+# ---------------------------------------------------------------------------
+
+def _rank_cases():
+    g = np.random.default_rng(1)
+    out = []
+    for n in [1, 2, 31, 4095, 4096, 4097, 100_003, 1_000_000]:
+        out.append(("normal", g.normal(size=n).astype(np.float32)))
+    out.append(("ties", g.integers(0, 5, size=300_001).astype(np.float32)))
+    out.append(("all_equal", np.full(50_000, 3.25, np.float32)))
+    v = g.normal(size=20_000).astype(np.float32)
+    v[::7] = 0.0
+    v[::11] = -0.0
+    v[::13] = np.inf
+    v[::17] = -np.inf
+    out.append(("signed_zero_inf", v))
+    out.append(("narrow_range", (5.0 + 1e-5 * g.random(size=2_000_000)).astype(np.float32)))
+    return out
+
+
+@pytest.mark.parametrize("case", _rank_cases(), ids=lambda c: f"{c[0]}-{c[1].size}")
+def test_rank_bit_exact(ctx, B, case):
+    _, J = case
+    order = ctx.rank(torch.from_numpy(J).cuda()).cpu().numpy().astype(np.int64)
+    check_status(ctx, B)
+    expect = O.rank(J) if np.all(np.isfinite(J)) else np.argsort(-J, kind="stable")
+    np.testing.assert_array_equal(order, expect)
+
+
+def test_rank_fp64_bit_exact(ctx, B):
+    g = np.random.default_rng(4)
+    J = np.concatenate([g.normal(size=70_001), np.full(999, 0.5), [-0.0, 0.0, 1e-300, -1e-300]])
+    order = ctx.rank(torch.from_numpy(J).cuda()).cpu().numpy().astype(np.int64)
+    np.testing.assert_array_equal(order, O.rank(J))
+
+
+def test_rank_nan_latches_nonfinite(ctx, B):
+    J = torch.ones(10_000, device="cuda")
+    J[1234] = float("nan")
+    ctx.rank(J)
+    assert ctx.sync_status() & B.AMBER_ERR_NONFINITE
+    assert ctx.sync_status() == 0  # cleared by the read
+
+
+# ---------------------------------------------------------------------------
+# Abundance matching (Sec. 3.4.2)
+# ---------------------------------------------------------------------------
+
+def zre_mismatch(zg, zo):
+    d = np.abs(np.asarray(zg, np.float64).reshape(-1) - np.asarray(zo, np.float64).reshape(-1))
+    return np.mean(d > 1e-3), d.max()
+
+
+def fraction_invariant(z_re, mass, t, slack_ulps=2):
+    z_re = np.asarray(z_re, np.float64).reshape(-1)
+    mass = np.asarray(mass, np.float64).reshape(-1)
+    T = mass.sum()
+    mmax = mass.max() / T
+    # cells whose float z_re sits within a few float ulps of z_j may fall either side
+    for zj, xj in zip(t.z[::7], t.x[::7]):
+        lo = mass[z_re >= np.float64(np.float32(zj)) + slack_ulps * np.spacing(np.float32(zj))].sum() / T
+        hi = mass[z_re >= np.float64(np.float32(zj)) - slack_ulps * np.spacing(np.float32(zj))].sum() / T
+        assert lo <= xj + 1e-9 and hi >= xj - mmax - 1e-9, (zj, xj, lo, hi)
+
+
+@pytest.mark.parametrize("n", [1, 5, 4096, 4097, 123_457, 1_000_000])
+def test_assign_vs_oracle_given_order(ctx, B, n):
+    g = np.random.default_rng(n)
+    mass = g.uniform(0.01, 8.0, n).astype(np.float32)
+    order = g.permutation(n).astype(np.int32)
+    h = B.history(8.0, 4.0, 3.0)
+    F = torch.empty(n, dtype=torch.float64, device="cuda")
+    z = ctx.assign_zre(torch.from_numpy(order).cuda(), torch.from_numpy(mass).cuda(), h, F=F)
+    check_status(ctx, B)
+    t = O.history_table(8.0, 4.0, 3.0)
+    zo = O.assign_zre(order, mass.astype(np.float64), t)
+    bad, dmax = zre_mismatch(z.cpu().numpy(), zo)
+    assert bad == 0.0 and dmax < 5e-5, (bad, dmax)
+    Fo = O.cumulative_mass_fraction(order, mass.astype(np.float64))
+    np.testing.assert_allclose(F.cpu().numpy(), Fo, rtol=1e-14, atol=0)
+
+
+def test_assign_equal_mass_closed_form(ctx, B):
+    n = 300_000
+    order = np.arange(n)[::-1].copy().astype(np.int32)
+    h = B.history(7.5, 4.0, 3.0)
+    z = ctx.assign_zre(torch.from_numpy(order).cuda(), torch.ones(n, device="cuda"), h).cpu().numpy()
+    t = O.history_table(7.5, 4.0, 3.0)
+    Fn = np.arange(1, n + 1) / n
+    zo = O.assign_from_fraction(Fn, t)            # F_n = n/C exactly
+    assert np.max(np.abs(z[order] - zo)) < 5e-5
+    inside = (Fn > t.x[-1] * 1.01) & (Fn < 0.999)
+    assert np.max(np.abs(z[order][inside] - O.weibull_inverse(Fn[inside], t.a_w, t.b_w, t.c_w))) < t.z[1] - t.z[0]
+
+
+def test_assign_low_a_w_lowers_table(ctx, B):
+    n = 200_000
+    g = np.random.default_rng(8)
+    mass = g.uniform(0.5, 1.5, n).astype(np.float32)
+    order = g.permutation(n).astype(np.int32)
+    h = B.history(6.5, 6.0, 1.5)  # a_w ~ 3.2 < 5
+    z = ctx.assign_zre(torch.from_numpy(order).cuda(), torch.from_numpy(mass).cuda(), h).cpu().numpy()
+    t = O.history_table(6.5, 6.0, 1.5)
+    zo = O.assign_zre(order, mass.astype(np.float64), t)
+    bad, dmax = zre_mismatch(z, zo)
+    assert bad == 0.0 and dmax < 5e-5
+    fraction_invariant(z, mass, t)
+
+
+def test_assign_bad_mass_latches(ctx, B):
+    n = 10_000
+    mass = torch.ones(n, device="cuda")
+    mass[77] = -1.0
+    order = torch.arange(n, dtype=torch.int32, device="cuda")
+    ctx.assign_zre(order, mass, B.history(8, 4, 3))
+    assert ctx.sync_status() & B.AMBER_ERR_INVALID_MASS
+
+
+def test_device_wait_timeout_reports_status(ctx, B):
+    ctx.test_wait_timeout(2000)
+    assert ctx.sync_status() == B.AMBER_ERR_DEVICE_TIMEOUT
+    # the context stays usable
+    J = ctx.radiation_field(torch.ones((8, 8, 8), device="cuda"), 10.0, 1.0)
+    assert ctx.sync_status() == 0 and abs(J.mean().item() - 1.0) < 1e-6
+
+
+def test_host_argument_errors_enqueue_nothing(ctx, B):
+    with pytest.raises(B.AmberError) as e:
+        ctx.radiation_field(torch.ones((6, 6, 6), device="cuda"), 10.0, 1.0)
+    assert e.value.code == B.AMBER_ERR_INVALID_ARG
+    with pytest.raises(B.AmberError) as e:
+        ctx.radiation_field(torch.ones((512, 1, 1), device="cuda"), 10.0, 1.0)
+    with pytest.raises(B.AmberError) as e:
+        ctx.solve(torch.ones((8, 8, 8), device="cuda"), torch.ones((8, 8, 8), device="cuda"), 10.0, -1.0,
+                  B.history(8, 4, 3))
+    assert e.value.code == B.AMBER_ERR_INVALID_ARG
+
+
+# ---------------------------------------------------------------------------
+# Whole path
+# ---------------------------------------------------------------------------
+
+def _solve_and_compare(ctx, B, n, box, l, hist, precision=32, seed=0):
+    S, m = synth.realisation(n, box, seed)
+    h = B.history(*hist)
+    if precision == 64:
+        Sd = S.double().cuda()
+        J = torch.empty_like(Sd)
+    else:
+        Sd = S.cuda()
+        J = torch.empty_like(Sd)
+    z = ctx.solve(Sd, m.cuda(), box, l, h, J_out=J)
+    check_status(ctx, B)
+    Jo, order_o, zo = O.solve(S.double().numpy(), m.double().numpy(), box, l, *hist)
+    t = O.history_table(*hist)
+    return J.cpu().numpy(), z.cpu().numpy(), Jo, zo, m.numpy(), t
+
+
+def test_solve_64cube_fp64(ctx, B):
+    # plain method, 64^3, box 100, FP64 intensity; l = 3, history (8, 4, 3)
+    Jg, zg, Jo, zo, m, t = _solve_and_compare(ctx, B, 64, 100.0, 3.0, (8.0, 4.0, 3.0), precision=64)
+    rel_l2, max_rel = j_errors(Jg, Jo)
+    assert rel_l2 <= 1e-12 and max_rel <= 1e-11
+    bad, dmax = zre_mismatch(zg, zo)
+    assert bad <= 1e-4, (bad, dmax)
+    fraction_invariant(zg, m, t)
+
+
+def test_solve_64cube_fp32(ctx, B):
+    Jg, zg, Jo, zo, m, t = _solve_and_compare(ctx, B, 64, 100.0, 3.0, (8.0, 4.0, 3.0))
+    rel_l2, max_rel = j_errors(Jg, Jo)
+    assert rel_l2 <= 1e-5 and max_rel <= 1e-4
+    bad, dmax = zre_mismatch(zg, zo)
+    assert bad <= 1e-4, (bad, dmax)
+
+
+@pytest.mark.parametrize("l", [1.0, 3.0, 10.0])
+def test_solve_256cube_fp32(ctx, B, l):
+    # single instance 256^3, box 200, z_mid 7.5, dz 4, Az 3
+    Jg, zg, Jo, zo, m, t = _solve_and_compare(ctx, B, 256, 200.0, l, (7.5, 4.0, 3.0), seed=1)
+    rel_l2, max_rel = j_errors(Jg, Jo)
+    assert rel_l2 <= 1e-5 and max_rel <= 1e-4, (rel_l2, max_rel)
+    bad, dmax = zre_mismatch(zg, zo)
+    assert bad <= 1e-4, (bad, dmax)
+    fraction_invariant(zg, m, t)
+    # ranks bit-exact given the GPU's own keys
+    order = ctx.rank(torch.from_numpy(Jg).cuda()).cpu().numpy().astype(np.int64)
+    np.testing.assert_array_equal(order, np.argsort(-Jg.reshape(-1), kind="stable"))
+    # monotone: z non-increasing along descending J
+    assert np.all(np.diff(zg.reshape(-1)[order]) <= 0)
