@@ -1,0 +1,344 @@
+"""Benchmark of the z_re(x) path on GB300: one JSON line on rank 0.
+
+A step is one amber_solve (radiation field -> rank -> abundance matching) of
+one seeded synthetic 1024^3 realisation (box 1000 h^-1 Mpc, l_mfp 5,
+history z_mid 8, dz 4, Az 3), inputs resident in HBM.  Multi-GPU runs are
+independent replicas (one realisation per GPU, no collective on the data
+path), so value = all ranks' cells / max-over-ranks time.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl amber|reference] [--n 1024]
+
+--impl reference times the FP64 CPU oracle (the only other implementation
+of the method) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "z_re cells/s at 1024^3 (plain vs batched) at oracle tol; serving p50/p99 ms"
+HIST = (8.0, 4.0, 3.0)
+L_MFP = 5.0
+
+
+def _workload(n: int, box: float) -> dict:
+    return {"workload": f"single instance {n}^3 z_re solve (radiation field, rank, abundance match)",
+            "n": n, "cells": n ** 3, "box_mpc_h": box, "l_mfp": L_MFP,
+            "history": {"z_mid": HIST[0], "dz": HIST[1], "Az": HIST[2], "n_table": 2000},
+            "inputs": "seeded synthetic Gaussian-recipe source and mass fields (realisation r uses seed 1000+r)",
+            "l2": "inputs larger than L2 (each field 4 B/cell; 4.3 GB at 1024^3 vs 129 MB L2)",
+            "parallelism": "replicas"}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ---------------------------------------------------------------------------
+# Reference arm: the FP64 CPU oracle on bounded samples
+# ---------------------------------------------------------------------------
+
+def oracle_sample_rate(n_sample: int, box: float, min_seconds: float, max_reps: int = 50):
+    from oracle import amber_oracle as O
+    from paper_2109_10375_gb300 import synth
+    S, m = synth.realisation(n_sample, box, 0)
+    S, m = S.double().numpy(), m.double().numpy()
+    t0 = time.perf_counter()
+    reps = 0
+    while True:
+        O.solve(S, m, box, L_MFP, *HIST)
+        reps += 1
+        el = time.perf_counter() - t0
+        if el >= min_seconds or reps >= max_reps:
+            break
+    return reps * n_sample ** 3 / el, reps, el
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    n = args.n
+    box = 1000.0 * n / 1024
+    ns = args.cpu_sample_n
+    box_s = box * ns / n  # same cell size as the workload
+    from oracle import amber_oracle as O
+    from paper_2109_10375_gb300 import synth
+    S, m = synth.realisation(ns, box_s, 0)
+    S, m = S.double().numpy(), m.double().numpy()
+    for _ in range(args.warmup):
+        O.solve(S, m, box_s, L_MFP, *HIST)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        O.solve(S, m, box_s, L_MFP, *HIST)
+    el = time.perf_counter() - t0
+    value = args.steps * ns ** 3 / el
+    sample = f"{ns}^3 realisation per step (same recipe and cell size), {args.steps} steps"
+    line = {"metric": METRIC, "value": value, "unit": "cells/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": _workload(n, box), "impl": "reference",
+            "cpu_baseline": {"value": value, "unit": "cells/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "cells/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# Clocks during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.gpu), "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx = float(p[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": 0}
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# Roofline bookkeeping: algorithmic bytes per launch of each kernel
+# ---------------------------------------------------------------------------
+
+def algorithmic_bytes(n: int) -> dict:
+    C = n ** 3
+    H = 8 * n * n * (n // 2 + 1)  # half spectrum, complex64
+    return {
+        "fft_r2c_x": 4 * C + H, "fft_y_fwd": 2 * H, "fft_z_conv": 2 * H, "fft_y_inv": 2 * H,
+        "fft_c2r_x": H + 4 * C,
+        "sort_histogram": 4 * C,
+        "sort_pass": (12 + 16 + 16 + 12) * C / 4,  # mean over the 4 digit passes
+        "mass_reduce": 4 * C, "thresholds": 0, "scan_assign": 12 * C,
+    }
+
+
+def _src_hash() -> str:
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2109_10375_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def _traffic(kernel: str, n: int):
+    """DRAM bytes per launch from the committed ncu summary, if it matches the sources."""
+    p = os.path.join(ROOT, "profiles", "dram_traffic.json")
+    try:
+        d = json.load(open(p))
+    except Exception:
+        return None
+    if d.get("src_hash") != _src_hash():
+        return None
+    k = d.get("kernels", {}).get(kernel)
+    if not k:
+        return None
+    return k["bytes_per_launch"] * (n ** 3) / k["cells"]
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0}, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def run_amber(args):
+    import torch
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2109_10375_gb300 import binding as B, synth
+
+    n = args.n
+    box = 1000.0 * n / 1024
+    C = n ** 3
+    S, m = synth.realisation(n, box, rank, device="cuda")
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    h = B.history(*HIST)
+    ctx = B.Context(C, device=local)
+    z = torch.empty_like(S)
+    stream = torch.cuda.current_stream()
+
+    for _ in range(args.warmup):
+        ctx.solve(S, m, box, L_MFP, h, out=z)
+    st = ctx.sync_status()
+    if st != 0:
+        raise RuntimeError(f"device status after warm-up: {B.status_string(st)}")
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # --- device-resident timed region (kernel timing events on the same stream)
+    ctx.profile(True)
+    ctx.profile_reset()
+    clk = ClockSampler(local)
+    clk.start()
+    time.sleep(0.3)
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        ctx.solve(S, m, box, L_MFP, h, out=z)
+    e1.record(stream)
+    barrier()
+    clocks = clk.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    st = ctx.sync_status()
+    if st != 0:
+        raise RuntimeError(f"device status after timed region: {B.status_string(st)}")
+    t = torch.tensor([ms], device="cuda")
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+
+    # --- end to end through the public API with pinned host buffers
+    S_h = S.cpu().pin_memory()
+    m_h = m.cpu().pin_memory()
+    z_h = torch.empty(S.shape, dtype=torch.float32).pin_memory()
+    S_d, m_d = torch.empty_like(S), torch.empty_like(m)
+    del S, m
+    torch.cuda.empty_cache()
+    e_steps = max(1, min(args.steps, 5))
+    barrier()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    for _ in range(e_steps):
+        S_d.copy_(S_h, non_blocking=True)
+        m_d.copy_(m_h, non_blocking=True)
+        ctx.solve(S_d, m_d, box, L_MFP, h, out=z)
+        z_h.copy_(z, non_blocking=True)
+    f1.record(stream)
+    barrier()
+    e2e_ms = f0.elapsed_time(f1) / e_steps
+    t2 = torch.tensor([e2e_ms], device="cuda")
+    if dist is not None:
+        dist.all_reduce(t2, op=dist.ReduceOp.MAX)
+    e2e_ms = float(t2.item())
+
+    launches_per_step = sum(v[1] for v in prof.values()) / args.steps
+    # dominant kernel and its roofline
+    ab = algorithmic_bytes(n)
+    dom = max(prof, key=lambda k: prof[k][0])
+    dom_ms, dom_launches = prof[dom]
+    peaks, src = _peaks()
+    achieved = ab[dom] / (dom_ms / dom_launches / 1e3) / 1e9
+    kernels = {k: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps,
+                   "GBps": (ab[k] * v[1] / (v[0] / 1e3) / 1e9) if v[0] > 0 and ab[k] else None}
+               for k, v in prof.items() if v[1]}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        ns = args.cpu_sample_n
+        rate, reps, el = oracle_sample_rate(ns, box * ns / n, args.cpu_seconds)
+        cpu = {"value": rate, "unit": "cells/s", "cores": 1, "kind": "oracle",
+               "sample": f"{reps} x {ns}^3 realisation(s) of the same recipe and cell size, {el:.1f} s"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": C * ws / (ms_max / 1e3), "unit": "cells/s", "n_gpus": ws,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": _workload(n, box),
+                "e2e": {"value": C * ws / (e2e_ms / 1e3), "unit": "cells/s", "h2d_bytes_per_step": 8 * C,
+                        "d2h_bytes_per_step": 4 * C},
+                "gpu_launches": int(round(launches_per_step * args.steps)),
+                "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peaks["hbm_gbs"],
+                             "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": _traffic(dom, n),
+                             "peak_source": src,
+                             "path_frac": (112 * C / (ms_max / 1e3) / 1e9) / peaks["hbm_gbs"]},
+                "kernels": kernels,
+                "clocks": clocks,
+                "cpu_baseline": cpu}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="amber", choices=["amber", "reference"])
+    ap.add_argument("--n", type=int, default=1024)
+    ap.add_argument("--cpu-sample-n", type=int, default=128)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "amber":
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_amber(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

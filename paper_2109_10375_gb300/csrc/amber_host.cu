@@ -23,7 +23,7 @@ cudaError_t radiation_field_f64(int n, const double* src, double* J, void* H, co
 // ---------------------------------------------------------------------------
 static const char* kProfNames[PK_COUNT] = {
     "fft_r2c_x", "fft_y_fwd", "fft_z_conv", "fft_y_inv", "fft_c2r_x",
-    "sort_histogram", "sort_pass", "mass_reduce", "thresholds", "scan_assign"};
+    "sort_histogram", "sort_pass", "mass_reduce", "thresholds", "scan_assign", "scatter_back"};
 
 struct FftProfile {
   bool on = false;
@@ -150,7 +150,7 @@ static int fft_nmax(int64_t cells) {
 struct Plan {
   int n32 = 0, n64 = 0;
   int64_t cells64 = 0;
-  size_t off_spec, off_keysA, off_keysB, off_idxA, off_idxB, off_lb, off_sctrl, off_actrl, off_X, off_invdx,
+  size_t off_spec, off_keysA, off_keysB, off_idxA, off_idxB, off_massA, off_massB, off_lb, off_sctrl, off_actrl, off_X, off_invdx,
       off_state, off_status, off_tw32, off_tw64, total;
   size_t tw32_off[11] = {}, tw64_off[11] = {};
 };
@@ -175,6 +175,8 @@ static Plan make_plan(int64_t max_cells) {
   p.off_keysB = take(keyb);
   p.off_idxA = take(idxb);
   p.off_idxB = take(idxb);
+  p.off_massA = take(idxb);
+  p.off_massB = take(idxb);
   p.off_lb = take(lb);
   p.off_sctrl = take(kSortCtrlBytes);
   p.off_actrl = take(kAssignCtrlBytes);
@@ -308,6 +310,8 @@ int amber_create(amber_ctx** out, int device, int64_t max_cells) {
   c->sortw.keysB = c->ws + p.off_keysB;
   c->sortw.idxA = reinterpret_cast<uint32_t*>(c->ws + p.off_idxA);
   c->sortw.idxB = reinterpret_cast<uint32_t*>(c->ws + p.off_idxB);
+  c->sortw.massA = reinterpret_cast<float*>(c->ws + p.off_massA);
+  c->sortw.massB = reinterpret_cast<float*>(c->ws + p.off_massB);
   c->sortw.lookback = reinterpret_cast<uint32_t*>(c->ws + p.off_lb);
   c->sortw.ctrl = reinterpret_cast<uint32_t*>(c->ws + p.off_sctrl);
   c->sortw.num_sms = c->num_sms;
@@ -315,6 +319,9 @@ int amber_create(amber_ctx** out, int device, int64_t max_cells) {
   c->assw.X = reinterpret_cast<u128*>(c->ws + p.off_X);
   c->assw.inv_dx = reinterpret_cast<float*>(c->ws + p.off_invdx);
   c->assw.state = reinterpret_cast<ScanTile*>(c->ws + p.off_state);
+  // bucketed (cell, z) pairs reuse sort buffers that are free by then
+  c->assw.bcell = c->sortw.idxA;
+  c->assw.bz = reinterpret_cast<float*>(c->sortw.keysA);
   c->assw.num_sms = c->num_sms;
   // twiddles w_n^m = exp(-2 pi i m / n), FP64 on the host, rounded for FP32
   for (int l = 6, n = 64; n <= p.n32; ++l, n *= 2) {
@@ -397,7 +404,8 @@ int amber_rank(amber_ctx* c, const float* d_J, int64_t ncells, uint32_t* d_order
   DeviceGuard g(c->device);
   cudaStream_t s = (cudaStream_t)stream;
   c->last_stream = s;
-  return cuda_status(rank_impl<float>(c->sortw, d_J, ncells, d_order, c->status, s, &c->prof, kSpinLimit));
+  return cuda_status(rank_impl<float>(c->sortw, d_J, ncells, d_order, nullptr, nullptr, nullptr, c->status, s,
+                                      &c->prof, kSpinLimit));
 }
 
 int amber_rank_f64(amber_ctx* c, const double* d_J, int64_t ncells, uint32_t* d_order, void* stream) {
@@ -407,7 +415,8 @@ int amber_rank_f64(amber_ctx* c, const double* d_J, int64_t ncells, uint32_t* d_
   DeviceGuard g(c->device);
   cudaStream_t s = (cudaStream_t)stream;
   c->last_stream = s;
-  return cuda_status(rank_impl<double>(c->sortw, d_J, ncells, d_order, c->status, s, &c->prof, kSpinLimit));
+  return cuda_status(rank_impl<double>(c->sortw, d_J, ncells, d_order, nullptr, nullptr, nullptr, c->status, s,
+                                       &c->prof, kSpinLimit));
 }
 
 int amber_assign_zre(amber_ctx* c, const uint32_t* d_order, const float* d_mass, int64_t ncells,
@@ -421,8 +430,8 @@ int amber_assign_zre(amber_ctx* c, const uint32_t* d_order, const float* d_mass,
   DeviceGuard g(c->device);
   cudaStream_t s = (cudaStream_t)stream;
   c->last_stream = s;
-  return cuda_status(assign_impl(c->assw, d_order, d_mass, ncells, hc, d_zre, d_F_opt, c->status, s, &c->prof,
-                                 kSpinLimit));
+  return cuda_status(assign_impl(c->assw, d_order, d_mass, false, false, ncells, hc, d_zre, d_F_opt, c->status, s,
+                                 &c->prof, kSpinLimit));
 }
 
 static int solve_args(amber_ctx* c, const void* src, const float* mass, const amber_params_t* p, const float* zre,
@@ -449,9 +458,15 @@ int amber_solve(amber_ctx* c, const float* d_src, const float* d_mass, const amb
   float* J = d_J_opt ? d_J_opt : reinterpret_cast<float*>(c->sortw.keysB);
   cudaError_t e = radiation_field_f32(n, d_src, J, c->ws + pl.off_spec, c->ws + pl.off_tw32 + pl.tw32_off[ilog2i(n)],
                                       p->box, p->l_mfp, c->status, s, &c->prof);
-  if (e == cudaSuccess) e = rank_impl<float>(c->sortw, J, C, c->sortw.idxB, c->status, s, &c->prof, kSpinLimit);
+  // the first sort pass sums the masses into the assignment's total
+  unsigned long long* total = reinterpret_cast<unsigned long long*>(c->assw.ctrl);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->assw.ctrl, 0, kAssignCtrlBytes, s);
   if (e == cudaSuccess)
-    e = assign_impl(c->assw, c->sortw.idxB, d_mass, C, hc, d_zre, nullptr, c->status, s, &c->prof, kSpinLimit);
+    e = rank_impl<float>(c->sortw, J, C, c->sortw.idxB, d_mass, c->sortw.massB, total, c->status, s, &c->prof,
+                        kSpinLimit);
+  if (e == cudaSuccess)
+    e = assign_impl(c->assw, c->sortw.idxB, c->sortw.massB, true, true, C, hc, d_zre, nullptr, c->status, s,
+                    &c->prof, kSpinLimit);
   return cuda_status(e);
 }
 
@@ -470,9 +485,15 @@ int amber_solve_f64(amber_ctx* c, const double* d_src, const float* d_mass, cons
   double* J = d_J_opt ? d_J_opt : reinterpret_cast<double*>(c->sortw.keysB);
   cudaError_t e = radiation_field_f64(n, d_src, J, c->ws + pl.off_spec, c->ws + pl.off_tw64 + pl.tw64_off[ilog2i(n)],
                                       p->box, p->l_mfp, c->status, s, &c->prof);
-  if (e == cudaSuccess) e = rank_impl<double>(c->sortw, J, C, c->sortw.idxB, c->status, s, &c->prof, kSpinLimit);
+  // the first sort pass sums the masses into the assignment's total
+  unsigned long long* total = reinterpret_cast<unsigned long long*>(c->assw.ctrl);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->assw.ctrl, 0, kAssignCtrlBytes, s);
   if (e == cudaSuccess)
-    e = assign_impl(c->assw, c->sortw.idxB, d_mass, C, hc, d_zre, nullptr, c->status, s, &c->prof, kSpinLimit);
+    e = rank_impl<double>(c->sortw, J, C, c->sortw.idxB, d_mass, c->sortw.massB, total, c->status, s, &c->prof,
+                        kSpinLimit);
+  if (e == cudaSuccess)
+    e = assign_impl(c->assw, c->sortw.idxB, c->sortw.massB, true, true, C, hc, d_zre, nullptr, c->status, s,
+                    &c->prof, kSpinLimit);
   return cuda_status(e);
 }
 

@@ -5,15 +5,15 @@
 
 #include "common.cuh"
 #include "fft.cuh"  // FftProfile, prof_begin/prof_end, ProfKind
+#include "fixed128.cuh"
 
 namespace amber {
-
-typedef unsigned __int128 u128;
 
 constexpr int kScanThreads = 256;
 constexpr int kScanItems = 16;
 constexpr int kScanTile = kScanThreads * kScanItems;
 constexpr int kMaxTable = 1 << 16;
+constexpr int kMaxBuckets = 256;
 
 // Per-tile look-back record: flag (0 none, 1 aggregate, 2 inclusive) and the
 // two 128-bit values; the flag is released after the value is written.
@@ -23,14 +23,17 @@ struct __align__(16) ScanTile {
   unsigned long long agg_lo, agg_hi, inc_lo, inc_hi;
 };
 
-// ctrl: total mass (2 x u64) then the tile ticket (u32), zeroed per call
-constexpr size_t kAssignCtrlBytes = 256;
+// ctrl: total mass (2 x u64) at 0, tile ticket (u32) at 16, bucket fill
+// counters (kMaxBuckets x u32) at 64; zeroed per call
+constexpr size_t kAssignCtrlBytes = 64 + kMaxBuckets * 4;
 
 struct AssignWork {
   unsigned char* ctrl;
-  u128* X;        // [kMaxTable] thresholds
-  float* inv_dx;  // [kMaxTable]
+  u128* X;         // [kMaxTable] thresholds
+  float* inv_dx;   // [kMaxTable]
   ScanTile* state;
+  uint32_t* bcell;  // bucketed (cell, z) pairs, n each
+  float* bz;
   int num_sms;
 };
 
@@ -40,8 +43,34 @@ struct HistoryCoeffs {
   int n_table;
 };
 
-cudaError_t assign_impl(const AssignWork& w, const uint32_t* order, const float* mass, int64_t n,
-                        const HistoryCoeffs& hc, float* zre, double* F, unsigned int* status, cudaStream_t s,
-                        FftProfile* prof, unsigned int spin_limit);
+struct ScanArgs {
+  const uint32_t* order;
+  const float* mass;  // cell order (gathered through order) or rank order
+  int64_t n;
+  const unsigned long long* total;
+  const u128* X;
+  const float* inv_dx;
+  int n_table;
+  float z_lo, z_hi, dzt;
+  double* F;
+  ScanTile* state;
+  uint32_t* ticket;
+  uint32_t* fill;
+  int nbuckets;
+  uint32_t bucket_w;
+  uint32_t* bcell;
+  float* bz;
+  unsigned int* status;
+  unsigned int spin_limit;
+};
+
+void bucket_plan(int64_t n, int* nbuckets, int64_t* width);
+
+// mass_in_rank_order: mass[n] belongs to rank n (sort payload) instead of to
+// cell n.  total_ready: the 128-bit mass total in w.ctrl was already summed
+// (by the first sort pass) and must be kept.
+cudaError_t assign_impl(const AssignWork& w, const uint32_t* order, const float* mass, bool mass_in_rank_order,
+                        bool total_ready, int64_t n, const HistoryCoeffs& hc, float* zre, double* F,
+                        unsigned int* status, cudaStream_t s, FftProfile* prof, unsigned int spin_limit);
 
 }  // namespace amber

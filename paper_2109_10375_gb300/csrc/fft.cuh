@@ -395,7 +395,7 @@ void prof_end(FftProfile* p, int kind, cudaStream_t s);
 
 enum ProfKind {
   PK_R2C_X = 0, PK_FFT_Y_FWD, PK_FFT_Z_CONV, PK_FFT_Y_INV, PK_C2R_X,
-  PK_SORT_HIST, PK_SORT_PASS, PK_MASS_REDUCE, PK_THRESHOLDS, PK_SCAN_ASSIGN, PK_COUNT
+  PK_SORT_HIST, PK_SORT_PASS, PK_MASS_REDUCE, PK_THRESHOLDS, PK_SCAN_ASSIGN, PK_SCATTER_BACK, PK_COUNT
 };
 
 template <typename T, int N>

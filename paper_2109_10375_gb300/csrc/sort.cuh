@@ -28,17 +28,43 @@ struct SortWork {
   void* keysB;
   uint32_t* idxA;
   uint32_t* idxB;
+  float* massA;        // mass payload ping-pong (whole-path variant)
+  float* massB;
   uint32_t* lookback;  // two regions of sort_tiles(max) * 256 words
   uint32_t* ctrl;      // kSortCtrlBytes
   int num_sms;
 };
 
-size_t sort_pass_smem(int key_bytes);
+// Arguments of one digit pass (see k_sort_pass).
+struct PassArgs {
+  const void* J;           // FIRST: intensities (float or double)
+  const void* kin;         // !FIRST: keys
+  const uint32_t* vin;     // !FIRST: cell indices
+  const float* min;        // MASS: masses (cell order if FIRST, else ping-pong)
+  void* kout;              // !LAST
+  uint32_t* vout;
+  float* mout;             // MASS
+  int64_t n;
+  int shift;
+  const uint32_t* bin_off;
+  uint32_t* lb;
+  uint32_t* lb_next;
+  uint32_t* ticket;
+  unsigned long long* mass_total;  // FIRST && MASS: 128-bit sum (lo, hi)
+  unsigned int* status;
+  unsigned int spin_limit;
+};
+
+size_t sort_pass_smem(int key_bytes, bool mass);
 int64_t sort_tiles(int64_t n);
 
+// Stable descending rank of J into order.  With mass_in != NULL the masses
+// ride along as a payload: mass_out receives them in rank order and
+// mass_total (zeroed by the caller) their exact 128-bit sum.
 template <typename SRC>
-cudaError_t rank_impl(const SortWork& w, const SRC* J, int64_t n, uint32_t* order, unsigned int* status,
-                      cudaStream_t s, FftProfile* prof, unsigned int spin_limit);
+cudaError_t rank_impl(const SortWork& w, const SRC* J, int64_t n, uint32_t* order, const float* mass_in,
+                      float* mass_out, unsigned long long* mass_total, unsigned int* status, cudaStream_t s,
+                      FftProfile* prof, unsigned int spin_limit);
 
 cudaError_t wait_timeout_test(uint32_t* zero_word, unsigned int* status, unsigned int spin_limit, cudaStream_t s);
 
