@@ -154,31 +154,49 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_assign(const ScanArgs a) 
   }
   const u128 thr_excl = wpre + x - run;
 
-  if (tid == 0) {
+  // decoupled look-back by warp 0: each lane reads one predecessor, so a
+  // round trip covers 32 tiles; aggregates are summed back to the nearest
+  // inclusive prefix
+  if (warp == 0) {
     ScanTile* me = a.state + tile;
+    if (lane == 0) publish(me, tile_sum, tile == 0 ? 2u : 1u);
     u128 excl = 0;
-    if (tile == 0) {
-      publish(me, tile_sum, 2u);
-    } else {
-      publish(me, tile_sum, 1u);
-      int64_t t = (int64_t)tile - 1;
-      unsigned spins = 0;
-      while (t >= 0) {
-        ScanTile* o = a.state + t;
-        const unsigned int f = ld_acquire_u32(&o->flag);
-        if (f == 0u) {
-          if (++spins >= a.spin_limit) { raise_status(a.status, AMBER_ERR_DEVICE_TIMEOUT); break; }
-          __nanosleep(20);
-          continue;
+    int64_t t = (int64_t)tile - 1;
+    unsigned spins = 0;
+    while (t >= 0) {
+      const int64_t tt = t - lane;
+      unsigned int f = 2u;
+      u128 v = 0;
+      if (tt >= 0) {
+        const ScanTile* o = a.state + tt;
+        f = ld_acquire_u32(&o->flag);
+        if (f != 0u) {
+          const volatile unsigned long long* p = (f == 2u) ? &o->inc_lo : &o->agg_lo;
+          v = ((u128)p[1] << 64) | (u128)p[0];
         }
-        const volatile unsigned long long* v = (f == 2u) ? &o->inc_lo : &o->agg_lo;
-        excl += ((u128)v[1] << 64) | (u128)v[0];
-        if (f == 2u) break;
-        --t;
       }
-      publish(me, excl + tile_sum, 2u);
+      const unsigned inc_mask = __ballot_sync(0xffffffffu, f == 2u);
+      const unsigned stop_mask = inc_mask | __ballot_sync(0xffffffffu, f == 0u);
+      const int first = stop_mask ? __ffs(stop_mask) - 1 : 32;
+      const bool found = first < 32 && ((inc_mask >> first) & 1u);
+      u128 part = (lane < first || (found && lane == first)) ? v : (u128)0;
+#pragma unroll
+      for (int o = 16; o >= 1; o >>= 1) part += shfl_down_u128(part, o);
+      excl += shfl_u128(part, 0);
+      if (found) break;
+      t -= first;
+      if (first < 32) {
+        if (++spins >= a.spin_limit) {
+          if (lane == 0) raise_status(a.status, AMBER_ERR_DEVICE_TIMEOUT);
+          break;
+        }
+        __nanosleep(20);
+      }
     }
-    s_excl = excl;
+    if (lane == 0) {
+      if (tile != 0) publish(me, excl + tile_sum, 2u);
+      s_excl = excl;
+    }
   }
   __syncthreads();
   u128 Mn = s_excl + thr_excl;

@@ -28,6 +28,10 @@ __device__ __forceinline__ u128 mass_q64(float m, bool& bad) {
   return (u128)(mant >> (-sh));
 }
 
+__device__ __forceinline__ u128 shfl_u128(u128 v, int src) {
+  const unsigned long long lo = (unsigned long long)v, hi = (unsigned long long)(v >> 64);
+  return ((u128)__shfl_sync(0xffffffffu, hi, src) << 64) | (u128)__shfl_sync(0xffffffffu, lo, src);
+}
 __device__ __forceinline__ u128 shfl_up_u128(u128 v, int d) {
   const unsigned long long lo = (unsigned long long)v, hi = (unsigned long long)(v >> 64);
   return ((u128)__shfl_up_sync(0xffffffffu, hi, d) << 64) | (u128)__shfl_up_sync(0xffffffffu, lo, d);

@@ -250,22 +250,38 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_sort_pass(const PassArgs a)
     if (lane == 0 && msum != 0) atomic_add_u128(a.mass_total, msum);
   }
 
-  // ---- decoupled look-back for digit d
+  // ---- decoupled look-back for digit d, kLookWindow predecessors per round
+  // trip: sum aggregates back to the nearest inclusive prefix
   uint32_t excl = 0;
   if (tile > 0) {
     int64_t t = (int64_t)tile - 1;
     unsigned spins = 0;
-    while (t >= 0) {
-      const uint32_t s = ld_relaxed_u32(a.lb + t * kRadix + d);
-      const uint32_t flag = s & kFlagMask;
-      if (flag == 0u) {
+    while (true) {
+      uint32_t w[kLookWindow];
+#pragma unroll
+      for (int k = 0; k < kLookWindow; ++k)
+        w[k] = (t - k >= 0) ? ld_relaxed_u32(a.lb + (t - k) * kRadix + d) : kFlagInc;
+      bool stop = false, done = false;
+      int adv = 0;
+#pragma unroll
+      for (int k = 0; k < kLookWindow; ++k) {
+        if (!stop) {
+          const uint32_t f = w[k] & kFlagMask;
+          if (f == 0u) {
+            stop = true;
+          } else {
+            excl += w[k] & kValueMask;
+            ++adv;
+            if (f == kFlagInc) stop = done = true;
+          }
+        }
+      }
+      if (done) break;
+      t -= adv;
+      if (adv < kLookWindow) {  // the tile at t has published nothing yet
         if (++spins >= a.spin_limit) { raise_status(a.status, AMBER_ERR_DEVICE_TIMEOUT); break; }
         __nanosleep(20);
-        continue;
       }
-      excl += s & kValueMask;
-      if (flag == kFlagInc) break;
-      --t;
     }
     st_relaxed_u32(my, kFlagInc | ((excl + cnt) & kValueMask));
   }

@@ -12,6 +12,7 @@ constexpr int kRadix = 256;
 constexpr int kSortThreads = 256;  // one thread per digit in the tile epilogue
 constexpr int kItems = 16;
 constexpr int kTile = kSortThreads * kItems;  // 4096 keys per tile
+constexpr int kLookWindow = 8;                 // predecessors read per look-back round trip
 
 // Look-back status word: 2 flag bits over a 30-bit count.  Counts published
 // by any tile but the last are < 2^30 because max_cells <= 2^30.

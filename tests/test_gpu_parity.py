@@ -1,11 +1,14 @@
 """GPU path vs the FP64 oracle, through the C ABI (needs a GB300).
 
 Tolerances (stated for the method):
-  intensity  relative L2 <= 1e-5 and max relative <= 1e-4.  FP32 transform
-             error is absolute, about eps_f32 sqrt(log2 C) rms(J) per cell
-             (measured ~2e-7 rms(J)), so the max relative error is taken with
-             denominator max(|J|, 1e-2 rms(J)), which holds every cell to
-             |dJ| <= 1e-6 rms(J) or 1e-4 |J|;
+  intensity  relative L2 <= 1e-5 and max relative <= 1e-4.  The FP32
+             transform's error is absolute and white: per cell about
+             u sqrt(log2 C) rms(J) (u = 2^-24; measured 2.4e-7 rms(J)), so its
+             largest value over C cells is ~sqrt(2 ln C) times that, 1.7e-6
+             rms(J) at 256^3 and 2.1e-6 at 1024^3.  The max relative error is
+             therefore taken with denominator max(|J|, 5e-2 rms(J)) (a 2.4x
+             margin over that extreme), which still holds every cell to
+             |dJ| <= 5e-6 rms(J) or 1e-4 |J|;
   ranking    bit-exact against a stable sort of the same float keys;
   z_re       |dz| > 1e-3 in at most 1e-4 of the cells;
   history    ionized-mass fraction above every table redshift within one
@@ -43,7 +46,7 @@ def j_errors(Jg, Jo):
     Jo = np.asarray(Jo, dtype=np.float64).reshape(-1)
     rel_l2 = np.linalg.norm(Jg - Jo) / np.linalg.norm(Jo)
     rms = np.sqrt(np.mean(Jo * Jo))
-    den = np.maximum(np.abs(Jo), 1e-2 * rms)
+    den = np.maximum(np.abs(Jo), 5e-2 * rms)
     return rel_l2, np.max(np.abs(Jg - Jo) / den)
 
 
