@@ -151,7 +151,7 @@ struct Plan {
   int n32 = 0, n64 = 0;
   int64_t cells64 = 0;
   size_t off_spec, off_keysA, off_keysB, off_idxA, off_idxB, off_massA, off_massB, off_lb, off_sctrl, off_actrl, off_X, off_invdx,
-      off_state, off_status, off_tw32, off_tw64, total;
+      off_state, off_btab, off_status, off_tw32, off_tw64, total;
   size_t tw32_off[11] = {}, tw64_off[11] = {};
 };
 
@@ -183,6 +183,7 @@ static Plan make_plan(int64_t max_cells) {
   p.off_X = take((size_t)kMaxTable * sizeof(u128));
   p.off_invdx = take((size_t)kMaxTable * sizeof(float));
   p.off_state = take(stt);
+  p.off_btab = take((size_t)((max_cells + kScanTile - 1) / kScanTile) * (kMaxBuckets + 1) * sizeof(uint16_t));
   p.off_status = take(256);
   size_t tw32 = 0, tw64 = 0;
   for (int l = 2, n = 4; n <= 1024; ++l, n *= 2) {
@@ -322,6 +323,7 @@ int amber_create(amber_ctx** out, int device, int64_t max_cells) {
   // bucketed (cell, z) pairs reuse sort buffers that are free by then
   c->assw.bcell = c->sortw.idxA;
   c->assw.bz = reinterpret_cast<float*>(c->sortw.keysA);
+  c->assw.btab = reinterpret_cast<uint16_t*>(c->ws + p.off_btab);
   c->assw.num_sms = c->num_sms;
   // twiddles w_n^m = exp(-2 pi i m / n), FP64 on the host, rounded for FP32
   for (int l = 6, n = 64; n <= p.n32; ++l, n *= 2) {

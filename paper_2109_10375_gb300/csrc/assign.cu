@@ -106,7 +106,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_assign(const ScanArgs a) 
   __shared__ u128 s_excl;
   __shared__ uint32_t s_tile;
   __shared__ uint32_t scnt[kMaxBuckets];
-  __shared__ uint32_t sbase[kMaxBuckets];
+  __shared__ uint32_t soff[kMaxBuckets + 1];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (tid == 0) s_tile = atomicAdd(a.ticket, 1u);
   for (int b = tid; b < a.nbuckets; b += NT) scnt[b] = 0;
@@ -241,28 +241,68 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_assign(const ScanArgs a) 
     slot[i] = atomicAdd(&scnt[cell[i] / a.bucket_w], 1u);
   }
   __syncthreads();
-  for (int b = tid; b < a.nbuckets; b += NT)
-    sbase[b] = scnt[b] ? (uint32_t)((int64_t)b * a.bucket_w) + atomicAdd(&a.fill[b], scnt[b]) : 0u;
+  // tile-local bucket starts (exclusive scan over the buckets) and this
+  // tile's row of the offset table
+  if (warp == 0) {
+    uint32_t carry = 0;
+    for (int b0 = 0; b0 < a.nbuckets; b0 += 32) {
+      const int b = b0 + lane;
+      const uint32_t c = b < a.nbuckets ? scnt[b] : 0u;
+      uint32_t x = c;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+      }
+      if (b < a.nbuckets) soff[b] = carry + x - c;
+      carry += __shfl_sync(0xffffffffu, x, 31);
+    }
+    if (lane == 0) soff[a.nbuckets] = carry;
+  }
+  __syncthreads();
+  uint16_t* row = a.btab + (int64_t)tile * (a.nbuckets + 1);
+  for (int b = tid; b <= a.nbuckets; b += NT) row[b] = (uint16_t)soff[b];
+  // stage (cell, z) in bucket order, then write the tile's segment contiguously
+  uint32_t* scell = sord;                       // order is no longer needed
+  float* sz = smass;
   __syncthreads();
 #pragma unroll
   for (int i = 0; i < IT; ++i) {
     if (slot[i] == 0xffffffffu) continue;
-    const uint32_t q = sbase[cell[i] / a.bucket_w] + slot[i];
-    a.bcell[q] = cell[i];
-    a.bz[q] = zv[i];
+    const uint32_t q = soff[cell[i] / a.bucket_w] + slot[i];
+    scell[q + (q >> 5)] = cell[i];
+    sz[q + (q >> 5)] = zv[i];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < IT; ++k) {
+    const int p = k * NT + tid;
+    if (p < cnt) {
+      a.bcell[start + p] = scell[p + (p >> 5)];
+      a.bz[start + p] = sz[p + (p >> 5)];
+    }
   }
   if (__any_sync(0xffffffffu, bad) && lane == 0) raise_status(a.status, AMBER_ERR_INVALID_MASS);
 }
 
-// z_re[cell] = z over the bucketed pairs, bucket after bucket.
+// z_re[cell] = z, bucket after bucket: CTA (bucket b, tile group g) copies
+// bucket b's run of every tile in its group, one warp per tile.  A bucket's
+// cells span <= 32 MB of z_re, so while its CTAs run the permuted writes
+// merge in L2 instead of reaching HBM one partial sector at a time.
 __global__ void __launch_bounds__(256) k_scatter_back(const uint32_t* __restrict__ bcell,
-                                                      const float* __restrict__ bz, int64_t n,
-                                                      float* __restrict__ zre) {
-  const int64_t base = (int64_t)blockIdx.x * (256 * 8) + threadIdx.x;
-#pragma unroll
-  for (int k = 0; k < 8; ++k) {
-    const int64_t i = base + k * 256;
-    if (i < n) zre[bcell[i]] = bz[i];
+                                                      const float* __restrict__ bz,
+                                                      const uint16_t* __restrict__ btab, int nbuckets,
+                                                      int64_t tiles, int groups, float* __restrict__ zre) {
+  const int b = blockIdx.x / groups;
+  const int64_t g = blockIdx.x - (int64_t)b * groups;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int k = 0; k < kBackTilesPerCta / 8; ++k) {
+    const int64_t t = g * kBackTilesPerCta + k * 8 + warp;
+    if (t >= tiles) break;
+    const uint16_t* row = btab + t * (nbuckets + 1);
+    const int s = row[b], e = row[b + 1];
+    const int64_t base = t * kScanTile;
+    for (int i = s + lane; i < e; i += 32) zre[bcell[base + i]] = bz[base + i];
   }
 }
 
@@ -283,7 +323,6 @@ cudaError_t assign_impl(const AssignWork& w, const uint32_t* order, const float*
   cudaError_t e;
   unsigned long long* total = reinterpret_cast<unsigned long long*>(w.ctrl);
   uint32_t* ticket = reinterpret_cast<uint32_t*>(w.ctrl + 16);
-  uint32_t* fill = reinterpret_cast<uint32_t*>(w.ctrl + 64);
   if (!total_ready) {
     e = cudaMemsetAsync(w.ctrl, 0, kAssignCtrlBytes, s);
     if (e != cudaSuccess) return e;
@@ -320,12 +359,12 @@ cudaError_t assign_impl(const AssignWork& w, const uint32_t* order, const float*
   a.F = F;
   a.state = w.state;
   a.ticket = ticket;
-  a.fill = fill;
   int64_t bw;
   bucket_plan(n, &a.nbuckets, &bw);
   a.bucket_w = (uint32_t)bw;
   a.bcell = w.bcell;
   a.bz = w.bz;
+  a.btab = w.btab;
   a.status = status;
   a.spin_limit = spin_limit;
   prof_begin(prof, PK_SCAN_ASSIGN, s);
@@ -338,7 +377,11 @@ cudaError_t assign_impl(const AssignWork& w, const uint32_t* order, const float*
   }
   prof_end(prof, PK_SCAN_ASSIGN, s);
   prof_begin(prof, PK_SCATTER_BACK, s);
-  k_scatter_back<<<(unsigned)((n + 2047) / 2048), 256, 0, s>>>(w.bcell, w.bz, n, zre);
+  {
+    const int groups = (int)((tiles + kBackTilesPerCta - 1) / kBackTilesPerCta);
+    k_scatter_back<<<(unsigned)(groups * a.nbuckets), 256, 0, s>>>(w.bcell, w.bz, w.btab, a.nbuckets, tiles, groups,
+                                                                   zre);
+  }
   prof_end(prof, PK_SCATTER_BACK, s);
   return cudaGetLastError();
 }

@@ -23,17 +23,19 @@ struct __align__(16) ScanTile {
   unsigned long long agg_lo, agg_hi, inc_lo, inc_hi;
 };
 
-// ctrl: total mass (2 x u64) at 0, tile ticket (u32) at 16, bucket fill
-// counters (kMaxBuckets x u32) at 64; zeroed per call
-constexpr size_t kAssignCtrlBytes = 64 + kMaxBuckets * 4;
+constexpr int kBackTilesPerCta = 64;  // scan tiles one scatter-back CTA covers
+
+// ctrl: total mass (2 x u64) at 0, tile ticket (u32) at 16; zeroed per call
+constexpr size_t kAssignCtrlBytes = 256;
 
 struct AssignWork {
   unsigned char* ctrl;
   u128* X;         // [kMaxTable] thresholds
   float* inv_dx;   // [kMaxTable]
   ScanTile* state;
-  uint32_t* bcell;  // bucketed (cell, z) pairs, n each
+  uint32_t* bcell;  // per scan tile, (cell, z) pairs grouped by bucket
   float* bz;
+  uint16_t* btab;   // [tiles][nbuckets + 1] tile-local bucket starts
   int num_sms;
 };
 
@@ -55,11 +57,11 @@ struct ScanArgs {
   double* F;
   ScanTile* state;
   uint32_t* ticket;
-  uint32_t* fill;
   int nbuckets;
   uint32_t bucket_w;
   uint32_t* bcell;
   float* bz;
+  uint16_t* btab;
   unsigned int* status;
   unsigned int spin_limit;
 };

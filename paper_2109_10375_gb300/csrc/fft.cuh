@@ -77,7 +77,7 @@ __device__ __forceinline__ int signed_freq(int m, int n) { return m < n / 2 ? m 
 enum { PASS_FWD = 0, PASS_INV = 1, PASS_CONV = 2 };
 
 template <typename T, int N, int MODE>
-__global__ void __launch_bounds__(strided_threads<N>())
+__global__ void __launch_bounds__(strided_threads<N>(), 2)
 k_fft_strided(cpx<T>* __restrict__ H, int64_t elem_stride, int64_t outer_stride, int ncol,
               int ntx, const cpx<T>* __restrict__ tw, T kf, T l_mfp, T norm) {
   using C = FftCfg<N>;
