@@ -154,15 +154,20 @@ class ClockSampler:
 # Roofline bookkeeping: algorithmic bytes per launch of each kernel
 # ---------------------------------------------------------------------------
 
-def algorithmic_bytes(n: int) -> dict:
+def algorithmic_bytes(n: int, sort_passes: int) -> dict:
+    """Algorithmic HBM bytes per step of each kernel kind (the design's byte model)."""
     C = n ** 3
     H = 8 * n * n * (n // 2 + 1)  # half spectrum, complex64
+    if sort_passes == 1:
+        sort = 16 * C                       # J 4 + mass 4 in, order 4 + mass 4 out
+    else:
+        sort = (20 + 24 * (sort_passes - 2) + 20) * C  # first / middle / last pass
     return {
         "fft_r2c_x": 4 * C + H, "fft_y_fwd": 2 * H, "fft_z_conv": 2 * H, "fft_y_inv": 2 * H,
         "fft_c2r_x": H + 4 * C,
-        "sort_histogram": 4 * C,
-        "sort_pass": (12 + 16 + 16 + 12) * C / 4,  # mean over the 4 digit passes
-        "mass_reduce": 4 * C, "thresholds": 0, "scan_assign": 12 * C,
+        "sort_histogram": 8 * C,            # key range + digit histogram, 4 B/cell each
+        "sort_pass": sort,
+        "mass_reduce": 4 * C, "thresholds": 0, "scan_assign": 16 * C, "scatter_back": 12 * C,
     }
 
 
@@ -283,16 +288,20 @@ def run_amber(args):
     e2e_ms = float(t2.item())
 
     launches_per_step = sum(v[1] for v in prof.values()) / args.steps
-    # dominant kernel and its roofline
-    ab = algorithmic_bytes(n)
-    dom = max(prof, key=lambda k: prof[k][0])
-    dom_ms, dom_launches = prof[dom]
+    passes = ctx.sort_passes()
+    ab = algorithmic_bytes(n, passes)
+    kernels = {}
+    for k, (ms_k, cnt) in prof.items():
+        if cnt == 0:
+            continue
+        ms_step = ms_k / args.steps
+        kernels[k] = {"ms_per_step": ms_step, "launches_per_step": cnt / args.steps,
+                      "algorithmic_bytes_per_step": ab.get(k, 0),
+                      "GBps": (ab.get(k, 0) / (ms_step / 1e3) / 1e9) if ms_step > 0 else None}
+    dom = max(kernels, key=lambda k: kernels[k]["ms_per_step"])
     peaks, src = _peaks()
-    achieved = ab[dom] / (dom_ms / dom_launches / 1e3) / 1e9
-    kernels = {k: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps,
-                   "GBps": (ab[k] * v[1] / (v[0] / 1e3) / 1e9) if v[0] > 0 and ab[k] else None}
-               for k, v in prof.items() if v[1]}
-
+    achieved = kernels[dom]["GBps"]
+    path_bytes = sum(ab.get(k, 0) for k in kernels)
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         ns = args.cpu_sample_n
@@ -311,7 +320,10 @@ def run_amber(args):
                 "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peaks["hbm_gbs"],
                              "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": _traffic(dom, n),
                              "peak_source": src,
-                             "path_frac": (112 * C / (ms_max / 1e3) / 1e9) / peaks["hbm_gbs"]},
+                             "path_bytes_per_cell": path_bytes / C,
+                             "path_frac": (path_bytes / (ms_max / 1e3) / 1e9) / peaks["hbm_gbs"],
+                             "path_frac_112B_model": (112 * C / (ms_max / 1e3) / 1e9) / peaks["hbm_gbs"],
+                             "sort_passes": passes},
                 "kernels": kernels,
                 "clocks": clocks,
                 "cpu_baseline": cpu}

@@ -160,6 +160,11 @@ int amber_profile_reset(amber_ctx *ctx);
 int amber_profile_kinds(void);
 int amber_profile_read(amber_ctx *ctx, int kind, const char **name, double *total_ms, int64_t *launches);
 
+/* Digit passes the last ranking needed (diagnostic; synchronises the
+ * context's last stream).  The sort runs on key - min(key) with 9-bit digits,
+ * so an intensity field spanning few octaves needs 3 passes, at most 4. */
+int amber_sort_passes(amber_ctx *ctx, int *out_passes);
+
 /* Test hook for failure detection: runs the production lookback wait on a
  * status array nothing ever publishes, with `spin_limit` iterations, and
  * latches AMBER_ERR_DEVICE_TIMEOUT.  No fault, no trap: the kernel returns. */

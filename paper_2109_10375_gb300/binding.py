@@ -28,7 +28,7 @@ EXPORTED = [
     "amber_workspace_bytes", "amber_radiation_field", "amber_radiation_field_f64", "amber_rank",
     "amber_rank_f64", "amber_assign_zre", "amber_solve", "amber_solve_f64", "amber_sync_status",
     "amber_status_string", "amber_profile_enable", "amber_profile_reset", "amber_profile_kinds",
-    "amber_profile_read", "amber_test_wait_timeout",
+    "amber_profile_read", "amber_sort_passes", "amber_test_wait_timeout",
 ]
 
 
@@ -75,6 +75,7 @@ def _load():
         "amber_profile_reset": (i32, [vp]),
         "amber_profile_kinds": (i32, []),
         "amber_profile_read": (i32, [vp, i32, C.POINTER(C.c_char_p), C.POINTER(dbl), C.POINTER(i64)]),
+        "amber_sort_passes": (i32, [vp, C.POINTER(i32)]),
         "amber_test_wait_timeout": (i32, [vp, C.c_uint, vp]),
     }
     for name, (res, args) in sig.items():
@@ -221,6 +222,11 @@ class Context:
             _check(lib.amber_profile_read(self._h, k, C.byref(name), C.byref(ms), C.byref(cnt)), "amber_profile_read")
             out[name.value.decode()] = (ms.value, cnt.value)
         return out
+
+    def sort_passes(self) -> int:
+        out = C.c_int()
+        _check(lib.amber_sort_passes(self._h, C.byref(out)), "amber_sort_passes")
+        return out.value
 
     def test_wait_timeout(self, spin_limit: int, stream=None):
         _check(lib.amber_test_wait_timeout(self._h, spin_limit, _stream(stream)), "amber_test_wait_timeout")

@@ -166,7 +166,7 @@ static Plan make_plan(int64_t max_cells) {
   const size_t spec = std::max(spec_bytes(p.n32, 8), spec_bytes(p.n64, 16));
   const size_t keyb = std::max((size_t)max_cells * 4, (size_t)p.cells64 * 8);
   const size_t idxb = (size_t)max_cells * 4;
-  const size_t lb = 2 * (size_t)sort_tiles(max_cells) * kRadix * 4;
+  const size_t lb = 2 * sort_lookback_words(max_cells) * 4;
   const size_t stt = (size_t)((max_cells + kScanTile - 1) / kScanTile) * sizeof(ScanTile);
   size_t o = 0;
   auto take = [&](size_t bytes) { const size_t at = o; o += align256(bytes); return at; };
@@ -178,7 +178,7 @@ static Plan make_plan(int64_t max_cells) {
   p.off_massA = take(idxb);
   p.off_massB = take(idxb);
   p.off_lb = take(lb);
-  p.off_sctrl = take(kSortCtrlBytes);
+  p.off_sctrl = take(sizeof(SortCtrl));
   p.off_actrl = take(kAssignCtrlBytes);
   p.off_X = take((size_t)kMaxTable * sizeof(u128));
   p.off_invdx = take((size_t)kMaxTable * sizeof(float));
@@ -314,7 +314,8 @@ int amber_create(amber_ctx** out, int device, int64_t max_cells) {
   c->sortw.massA = reinterpret_cast<float*>(c->ws + p.off_massA);
   c->sortw.massB = reinterpret_cast<float*>(c->ws + p.off_massB);
   c->sortw.lookback = reinterpret_cast<uint32_t*>(c->ws + p.off_lb);
-  c->sortw.ctrl = reinterpret_cast<uint32_t*>(c->ws + p.off_sctrl);
+  c->sortw.ctrl = reinterpret_cast<SortCtrl*>(c->ws + p.off_sctrl);
+  c->sortw.max_cells = max_cells;
   c->sortw.num_sms = c->num_sms;
   c->assw.ctrl = c->ws + p.off_actrl;
   c->assw.X = reinterpret_cast<u128*>(c->ws + p.off_X);
@@ -406,7 +407,7 @@ int amber_rank(amber_ctx* c, const float* d_J, int64_t ncells, uint32_t* d_order
   DeviceGuard g(c->device);
   cudaStream_t s = (cudaStream_t)stream;
   c->last_stream = s;
-  return cuda_status(rank_impl<float>(c->sortw, d_J, ncells, d_order, nullptr, nullptr, nullptr, c->status, s,
+  return cuda_status(rank_impl<float>(c->sortw, d_J, ncells, d_order, nullptr, nullptr, nullptr, false, c->status, s,
                                       &c->prof, kSpinLimit));
 }
 
@@ -417,7 +418,7 @@ int amber_rank_f64(amber_ctx* c, const double* d_J, int64_t ncells, uint32_t* d_
   DeviceGuard g(c->device);
   cudaStream_t s = (cudaStream_t)stream;
   c->last_stream = s;
-  return cuda_status(rank_impl<double>(c->sortw, d_J, ncells, d_order, nullptr, nullptr, nullptr, c->status, s,
+  return cuda_status(rank_impl<double>(c->sortw, d_J, ncells, d_order, nullptr, nullptr, nullptr, false, c->status, s,
                                        &c->prof, kSpinLimit));
 }
 
@@ -464,7 +465,7 @@ int amber_solve(amber_ctx* c, const float* d_src, const float* d_mass, const amb
   unsigned long long* total = reinterpret_cast<unsigned long long*>(c->assw.ctrl);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->assw.ctrl, 0, kAssignCtrlBytes, s);
   if (e == cudaSuccess)
-    e = rank_impl<float>(c->sortw, J, C, c->sortw.idxB, d_mass, c->sortw.massB, total, c->status, s, &c->prof,
+    e = rank_impl<float>(c->sortw, J, C, c->sortw.idxB, d_mass, c->sortw.massB, total, false, c->status, s, &c->prof,
                         kSpinLimit);
   if (e == cudaSuccess)
     e = assign_impl(c->assw, c->sortw.idxB, c->sortw.massB, true, true, C, hc, d_zre, nullptr, c->status, s,
@@ -491,7 +492,7 @@ int amber_solve_f64(amber_ctx* c, const double* d_src, const float* d_mass, cons
   unsigned long long* total = reinterpret_cast<unsigned long long*>(c->assw.ctrl);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->assw.ctrl, 0, kAssignCtrlBytes, s);
   if (e == cudaSuccess)
-    e = rank_impl<double>(c->sortw, J, C, c->sortw.idxB, d_mass, c->sortw.massB, total, c->status, s, &c->prof,
+    e = rank_impl<double>(c->sortw, J, C, c->sortw.idxB, d_mass, c->sortw.massB, total, false, c->status, s, &c->prof,
                         kSpinLimit);
   if (e == cudaSuccess)
     e = assign_impl(c->assw, c->sortw.idxB, c->sortw.massB, true, true, C, hc, d_zre, nullptr, c->status, s,
@@ -560,6 +561,20 @@ int amber_profile_read(amber_ctx* c, int kind, const char** name, double* total_
   if (name) *name = kProfNames[kind];
   if (total_ms) *total_ms = c->prof.total_ms[kind];
   if (launches) *launches = c->prof.launches[kind];
+  return AMBER_OK;
+}
+
+int amber_sort_passes(amber_ctx* c, int* out_passes) {
+  if (!c || !out_passes) return AMBER_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(c->mu);
+  DeviceGuard g(c->device);
+  int np = 0;
+  if (cudaStreamSynchronize(c->last_stream) != cudaSuccess ||
+      cudaMemcpy(&np, &c->sortw.ctrl->npasses, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) {
+    cudaGetLastError();
+    return AMBER_ERR_CUDA;
+  }
+  *out_passes = np;
   return AMBER_OK;
 }
 

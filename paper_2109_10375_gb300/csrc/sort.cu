@@ -2,19 +2,25 @@
 // digit radix sort of order-preserving keys with the cell index as payload,
 // so order[r] is the cell of rank r in descending intensity with ties in
 // ascending cell index.  The paper ranks with a parallel quicksort; here the
-// sort is a onesweep LSD radix sort with 8-bit digits:
+// sort is a onesweep LSD radix sort:
 //
-//   k_sort_histogram : one read of the intensities; digit counts for every
-//                      digit position at once (shared-memory counters, with
-//                      one add per warp when all 32 lanes share a digit)
-//   k_sort_offsets   : exclusive scan of each digit histogram
+//   k_key_range      : min and max key (the sort runs on key - min, so a
+//                      field whose intensities span a few octaves needs
+//                      27 bits, i.e. three 9-bit digits instead of four)
+//   k_sort_histogram : one read of the intensities; counts of every digit
+//                      position at once (shared-memory counters, one add per
+//                      warp when all 32 lanes share a digit)
+//   k_sort_offsets   : exclusive scan of each digit histogram and the number
+//                      of passes the key range needs
 //   k_sort_pass      : per digit position, tiles claim ids from an atomic
-//                      ticket, rank keys locally (8 warp ballots give each
-//                      lane its peers of equal digit; per-warp digit
-//                      counters), publish per-digit tile counts, resolve
-//                      their global offset by decoupled look-back over
-//                      predecessor tiles, and scatter through shared memory
-//                      so each digit run is written contiguously.
+//                      ticket, rank keys locally (one warp ballot per digit
+//                      bit gives each lane its peers of equal digit; per-warp
+//                      digit counters), publish per-digit tile counts,
+//                      resolve their global offset by decoupled look-back
+//                      over predecessor tiles, and scatter through shared
+//                      memory so each digit run is written contiguously.
+//                      Passes beyond the needed count return at once; the
+//                      last needed pass writes only the payloads.
 //
 // The whole-path variant carries the cell mass as a second payload, so the
 // abundance matching reads masses in rank order without a random gather; its
@@ -29,24 +35,9 @@
 
 namespace amber {
 
-__device__ __forceinline__ uint32_t enc_desc(float v, bool& bad) {
-  bad |= isnan(v);
-  v = v + 0.0f;  // -0 -> +0
-  const uint32_t b = __float_as_uint(v);
-  const uint32_t u = (b & 0x80000000u) ? ~b : (b | 0x80000000u);
-  return ~u;
+template <typename SRC> constexpr int max_passes() {
+  return (8 * (int)sizeof(typename KeyOf<SRC>::K) + KeyOf<SRC>::RB - 1) / KeyOf<SRC>::RB;
 }
-__device__ __forceinline__ uint64_t enc_desc(double v, bool& bad) {
-  bad |= isnan(v);
-  v = v + 0.0;
-  const uint64_t b = (uint64_t)__double_as_longlong(v);
-  const uint64_t u = (b & 0x8000000000000000ull) ? ~b : (b | 0x8000000000000000ull);
-  return ~u;
-}
-
-template <typename SRC> struct KeyOf;
-template <> struct KeyOf<float> { using K = uint32_t; };
-template <> struct KeyOf<double> { using K = uint64_t; };
 
 __device__ __forceinline__ unsigned lanemask_lt() {
   unsigned m;
@@ -55,7 +46,7 @@ __device__ __forceinline__ unsigned lanemask_lt() {
 }
 
 // Count digit d of this lane into h[d]: a single add when the whole warp
-// agrees (the high key bytes of a narrow intensity range), else one per lane.
+// agrees (the high digits of a narrow intensity range), else one per lane.
 __device__ __forceinline__ void hist_add(uint32_t* h, unsigned d) {
   const unsigned d0 = __shfl_sync(0xffffffffu, d, 0);
   if (__all_sync(0xffffffffu, d == d0)) {
@@ -67,23 +58,38 @@ __device__ __forceinline__ void hist_add(uint32_t* h, unsigned d) {
 
 // ---------------------------------------------------------------------------
 template <typename SRC>
-__global__ void __launch_bounds__(256) k_sort_histogram(const SRC* __restrict__ J, int64_t n,
-                                                        uint32_t* __restrict__ hist,
-                                                        uint32_t* __restrict__ lb0, int64_t lb0_words,
-                                                        unsigned int* __restrict__ status) {
+__global__ void __launch_bounds__(256) k_key_range(const SRC* __restrict__ J, int64_t n,
+                                                   SortCtrl* __restrict__ ctrl, unsigned int* __restrict__ status) {
   using K = typename KeyOf<SRC>::K;
-  constexpr int P = sizeof(K);         // digit positions
+  bool bad = false;
+  K lo = ~K(0), hi = 0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const K k = enc_desc(J[i], bad);
+    lo = k < lo ? k : lo;
+    hi = k > hi ? k : hi;
+  }
+  key_range_commit(lo, hi, ctrl);
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) raise_status(status, AMBER_ERR_NONFINITE);
+}
+
+template <typename SRC>
+__global__ void __launch_bounds__(256) k_sort_histogram(const SRC* __restrict__ J, int64_t n,
+                                                        SortCtrl* __restrict__ ctrl,
+                                                        uint32_t* __restrict__ lb0, int64_t lb0_words) {
+  using K = typename KeyOf<SRC>::K;
+  constexpr int RB = KeyOf<SRC>::RB, R = 1 << RB, P = max_passes<SRC>();
   constexpr int V = 16 / sizeof(SRC);  // elements per 16-byte load
-  __shared__ uint32_t h[P][kRadix];
-  for (int i = threadIdx.x; i < P * kRadix; i += blockDim.x) (&h[0][0])[i] = 0;
+  __shared__ uint32_t h[P][R];
+  for (int i = threadIdx.x; i < P * R; i += blockDim.x) (&h[0][0])[i] = 0;
   __syncthreads();
+  const K kmin = (K)ctrl->kmin;
   bool bad = false;
   const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
   const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  // full 16-byte vectors; every lane of a warp runs the same trip count
   const int64_t nvec = n / V;
   const int64_t vec_iters = (nvec + nthreads - 1) / nthreads;
-  for (int64_t it = 0; it < vec_iters; ++it) {
+  for (int64_t it = 0; it < vec_iters; ++it) {  // the same trip count on every lane
     const int64_t v = it * nthreads + gtid;
     const bool ok = v < nvec;
     SRC x[V];
@@ -94,79 +100,110 @@ __global__ void __launch_bounds__(256) k_sort_histogram(const SRC* __restrict__ 
     const bool all_ok = __all_sync(0xffffffffu, ok);
 #pragma unroll
     for (int e = 0; e < V; ++e) {
-      const K key = ok ? enc_desc(x[e], bad) : K(0);
+      const K key = ok ? K(enc_desc(x[e], bad) - kmin) : K(0);
 #pragma unroll
       for (int p = 0; p < P; ++p) {
-        const unsigned d = (unsigned)(key >> (8 * p)) & 0xffu;
+        const unsigned d = (unsigned)(key >> (RB * p)) & (R - 1);
         if (all_ok) hist_add(h[p], d);
         else if (ok) atomicAdd(&h[p][d], 1u);
       }
     }
   }
-  // ragged tail (< V elements)
-  for (int64_t i = nvec * V + gtid; i < n; i += nthreads) {
-    const K key = enc_desc(J[i], bad);
+  for (int64_t i = nvec * V + gtid; i < n; i += nthreads) {  // ragged tail
+    const K key = K(enc_desc(J[i], bad) - kmin);
 #pragma unroll
-    for (int p = 0; p < P; ++p) atomicAdd(&h[p][(unsigned)(key >> (8 * p)) & 0xffu], 1u);
+    for (int p = 0; p < P; ++p) atomicAdd(&h[p][(unsigned)(key >> (RB * p)) & (R - 1)], 1u);
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < P * kRadix; i += blockDim.x) {
+  for (int i = threadIdx.x; i < P * R; i += blockDim.x) {
     const uint32_t c = (&h[0][0])[i];
-    if (c) atomicAdd(&hist[i], c);
+    if (c) atomicAdd(&ctrl->hist[i], c);
   }
-  // clear the look-back area of the first digit pass
-  for (int64_t w = gtid; w < lb0_words; w += nthreads) lb0[w] = 0;
-  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) raise_status(status, AMBER_ERR_NONFINITE);
+  for (int64_t w = gtid; w < lb0_words; w += nthreads) lb0[w] = 0;  // look-back of the first pass
 }
 
-// One CTA: exclusive scan of each of the P digit histograms -> bin offsets.
-__global__ void __launch_bounds__(kRadix) k_sort_offsets(const uint32_t* __restrict__ hist,
-                                                         uint32_t* __restrict__ offs, int P) {
-  __shared__ uint32_t s[kRadix];
+// One CTA: exclusive scan of each digit histogram, and the pass count.
+template <typename SRC>
+__global__ void __launch_bounds__(256) k_sort_offsets(SortCtrl* __restrict__ ctrl) {
+  using K = typename KeyOf<SRC>::K;
+  constexpr int RB = KeyOf<SRC>::RB, R = 1 << RB, P = max_passes<SRC>();
+  __shared__ uint32_t wsum[8];
+  __shared__ uint32_t carry;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int p = 0; p < P; ++p) {
-    const uint32_t c = hist[p * kRadix + threadIdx.x];
-    s[threadIdx.x] = c;
+    if (threadIdx.x == 0) carry = 0;
     __syncthreads();
-    for (int o = 1; o < kRadix; o <<= 1) {
-      const uint32_t t = threadIdx.x >= o ? s[threadIdx.x - o] : 0u;
+    for (int d0 = 0; d0 < R; d0 += 256) {
+      const int d = d0 + threadIdx.x;
+      const uint32_t c = ctrl->hist[p * R + d];
+      uint32_t x = c;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+      }
+      if (lane == 31) wsum[warp] = x;
       __syncthreads();
-      s[threadIdx.x] += t;
+      uint32_t pre = carry, tot = 0;
+#pragma unroll
+      for (int w = 0; w < 8; ++w) {
+        pre += (w < warp) ? wsum[w] : 0u;
+        tot += wsum[w];
+      }
+      ctrl->offs[p * R + d] = pre + x - c;
+      __syncthreads();
+      if (threadIdx.x == 0) carry += tot;
       __syncthreads();
     }
-    offs[p * kRadix + threadIdx.x] = s[threadIdx.x] - c;
-    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const K range = (K)ctrl->kmax - (K)ctrl->kmin;
+    int bits = 0;
+    while (bits < (int)(8 * sizeof(K)) && (range >> bits) != 0) ++bits;
+    const int np = (bits + RB - 1) / RB;
+    ctrl->npasses = np < 1 ? 1 : np;
   }
 }
 
 // ---------------------------------------------------------------------------
-// One digit pass.  FIRST: keys come from the intensities (encoded on load),
-// payload = cell index, and (MASS) masses are read in cell order, summed into
-// mass_total and checked.  LAST: only the payloads are written.
+// One digit pass.  FIRST: keys come from the intensities (encoded, minus the
+// minimum key), payload = cell index, and (MASS) masses are read in cell
+// order, summed into mass_total and checked.  The last needed pass writes
+// only the payloads (to the final arrays).
 // ---------------------------------------------------------------------------
-template <typename SRC, bool FIRST, bool LAST, bool MASS>
+template <typename SRC, bool FIRST, bool MASS>
 __global__ void __launch_bounds__(kSortThreads, 3) k_sort_pass(const PassArgs a) {
   using K = typename KeyOf<SRC>::K;
+  constexpr int RB = KeyOf<SRC>::RB, R = 1 << RB, DPT = R / kSortThreads;  // digits per thread
   constexpr int NW = kSortThreads / 32;
+  const int npasses = a.ctrl->npasses;
+  if (a.pass >= npasses) return;  // the key range needs fewer digits
+  const bool last = a.pass == npasses - 1;
+
   extern __shared__ __align__(16) unsigned char smem_raw[];
   K* skey = reinterpret_cast<K*>(smem_raw);                                  // [kTile]
   uint32_t* sval = reinterpret_cast<uint32_t*>(skey + kTile);               // [kTile]
   float* smass = reinterpret_cast<float*>(sval + kTile);                     // [kTile] if MASS
-  uint32_t* whist = reinterpret_cast<uint32_t*>(smass + (MASS ? kTile : 0)); // [NW][256]
-  uint32_t* dstart = whist + NW * kRadix;                                    // [256]
-  uint32_t* gbase = dstart + kRadix;                                         // [256]
+  uint32_t* whist = reinterpret_cast<uint32_t*>(smass + (MASS ? kTile : 0)); // [NW][R]
+  uint32_t* dstart = whist + NW * R;                                         // [R]
+  uint32_t* gbase = dstart + R;                                              // [R]
   __shared__ uint32_t s_tile;
   __shared__ uint32_t wsum[NW];
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  if (tid == 0) s_tile = atomicAdd(a.ticket, 1u);
-  for (int i = tid; i < NW * kRadix; i += kSortThreads) whist[i] = 0;
+  if (tid == 0) s_tile = atomicAdd(&a.ctrl->ticket[a.pass], 1u);
+  for (int i = tid; i < NW * R; i += kSortThreads) whist[i] = 0;
   __syncthreads();
   const uint32_t tile = s_tile;
   const int64_t start = (int64_t)tile * kTile;
   const int64_t n = a.n;
-  const int shift = a.shift;
-  if (a.lb_next) a.lb_next[(int64_t)tile * kRadix + tid] = 0;  // kSortThreads == kRadix
-  const int64_t wbase = start + warp * kItems * 32 + lane;       // item it at wbase + 32 it
+  const int shift = RB * a.pass;
+  if (a.lb_next) {
+#pragma unroll
+    for (int j = 0; j < DPT; ++j) a.lb_next[(int64_t)tile * R + j * kSortThreads + tid] = 0;
+  }
+  const int64_t wbase = start + warp * kItems * 32 + lane;  // item it at wbase + 32 it
+  const K kmin = FIRST ? (K)a.ctrl->kmin : K(0);
 
   // ---- keys (warp-striped) and their local ranks, packed rank | digit << 16
   K key[kItems];
@@ -176,18 +213,18 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_sort_pass(const PassArgs a)
   for (int it = 0; it < kItems; ++it) {
     const int64_t g = wbase + 32 * it;
     const bool ok = g < n;
-    if constexpr (FIRST) key[it] = ok ? enc_desc(reinterpret_cast<const SRC*>(a.J)[g], bad) : K(0);
+    if constexpr (FIRST) key[it] = ok ? K(enc_desc(reinterpret_cast<const SRC*>(a.J)[g], bad) - kmin) : K(0);
     else key[it] = ok ? reinterpret_cast<const K*>(a.kin)[g] : K(0);
   }
-  uint32_t* wh = whist + warp * kRadix;
+  uint32_t* wh = whist + warp * R;
   const unsigned lt = lanemask_lt();
 #pragma unroll
   for (int it = 0; it < kItems; ++it) {
     const bool ok = wbase + 32 * it < n;
-    const unsigned d = (unsigned)(key[it] >> shift) & 0xffu;
+    const unsigned d = (unsigned)(key[it] >> shift) & (R - 1);
     unsigned peers = __ballot_sync(0xffffffffu, ok);
 #pragma unroll
-    for (int b = 0; b < 8; ++b) {
+    for (int b = 0; b < RB; ++b) {
       const unsigned bb = __ballot_sync(0xffffffffu, (d >> b) & 1u);
       peers &= ((d >> b) & 1u) ? bb : ~bb;
     }
@@ -200,32 +237,46 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_sort_pass(const PassArgs a)
   }
   __syncthreads();
 
-  // ---- per digit (thread = digit): warp prefixes and the tile count
-  const int d = tid;
-  uint32_t cnt = 0;
+  // ---- per digit (thread tid owns digits tid + 256 j): warp prefixes, the
+  // tile count, and its publication for successors
+  uint32_t cnt[DPT];
 #pragma unroll
-  for (int w = 0; w < NW; ++w) {
-    const uint32_t c = whist[w * kRadix + d];
-    whist[w * kRadix + d] = cnt;
-    cnt += c;
-  }
-  uint32_t* my = a.lb + (int64_t)tile * kRadix + d;
-  st_relaxed_u32(my, (tile == 0 ? kFlagInc : kFlagAgg) | cnt);
-  {
-    uint32_t x = cnt;
+  for (int j = 0; j < DPT; ++j) {
+    const int d = j * kSortThreads + tid;
+    uint32_t c = 0;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-      if (lane >= o) x += y;
+    for (int w = 0; w < NW; ++w) {
+      const uint32_t x = whist[w * R + d];
+      whist[w * R + d] = c;
+      c += x;
     }
-    if (lane == 31) wsum[warp] = x;
-    __syncthreads();
-    uint32_t wpre = 0;
-#pragma unroll
-    for (int w = 0; w < NW; ++w) wpre += (w < warp) ? wsum[w] : 0u;
-    dstart[d] = wpre + x - cnt;
+    cnt[j] = c;
+    st_relaxed_u32(a.lb + (int64_t)tile * R + d, (tile == 0 ? kFlagInc : kFlagAgg) | c);
   }
-  __syncthreads();
+  {
+    // tile-local digit starts: exclusive scan over the R digits
+    uint32_t carry = 0;
+#pragma unroll
+    for (int j = 0; j < DPT; ++j) {
+      uint32_t x = cnt[j];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+      }
+      if (lane == 31) wsum[warp] = x;
+      __syncthreads();
+      uint32_t wpre = 0, tot = 0;
+#pragma unroll
+      for (int w = 0; w < NW; ++w) {
+        wpre += (w < warp) ? wsum[w] : 0u;
+        tot += wsum[w];
+      }
+      dstart[j * kSortThreads + tid] = carry + wpre + x - cnt[j];
+      carry += tot;
+      __syncthreads();
+    }
+  }
 
   // ---- keys and payloads into shared memory in tile-sorted order; payloads
   // are loaded here so they never occupy registers during the ranking
@@ -234,7 +285,7 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_sort_pass(const PassArgs a)
   for (int it = 0; it < kItems; ++it) {
     if (rd[it] == 0xffffffffu) continue;
     const unsigned dd = rd[it] >> 16;
-    const uint32_t p = dstart[dd] + whist[warp * kRadix + dd] + (rd[it] & 0xffffu);
+    const uint32_t p = dstart[dd] + whist[warp * R + dd] + (rd[it] & 0xffffu);
     const int64_t g = wbase + 32 * it;
     skey[p] = key[it];
     sval[p] = FIRST ? (uint32_t)g : a.vin[g];
@@ -250,55 +301,62 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_sort_pass(const PassArgs a)
     if (lane == 0 && msum != 0) atomic_add_u128(a.mass_total, msum);
   }
 
-  // ---- decoupled look-back for digit d, kLookWindow predecessors per round
+  // ---- decoupled look-back per digit, kLookWindow predecessors per round
   // trip: sum aggregates back to the nearest inclusive prefix
-  uint32_t excl = 0;
-  if (tile > 0) {
-    int64_t t = (int64_t)tile - 1;
-    unsigned spins = 0;
-    while (true) {
-      uint32_t w[kLookWindow];
 #pragma unroll
-      for (int k = 0; k < kLookWindow; ++k)
-        w[k] = (t - k >= 0) ? ld_relaxed_u32(a.lb + (t - k) * kRadix + d) : kFlagInc;
-      bool stop = false, done = false;
-      int adv = 0;
+  for (int j = 0; j < DPT; ++j) {
+    const int d = j * kSortThreads + tid;
+    uint32_t excl = 0;
+    if (tile > 0) {
+      int64_t t = (int64_t)tile - 1;
+      unsigned spins = 0;
+      while (true) {
+        uint32_t w[kLookWindow];
 #pragma unroll
-      for (int k = 0; k < kLookWindow; ++k) {
-        if (!stop) {
-          const uint32_t f = w[k] & kFlagMask;
-          if (f == 0u) {
-            stop = true;
-          } else {
-            excl += w[k] & kValueMask;
-            ++adv;
-            if (f == kFlagInc) stop = done = true;
+        for (int k = 0; k < kLookWindow; ++k)
+          w[k] = (t - k >= 0) ? ld_relaxed_u32(a.lb + (t - k) * R + d) : kFlagInc;
+        bool stop = false, done = false;
+        int adv = 0;
+#pragma unroll
+        for (int k = 0; k < kLookWindow; ++k) {
+          if (!stop) {
+            const uint32_t f = w[k] & kFlagMask;
+            if (f == 0u) {
+              stop = true;
+            } else {
+              excl += w[k] & kValueMask;
+              ++adv;
+              if (f == kFlagInc) stop = done = true;
+            }
           }
         }
+        if (done) break;
+        t -= adv;
+        if (adv < kLookWindow) {  // the tile at t has published nothing yet
+          if (++spins >= a.spin_limit) { raise_status(a.status, AMBER_ERR_DEVICE_TIMEOUT); break; }
+          __nanosleep(20);
+        }
       }
-      if (done) break;
-      t -= adv;
-      if (adv < kLookWindow) {  // the tile at t has published nothing yet
-        if (++spins >= a.spin_limit) { raise_status(a.status, AMBER_ERR_DEVICE_TIMEOUT); break; }
-        __nanosleep(20);
-      }
+      st_relaxed_u32(a.lb + (int64_t)tile * R + d, kFlagInc | ((excl + cnt[j]) & kValueMask));
     }
-    st_relaxed_u32(my, kFlagInc | ((excl + cnt) & kValueMask));
+    gbase[d] = a.ctrl->offs[a.pass * R + d] + excl - dstart[d];
   }
-  gbase[d] = a.bin_off[d] + excl - dstart[d];
   __syncthreads();
 
   // ---- write out: consecutive positions of one digit go to consecutive addresses
   const int cnt_tile = (int)(n - start < (int64_t)kTile ? n - start : (int64_t)kTile);
+  K* kout = reinterpret_cast<K*>(a.kout);
+  uint32_t* vout = last ? a.vfinal : a.vout;
+  float* mout = last ? a.mfinal : a.mout;
 #pragma unroll
   for (int it = 0; it < kItems; ++it) {
     const int p = it * kSortThreads + tid;
     if (p < cnt_tile) {
       const K kk = skey[p];
-      const uint32_t g = gbase[(unsigned)(kk >> shift) & 0xffu] + p;
-      if constexpr (!LAST) reinterpret_cast<K*>(a.kout)[g] = kk;
-      a.vout[g] = sval[p];
-      if constexpr (MASS) a.mout[g] = smass[p];
+      const uint32_t g = gbase[(unsigned)(kk >> shift) & (R - 1)] + p;
+      if (!last) kout[g] = kk;
+      vout[g] = sval[p];
+      if constexpr (MASS) mout[g] = smass[p];
     }
   }
   if (__any_sync(0xffffffffu, bad) && lane == 0)
@@ -308,55 +366,57 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_sort_pass(const PassArgs a)
 // ---------------------------------------------------------------------------
 // Host side.
 // ---------------------------------------------------------------------------
-size_t sort_pass_smem(int key_bytes, bool mass) {
-  return (size_t)kTile * key_bytes + (size_t)kTile * 4 * (mass ? 2 : 1) + (size_t)(kSortThreads / 32) * kRadix * 4 +
-         2 * kRadix * 4;
+template <typename SRC> static size_t pass_smem(bool mass) {
+  constexpr int R = 1 << KeyOf<SRC>::RB;
+  return (size_t)kTile * sizeof(typename KeyOf<SRC>::K) + (size_t)kTile * 4 * (mass ? 2 : 1) +
+         (size_t)(kSortThreads / 32) * R * 4 + 2 * R * 4;
 }
 
 int64_t sort_tiles(int64_t n) { return (n + kTile - 1) / kTile; }
+size_t sort_lookback_words(int64_t n) { return (size_t)sort_tiles(n) * kMaxRadix; }
 
-template <typename SRC, bool FIRST, bool LAST, bool MASS>
+template <typename SRC, bool FIRST, bool MASS>
 static void launch_pass(const PassArgs& a, int64_t tiles, cudaStream_t s) {
-  const size_t smem = sort_pass_smem(sizeof(typename KeyOf<SRC>::K), MASS);
+  const size_t smem = pass_smem<SRC>(MASS);
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_sort_pass<SRC, FIRST, LAST, MASS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_sort_pass<SRC, FIRST, MASS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     attr = true;
   }
-  k_sort_pass<SRC, FIRST, LAST, MASS><<<(unsigned)tiles, kSortThreads, smem, s>>>(a);
+  k_sort_pass<SRC, FIRST, MASS><<<(unsigned)tiles, kSortThreads, smem, s>>>(a);
 }
 
-template <typename SRC, bool MASS>
-static void launch_pass_rt(bool first, bool last, const PassArgs& a, int64_t tiles, cudaStream_t s) {
-  if (first && last) launch_pass<SRC, true, true, MASS>(a, tiles, s);
-  else if (first) launch_pass<SRC, true, false, MASS>(a, tiles, s);
-  else if (last) launch_pass<SRC, false, true, MASS>(a, tiles, s);
-  else launch_pass<SRC, false, false, MASS>(a, tiles, s);
+cudaError_t sort_ctrl_reset(SortCtrl* ctrl, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(ctrl, 0, sizeof(SortCtrl), s);
+  if (e != cudaSuccess) return e;
+  return cudaMemsetAsync(&ctrl->kmin, 0xff, sizeof(ctrl->kmin), s);
 }
 
 template <typename SRC>
 cudaError_t rank_impl(const SortWork& w, const SRC* J, int64_t n, uint32_t* order, const float* mass_in,
-                      float* mass_out, unsigned long long* mass_total, unsigned int* status, cudaStream_t s,
-                      FftProfile* prof, unsigned int spin_limit) {
+                      float* mass_out, unsigned long long* mass_total, bool range_ready, unsigned int* status,
+                      cudaStream_t s, FftProfile* prof, unsigned int spin_limit) {
   using K = typename KeyOf<SRC>::K;
-  constexpr int P = sizeof(K);
+  constexpr int R = 1 << KeyOf<SRC>::RB, P = max_passes<SRC>();
   const bool with_mass = mass_in != nullptr;
   const int64_t tiles = sort_tiles(n);
-  const int64_t lbw = tiles * kRadix;  // words per look-back region
-  cudaError_t e = cudaMemsetAsync(w.ctrl, 0, kSortCtrlBytes, s);
-  if (e != cudaSuccess) return e;
-  uint32_t* hist = w.ctrl;                   // [8][256]
-  uint32_t* offs = w.ctrl + 8 * kRadix;      // [8][256]
-  uint32_t* tickets = w.ctrl + 16 * kRadix;  // [8]
+  const int64_t lbw = tiles * R;  // words per look-back region used
+  SortCtrl* ctrl = w.ctrl;
+  cudaError_t e;
+  if (!range_ready) {
+    e = sort_ctrl_reset(ctrl, s);
+    if (e != cudaSuccess) return e;
+  }
   uint32_t* lbA = w.lookback;
-  uint32_t* lbB = w.lookback + lbw;
+  uint32_t* lbB = w.lookback + sort_lookback_words(w.max_cells);
 
   prof_begin(prof, PK_SORT_HIST, s);
   {
     int grid = (int)std::min<int64_t>((n / (16 / (int)sizeof(SRC)) + 255) / 256, (int64_t)w.num_sms * 8);
     if (grid < 1) grid = 1;
-    k_sort_histogram<SRC><<<grid, 256, 0, s>>>(J, n, hist, lbA, lbw, status);
-    k_sort_offsets<<<1, kRadix, 0, s>>>(hist, offs, P);
+    if (!range_ready) k_key_range<SRC><<<grid, 256, 0, s>>>(J, n, ctrl, status);
+    k_sort_histogram<SRC><<<grid, 256, 0, s>>>(J, n, ctrl, lbA, lbw);
+    k_sort_offsets<SRC><<<1, 256, 0, s>>>(ctrl);
   }
   prof_end(prof, PK_SORT_HIST, s);
 
@@ -366,27 +426,32 @@ cudaError_t rank_impl(const SortWork& w, const SRC* J, int64_t n, uint32_t* orde
   const uint32_t* vin = nullptr;
   const float* mcur = mass_in;
   for (int p = 0; p < P; ++p) {
-    const bool first = p == 0, last = p == P - 1;
     PassArgs a;
     a.J = J;
     a.kin = kin;
     a.vin = vin;
     a.min = mcur;
     a.kout = (p & 1) ? (void*)kB : (void*)kA;
-    a.vout = last ? order : ((p & 1) ? w.idxB : w.idxA);
-    a.mout = with_mass ? (last ? mass_out : ((p & 1) ? w.massB : w.massA)) : nullptr;
+    a.vout = (p & 1) ? w.idxB : w.idxA;
+    a.mout = with_mass ? ((p & 1) ? w.massB : w.massA) : nullptr;
+    a.vfinal = order;
+    a.mfinal = mass_out;
     a.n = n;
-    a.shift = 8 * p;
-    a.bin_off = offs + p * kRadix;
+    a.pass = p;
     a.lb = (p & 1) ? lbB : lbA;
-    a.lb_next = last ? nullptr : ((p & 1) ? lbA : lbB);
-    a.ticket = tickets + p;
+    a.lb_next = (p == P - 1) ? nullptr : ((p & 1) ? lbA : lbB);
+    a.ctrl = ctrl;
     a.mass_total = mass_total;
     a.status = status;
     a.spin_limit = spin_limit;
     prof_begin(prof, PK_SORT_PASS, s);
-    if (with_mass) launch_pass_rt<SRC, true>(first, last, a, tiles, s);
-    else launch_pass_rt<SRC, false>(first, last, a, tiles, s);
+    if (p == 0) {
+      if (with_mass) launch_pass<SRC, true, true>(a, tiles, s);
+      else launch_pass<SRC, true, false>(a, tiles, s);
+    } else {
+      if (with_mass) launch_pass<SRC, false, true>(a, tiles, s);
+      else launch_pass<SRC, false, false>(a, tiles, s);
+    }
     prof_end(prof, PK_SORT_PASS, s);
     kin = a.kout;
     vin = a.vout;
@@ -396,9 +461,11 @@ cudaError_t rank_impl(const SortWork& w, const SRC* J, int64_t n, uint32_t* orde
 }
 
 template cudaError_t rank_impl<float>(const SortWork&, const float*, int64_t, uint32_t*, const float*, float*,
-                                      unsigned long long*, unsigned int*, cudaStream_t, FftProfile*, unsigned int);
+                                      unsigned long long*, bool, unsigned int*, cudaStream_t, FftProfile*,
+                                      unsigned int);
 template cudaError_t rank_impl<double>(const SortWork&, const double*, int64_t, uint32_t*, const float*, float*,
-                                       unsigned long long*, unsigned int*, cudaStream_t, FftProfile*, unsigned int);
+                                       unsigned long long*, bool, unsigned int*, cudaStream_t, FftProfile*,
+                                       unsigned int);
 
 // Failure-detection hook: the look-back wait on a word nothing publishes.
 __global__ void k_wait_never(const uint32_t* __restrict__ word, unsigned int* __restrict__ status,
