@@ -88,7 +88,7 @@ int amber_history_table(const amber_history_t *h, double *z_out, double *x_out);
 
 /* Create a context on `device` able to process up to max_cells cells
  * (max_cells <= 2^30; the FFT needs n^3 <= max_cells).  Allocates the whole
- * workspace once (about 21 bytes per cell plus the half spectrum, see
+ * workspace once (about 29 bytes per cell including the half spectrum, see
  * amber_workspace_bytes).  *ctx is owned by the caller and released with
  * amber_destroy.  Returns AMBER_ERR_CUDA when no device is usable and
  * AMBER_ERR_OOM when the workspace does not fit. */
@@ -132,6 +132,18 @@ int amber_rank_f64(amber_ctx *ctx, const double *d_J, int64_t ncells, uint32_t *
  * with a positive total.  d_order must be a permutation of [0, ncells). */
 int amber_assign_zre(amber_ctx *ctx, const uint32_t *d_order, const float *d_mass, int64_t ncells,
                      const amber_history_t *h, float *d_zre, double *d_F_opt, void *stream);
+
+/* Source field from a density field (the step before the radiation field in
+ * the serving path).  Sec. 3.3's excursion-set collapsed fraction with the
+ * ESF-E halo density (Eq. fcoll; rho_h = f_coll rho (1 + delta)):
+ *   mass = 1 + max(delta, -0.99),
+ *   S = mass * erfc((delta_c - delta)/(sqrt(2) sigma_f)), then S /= mean(S),
+ * with sigma_f standing in for sqrt(sigma^2(M_min) - sigma^2(M_s)).
+ * d_delta: ncells floats; d_S: ncells floats out; d_mass_opt: ncells floats
+ * out or NULL.  FP32 elementwise, exact fixed-point mean.  A NaN density
+ * latches AMBER_ERR_NONFINITE. */
+int amber_source_field(amber_ctx *ctx, const float *d_delta, int64_t ncells, double delta_c, double sigma_f,
+                       float *d_S, float *d_mass_opt, void *stream);
 
 /* The whole path for one realisation: radiation field -> rank -> assign.
  * d_src, d_mass: n^3 floats; d_zre: n^3 floats out; d_J_opt: if not NULL,

@@ -156,6 +156,25 @@ def history_table(z_mid: float, dz: float, Az: float, z_lo: float = 5.0, z_hi: f
 
 
 # ---------------------------------------------------------------------------
+# Source field (Sec. 3.3): excursion-set collapsed fraction, ESF-E density
+# ---------------------------------------------------------------------------
+
+def source_field(delta, delta_c: float = 1.686, sigma_f: float = 0.7):
+    """(S, mass) from a density field, float64.
+
+    f_coll = erfc((delta_c - delta) / sqrt(2 sigma_f^2))  (Eq. fcoll, with
+    sigma_f^2 standing for sigma^2(M_min) - sigma^2(M_s)); the halo density
+    is f_coll (1 + delta) (ESF-E form), with 1 + delta floored at 0.01;
+    S is that density divided by its mean; mass = 1 + max(delta, -0.99).
+    """
+    from scipy.special import erfc
+    d = np.asarray(delta, dtype=np.float64)
+    mass = 1.0 + np.maximum(d, -0.99)
+    S = mass * erfc((delta_c - d) / (math.sqrt(2.0) * sigma_f))
+    return S / S.mean(), mass
+
+
+# ---------------------------------------------------------------------------
 # Radiation field (Sec. 3.4.1, Eq. intensity)
 # ---------------------------------------------------------------------------
 

@@ -28,7 +28,7 @@ EXPORTED = [
     "amber_workspace_bytes", "amber_radiation_field", "amber_radiation_field_f64", "amber_rank",
     "amber_rank_f64", "amber_assign_zre", "amber_solve", "amber_solve_f64", "amber_sync_status",
     "amber_status_string", "amber_profile_enable", "amber_profile_reset", "amber_profile_kinds",
-    "amber_profile_read", "amber_sort_passes", "amber_test_wait_timeout",
+    "amber_profile_read", "amber_sort_passes", "amber_test_wait_timeout", "amber_source_field",
 ]
 
 
@@ -76,6 +76,7 @@ def _load():
         "amber_profile_kinds": (i32, []),
         "amber_profile_read": (i32, [vp, i32, C.POINTER(C.c_char_p), C.POINTER(dbl), C.POINTER(i64)]),
         "amber_sort_passes": (i32, [vp, C.POINTER(i32)]),
+        "amber_source_field": (i32, [vp, vp, i64, dbl, dbl, vp, vp, vp]),
         "amber_test_wait_timeout": (i32, [vp, C.c_uint, vp]),
     }
     for name, (res, args) in sig.items():
@@ -190,6 +191,15 @@ class Context:
             out = torch.empty(n, dtype=torch.float32, device=order.device)
         _check(lib.amber_assign_zre(self._h, _ptr(order), _ptr(mass), n, C.byref(h), _ptr(out), _ptr(F),
                                     _stream(stream)), "amber_assign_zre")
+        return out
+
+    def source_field(self, delta, delta_c: float = 1.686, sigma_f: float = 0.7, out=None, mass_out=None,
+                     stream=None):
+        import torch
+        if out is None:
+            out = torch.empty_like(delta)
+        _check(lib.amber_source_field(self._h, _ptr(delta), delta.numel(), delta_c, sigma_f, _ptr(out),
+                                      _ptr(mass_out), _stream(stream)), "amber_source_field")
         return out
 
     def solve(self, S, mass, box: float, l_mfp: float, h: amber_history_t, out=None, J_out=None, stream=None):

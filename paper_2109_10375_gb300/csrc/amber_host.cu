@@ -11,6 +11,7 @@
 #include "assign.cuh"
 #include "fft.cuh"
 #include "sort.cuh"
+#include "source.cuh"
 
 namespace amber {
 cudaError_t radiation_field_f32(int n, const float* src, float* J, void* H, const void* tw, double box, double l_mfp,
@@ -151,7 +152,7 @@ struct Plan {
   int n32 = 0, n64 = 0;
   int64_t cells64 = 0;
   size_t off_spec, off_keysA, off_keysB, off_idxA, off_idxB, off_massA, off_massB, off_lb, off_sctrl, off_actrl, off_X, off_invdx,
-      off_state, off_btab, off_status, off_tw32, off_tw64, total;
+      off_state, off_btab, off_status, off_srcsum, off_tw32, off_tw64, total;
   size_t tw32_off[11] = {}, tw64_off[11] = {};
 };
 
@@ -185,6 +186,7 @@ static Plan make_plan(int64_t max_cells) {
   p.off_state = take(stt);
   p.off_btab = take((size_t)((max_cells + kScanTile - 1) / kScanTile) * (kMaxBuckets + 1) * sizeof(uint16_t));
   p.off_status = take(256);
+  p.off_srcsum = take(256);
   size_t tw32 = 0, tw64 = 0;
   for (int l = 2, n = 4; n <= 1024; ++l, n *= 2) {
     if (n <= p.n32) { p.tw32_off[l] = tw32; tw32 += align256((size_t)n * 8); }
@@ -321,9 +323,9 @@ int amber_create(amber_ctx** out, int device, int64_t max_cells) {
   c->assw.X = reinterpret_cast<u128*>(c->ws + p.off_X);
   c->assw.inv_dx = reinterpret_cast<float*>(c->ws + p.off_invdx);
   c->assw.state = reinterpret_cast<ScanTile*>(c->ws + p.off_state);
-  // bucketed (cell, z) pairs reuse sort buffers that are free by then
-  c->assw.bcell = c->sortw.idxA;
-  c->assw.bz = reinterpret_cast<float*>(c->sortw.keysA);
+  // bucketed (cell, z) pairs reuse the key buffers, dead once ranked
+  c->assw.bcell = reinterpret_cast<uint32_t*>(c->sortw.keysA);
+  c->assw.bz = reinterpret_cast<float*>(c->sortw.keysB);
   c->assw.btab = reinterpret_cast<uint16_t*>(c->ws + p.off_btab);
   c->assw.num_sms = c->num_sms;
   // twiddles w_n^m = exp(-2 pi i m / n), FP64 on the host, rounded for FP32
@@ -465,11 +467,12 @@ int amber_solve(amber_ctx* c, const float* d_src, const float* d_mass, const amb
   unsigned long long* total = reinterpret_cast<unsigned long long*>(c->assw.ctrl);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->assw.ctrl, 0, kAssignCtrlBytes, s);
   if (e == cudaSuccess)
-    e = rank_impl<float>(c->sortw, J, C, c->sortw.idxB, d_mass, c->sortw.massB, total, false, c->status, s, &c->prof,
+    e = rank_impl<float>(c->sortw, J, C, nullptr, d_mass, nullptr, total, false, c->status, s, &c->prof,
                         kSpinLimit);
+  // the order and rank-order masses sit on the A or B side by pass parity
   if (e == cudaSuccess)
-    e = assign_impl(c->assw, c->sortw.idxB, c->sortw.massB, true, true, C, hc, d_zre, nullptr, c->status, s,
-                    &c->prof, kSpinLimit);
+    e = assign_impl(c->assw, c->sortw.idxA, c->sortw.massA, true, true, C, hc, d_zre, nullptr, c->status, s,
+                    &c->prof, kSpinLimit, c->sortw.idxB, c->sortw.massB, &c->sortw.ctrl->npasses);
   return cuda_status(e);
 }
 
@@ -492,11 +495,12 @@ int amber_solve_f64(amber_ctx* c, const double* d_src, const float* d_mass, cons
   unsigned long long* total = reinterpret_cast<unsigned long long*>(c->assw.ctrl);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->assw.ctrl, 0, kAssignCtrlBytes, s);
   if (e == cudaSuccess)
-    e = rank_impl<double>(c->sortw, J, C, c->sortw.idxB, d_mass, c->sortw.massB, total, false, c->status, s, &c->prof,
+    e = rank_impl<double>(c->sortw, J, C, nullptr, d_mass, nullptr, total, false, c->status, s, &c->prof,
                         kSpinLimit);
+  // the order and rank-order masses sit on the A or B side by pass parity
   if (e == cudaSuccess)
-    e = assign_impl(c->assw, c->sortw.idxB, c->sortw.massB, true, true, C, hc, d_zre, nullptr, c->status, s,
-                    &c->prof, kSpinLimit);
+    e = assign_impl(c->assw, c->sortw.idxA, c->sortw.massA, true, true, C, hc, d_zre, nullptr, c->status, s,
+                    &c->prof, kSpinLimit, c->sortw.idxB, c->sortw.massB, &c->sortw.ctrl->npasses);
   return cuda_status(e);
 }
 
@@ -562,6 +566,20 @@ int amber_profile_read(amber_ctx* c, int kind, const char** name, double* total_
   if (total_ms) *total_ms = c->prof.total_ms[kind];
   if (launches) *launches = c->prof.launches[kind];
   return AMBER_OK;
+}
+
+int amber_source_field(amber_ctx* c, const float* d_delta, int64_t ncells, double delta_c, double sigma_f,
+                       float* d_S, float* d_mass_opt, void* stream) {
+  if (!c || !d_delta || !d_S || ncells < 1 || !std::isfinite(delta_c) || !(sigma_f > 0.0) || !std::isfinite(sigma_f))
+    return AMBER_ERR_INVALID_ARG;
+  if (ncells > c->max_cells) return AMBER_ERR_CAPACITY;
+  std::lock_guard<std::mutex> lk(c->mu);
+  DeviceGuard g(c->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  c->last_stream = s;
+  return cuda_status(source_field_impl(d_delta, ncells, delta_c, sigma_f, d_S, d_mass_opt,
+                                       reinterpret_cast<unsigned long long*>(c->ws + c->plan.off_srcsum), c->num_sms,
+                                       c->status, s));
 }
 
 int amber_sort_passes(amber_ctx* c, int* out_passes) {

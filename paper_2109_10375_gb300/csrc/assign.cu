@@ -115,14 +115,17 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_assign(const ScanArgs a) 
   const int64_t start = (int64_t)tile * TILE;
   const int64_t n = a.n;
   const int cnt = (int)(n - start < (int64_t)TILE ? n - start : (int64_t)TILE);
+  const bool side_b = a.pick && ((*a.pick - 1) & 1);
+  const uint32_t* order = side_b ? a.order_b : a.order;
+  const float* mass = side_b ? a.mass_b : a.mass;
 
   // order (and rank-order masses): coalesced striped loads -> padded shared
   // memory -> a blocked run of IT consecutive ranks per thread
 #pragma unroll
   for (int k = 0; k < IT; ++k) {
     const int p = k * NT + tid;
-    sord[p + (p >> 5)] = p < cnt ? a.order[start + p] : 0u;
-    if constexpr (!GATHER) smass[p + (p >> 5)] = p < cnt ? a.mass[start + p] : 0.0f;
+    sord[p + (p >> 5)] = p < cnt ? order[start + p] : 0u;
+    if constexpr (!GATHER) smass[p + (p >> 5)] = p < cnt ? mass[start + p] : 0.0f;
   }
   __syncthreads();
   uint32_t cell[IT];
@@ -134,7 +137,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_assign(const ScanArgs a) 
     const int p = tid * IT + i;
     cell[i] = sord[p + (p >> 5)];
     mv[i] = 0.0f;
-    if (p < cnt) mv[i] = GATHER ? a.mass[cell[i]] : smass[p + (p >> 5)];
+    if (p < cnt) mv[i] = GATHER ? mass[cell[i]] : smass[p + (p >> 5)];
     run += mass_q64(mv[i], bad);
   }
   // block exclusive scan of the thread totals
@@ -318,7 +321,8 @@ void bucket_plan(int64_t n, int* nbuckets, int64_t* width) {
 
 cudaError_t assign_impl(const AssignWork& w, const uint32_t* order, const float* mass, bool mass_in_rank_order,
                         bool total_ready, int64_t n, const HistoryCoeffs& hc, float* zre, double* F,
-                        unsigned int* status, cudaStream_t s, FftProfile* prof, unsigned int spin_limit) {
+                        unsigned int* status, cudaStream_t s, FftProfile* prof, unsigned int spin_limit,
+                        const uint32_t* order_b, const float* mass_b, const int* pick) {
   const int64_t tiles = (n + kScanTile - 1) / kScanTile;
   cudaError_t e;
   unsigned long long* total = reinterpret_cast<unsigned long long*>(w.ctrl);
@@ -348,6 +352,9 @@ cudaError_t assign_impl(const AssignWork& w, const uint32_t* order, const float*
   ScanArgs a;
   a.order = order;
   a.mass = mass;
+  a.order_b = order_b;
+  a.mass_b = mass_b;
+  a.pick = pick;
   a.n = n;
   a.total = total;
   a.X = w.X;

@@ -48,6 +48,9 @@ struct HistoryCoeffs {
 struct ScanArgs {
   const uint32_t* order;
   const float* mass;  // cell order (gathered through order) or rank order
+  const uint32_t* order_b;  // with pick: the sort's results sit in (order, mass)
+  const float* mass_b;      // for an odd pass count and in (order_b, mass_b) else
+  const int* pick;          // &SortCtrl::npasses or null
   int64_t n;
   const unsigned long long* total;
   const u128* X;
@@ -71,8 +74,10 @@ void bucket_plan(int64_t n, int* nbuckets, int64_t* width);
 // mass_in_rank_order: mass[n] belongs to rank n (sort payload) instead of to
 // cell n.  total_ready: the 128-bit mass total in w.ctrl was already summed
 // (by the first sort pass) and must be kept.
+// order_b/mass_b/pick: see ScanArgs (null for a caller-given order).
 cudaError_t assign_impl(const AssignWork& w, const uint32_t* order, const float* mass, bool mass_in_rank_order,
                         bool total_ready, int64_t n, const HistoryCoeffs& hc, float* zre, double* F,
-                        unsigned int* status, cudaStream_t s, FftProfile* prof, unsigned int spin_limit);
+                        unsigned int* status, cudaStream_t s, FftProfile* prof, unsigned int spin_limit,
+                        const uint32_t* order_b = nullptr, const float* mass_b = nullptr, const int* pick = nullptr);
 
 }  // namespace amber

@@ -346,8 +346,10 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_sort_pass(const PassArgs a)
   // ---- write out: consecutive positions of one digit go to consecutive addresses
   const int cnt_tile = (int)(n - start < (int64_t)kTile ? n - start : (int64_t)kTile);
   K* kout = reinterpret_cast<K*>(a.kout);
-  uint32_t* vout = last ? a.vfinal : a.vout;
-  float* mout = last ? a.mfinal : a.mout;
+  // the last needed pass writes the order to vfinal when given, else to its
+  // own parity's buffers (which it does not read)
+  uint32_t* vout = (last && a.vfinal) ? a.vfinal : a.vout;
+  float* mout = (last && a.mfinal) ? a.mfinal : a.mout;
 #pragma unroll
   for (int it = 0; it < kItems; ++it) {
     const int p = it * kSortThreads + tid;

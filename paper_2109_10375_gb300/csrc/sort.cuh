@@ -100,8 +100,9 @@ struct PassArgs {
   void* kout;
   uint32_t* vout;
   float* mout;
-  uint32_t* vfinal;     // the last needed pass writes the order here
-  float* mfinal;        // ... and the masses in rank order here
+  uint32_t* vfinal;     // if not null the last needed pass writes the order here,
+  float* mfinal;        // and the masses in rank order here; else to its own
+                        // parity's vout/mout (pass p writes the A side if p is even)
   int64_t n;
   int pass;
   uint32_t* lb;
@@ -118,7 +119,9 @@ cudaError_t sort_ctrl_reset(SortCtrl* ctrl, cudaStream_t s);
 
 // Stable descending rank of J into order.  With mass_in != NULL the masses
 // ride along as a payload: mass_out receives them in rank order and
-// mass_total (zeroed by the caller) their exact 128-bit sum.  range_ready:
+// mass_total (zeroed by the caller) their exact 128-bit sum.  With order (and
+// mass_out) NULL the results stay in idxA/massA when the needed pass count
+// is odd and in idxB/massB when it is even (read it from ctrl->npasses).  range_ready:
 // ctrl was reset and its key range already folded in (by the intensity
 // kernel), so the range pass is skipped.
 template <typename SRC>

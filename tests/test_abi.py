@@ -71,9 +71,10 @@ def test_entry_points_reject_null_context(B):
 
 
 def test_workspace_plan(B):
-    # 1024^3: half spectrum + 4 sort buffers + look-back, all allocated once
+    # 1024^3: half spectrum (4 B/cell), six 4 B/cell sort buffers, two
+    # 9-bit look-back regions (1 B/cell) and the bucket table, allocated once
     wb = B.workspace_bytes(1 << 30)
-    assert 20e9 < wb < 24e9
+    assert 29e9 < wb < 33e9
     with pytest.raises(B.AmberError):
         B.workspace_bytes((1 << 30) + 1)
 

@@ -261,6 +261,28 @@ def test_host_argument_errors_enqueue_nothing(ctx, B):
 
 
 # ---------------------------------------------------------------------------
+# Source field from density (Sec. 3.3)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n", [1, 1000, 100_003, 64 ** 3])
+def test_source_field_vs_oracle(ctx, B, n):
+    g = np.random.default_rng(n)
+    d = (1.5 * g.normal(size=n)).astype(np.float32)
+    d[::97] = 1.686
+    S = torch.empty(n, device="cuda")
+    m = torch.empty(n, device="cuda")
+    ctx.source_field(torch.from_numpy(d).cuda(), 1.686, 0.7, out=S, mass_out=m)
+    check_status(ctx, B)
+    So, mo = O.source_field(d.astype(np.float64), 1.686, 0.7)
+    np.testing.assert_array_equal(m.cpu().numpy(), mo.astype(np.float32))
+    Sg = S.cpu().numpy().astype(np.float64)
+    # FP32 erfc (a few ulp) times a float mass, then one scale
+    big = So > 1e-30
+    assert np.max(np.abs(Sg[big] - So[big]) / So[big]) < 2e-6
+    assert np.max(np.abs(Sg - So)) < 1e-6 * max(So.max(), 1.0)
+
+
+# ---------------------------------------------------------------------------
 # Whole path
 # ---------------------------------------------------------------------------
 

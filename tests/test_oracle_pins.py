@@ -99,6 +99,24 @@ def test_table_interpolation_vs_analytic_inverse():
 
 
 # ----------------------------------------------------------------------------
+# Source field: Sec. 3.3, Eq. fcoll (ESF-E density)
+# ----------------------------------------------------------------------------
+
+def test_source_field_closed_forms():
+    dc, sf = 1.686, 0.7
+    d = np.array([dc, -50.0, 0.0, 3.0, -0.995, 10.0])
+    S, m = o.source_field(d, dc, sf)
+    np.testing.assert_allclose(m, [1 + dc, 0.01, 1.0, 4.0, 0.01, 11.0], rtol=1e-14)
+    raw = np.array([mi * math.erfc((dc - di) / (math.sqrt(2) * sf)) for di, mi in zip(d, m)])
+    np.testing.assert_allclose(S, raw / raw.mean(), rtol=1e-14)
+    assert abs(S.mean() - 1.0) < 1e-14
+    # at the barrier erfc(0) = 1: the raw density is the mass itself
+    assert abs(raw[0] - (1 + dc)) < 1e-14
+    # deep voids collapse nothing; a high peak collapses (almost) everything
+    assert raw[1] < 1e-300 and abs(raw[5] / m[5] - 2.0) < 1e-12
+
+
+# ----------------------------------------------------------------------------
 # Radiation kernel: Sec. 3.4.1, Eq. intensity
 # ----------------------------------------------------------------------------
 
