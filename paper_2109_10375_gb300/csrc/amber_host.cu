@@ -14,10 +14,13 @@
 #include "source.cuh"
 
 namespace amber {
+// krange: if not null, the intensities' key range is folded into it (the
+// sort's control block, reset beforehand) so the ranking needs no range pass.
 cudaError_t radiation_field_f32(int n, const float* src, float* J, void* H, const void* tw, double box, double l_mfp,
-                               unsigned int* status, cudaStream_t s, FftProfile* prof);
+                               unsigned int* status, cudaStream_t s, FftProfile* prof, SortCtrl* krange);
 cudaError_t radiation_field_f64(int n, const double* src, double* J, void* H, const void* tw, double box,
-                               double l_mfp, unsigned int* status, cudaStream_t s, FftProfile* prof);
+                               double l_mfp, unsigned int* status, cudaStream_t s, FftProfile* prof,
+                               SortCtrl* krange);
 
 // ---------------------------------------------------------------------------
 // Per-kernel timing: a pool of events recorded around launches.
@@ -385,7 +388,7 @@ int amber_radiation_field(amber_ctx* c, const float* d_src, int n, double box, d
   const Plan& p = c->plan;
   const int l = ilog2i(n);
   return cuda_status(radiation_field_f32(n, d_src, d_J, c->ws + p.off_spec, c->ws + p.off_tw32 + p.tw32_off[l], box,
-                                         l_mfp, c->status, s, &c->prof));
+                                         l_mfp, c->status, s, &c->prof, nullptr));
 }
 
 int amber_radiation_field_f64(amber_ctx* c, const double* d_src, int n, double box, double l_mfp, double* d_J,
@@ -399,7 +402,7 @@ int amber_radiation_field_f64(amber_ctx* c, const double* d_src, int n, double b
   const Plan& p = c->plan;
   const int l = ilog2i(n);
   return cuda_status(radiation_field_f64(n, d_src, d_J, c->ws + p.off_spec, c->ws + p.off_tw64 + p.tw64_off[l], box,
-                                         l_mfp, c->status, s, &c->prof));
+                                         l_mfp, c->status, s, &c->prof, nullptr));
 }
 
 int amber_rank(amber_ctx* c, const float* d_J, int64_t ncells, uint32_t* d_order, void* stream) {
@@ -461,13 +464,15 @@ int amber_solve(amber_ctx* c, const float* d_src, const float* d_mass, const amb
   const int n = p->n;
   const int64_t C = (int64_t)n * n * n;
   float* J = d_J_opt ? d_J_opt : reinterpret_cast<float*>(c->sortw.keysB);
-  cudaError_t e = radiation_field_f32(n, d_src, J, c->ws + pl.off_spec, c->ws + pl.off_tw32 + pl.tw32_off[ilog2i(n)],
-                                      p->box, p->l_mfp, c->status, s, &c->prof);
+  cudaError_t e = sort_ctrl_reset(c->sortw.ctrl, s);
+  if (e == cudaSuccess)
+    e = radiation_field_f32(n, d_src, J, c->ws + pl.off_spec, c->ws + pl.off_tw32 + pl.tw32_off[ilog2i(n)], p->box,
+                           p->l_mfp, c->status, s, &c->prof, c->sortw.ctrl);
   // the first sort pass sums the masses into the assignment's total
   unsigned long long* total = reinterpret_cast<unsigned long long*>(c->assw.ctrl);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->assw.ctrl, 0, kAssignCtrlBytes, s);
   if (e == cudaSuccess)
-    e = rank_impl<float>(c->sortw, J, C, nullptr, d_mass, nullptr, total, false, c->status, s, &c->prof,
+    e = rank_impl<float>(c->sortw, J, C, nullptr, d_mass, nullptr, total, true, c->status, s, &c->prof,
                         kSpinLimit);
   // the order and rank-order masses sit on the A or B side by pass parity
   if (e == cudaSuccess)
@@ -489,13 +494,15 @@ int amber_solve_f64(amber_ctx* c, const double* d_src, const float* d_mass, cons
   const int n = p->n;
   const int64_t C = (int64_t)n * n * n;
   double* J = d_J_opt ? d_J_opt : reinterpret_cast<double*>(c->sortw.keysB);
-  cudaError_t e = radiation_field_f64(n, d_src, J, c->ws + pl.off_spec, c->ws + pl.off_tw64 + pl.tw64_off[ilog2i(n)],
-                                      p->box, p->l_mfp, c->status, s, &c->prof);
+  cudaError_t e = sort_ctrl_reset(c->sortw.ctrl, s);
+  if (e == cudaSuccess)
+    e = radiation_field_f64(n, d_src, J, c->ws + pl.off_spec, c->ws + pl.off_tw64 + pl.tw64_off[ilog2i(n)], p->box,
+                           p->l_mfp, c->status, s, &c->prof, c->sortw.ctrl);
   // the first sort pass sums the masses into the assignment's total
   unsigned long long* total = reinterpret_cast<unsigned long long*>(c->assw.ctrl);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->assw.ctrl, 0, kAssignCtrlBytes, s);
   if (e == cudaSuccess)
-    e = rank_impl<double>(c->sortw, J, C, nullptr, d_mass, nullptr, total, false, c->status, s, &c->prof,
+    e = rank_impl<double>(c->sortw, J, C, nullptr, d_mass, nullptr, total, true, c->status, s, &c->prof,
                         kSpinLimit);
   // the order and rank-order masses sit on the A or B side by pass parity
   if (e == cudaSuccess)

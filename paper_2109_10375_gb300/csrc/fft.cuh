@@ -18,6 +18,7 @@
 #pragma once
 
 #include "common.cuh"
+#include "keys.cuh"
 
 namespace amber {
 
@@ -300,9 +301,10 @@ k_fft_r2c_x(const T* __restrict__ src, cpx<T>* __restrict__ H, int64_t nrows, in
 template <typename T, int N>
 __global__ void __launch_bounds__(xpass_threads<N>())
 k_fft_c2r_x(const cpx<T>* __restrict__ H, T* __restrict__ J, int64_t nrows, int RS,
-            const cpx<T>* __restrict__ tw, unsigned int* __restrict__ status) {
+            const cpx<T>* __restrict__ tw, unsigned int* __restrict__ status, SortCtrl* __restrict__ krange) {
   using C = FftCfg<N>;
   using L = XSmem<T, N>;
+  using K = typename KeyOf<T>::K;
   constexpr int R0 = C::R0, R1 = C::R1, E = C::E, XP = C::XP, NT = xpass_threads<N>();
   constexpr int QA = E / R0, QB = (R1 > 1) ? E / R1 : 0;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -310,18 +312,36 @@ k_fft_c2r_x(const cpx<T>* __restrict__ H, T* __restrict__ J, int64_t nrows, int 
   const int tid = threadIdx.x;
   const int64_t row0 = (int64_t)blockIdx.x * 2 * XP;
 
-  constexpr int NK = N / 2 + 1;
-  for (int idx = tid; idx < XP * NK; idx += NT) {
-    const int p = idx / NK, k = idx - p * NK;
+  // columns k < N/2 of both rows of each pair: E/2 per thread, all loads
+  // issued before any shared-memory store
+  constexpr int LPT = (XP * (N / 2)) / NT;
+  static_assert(LPT * NT == XP * (N / 2), "x-pass tile must split evenly");
+  cpx<T> A[LPT], Bv[LPT];
+#pragma unroll
+  for (int u = 0; u < LPT; ++u) {
+    const int idx = tid + u * NT;
+    const int p = idx / (N / 2), k = idx - p * (N / 2);
     const int64_t ra = row0 + 2 * p;
-    cpx<T> A = mk<T>(0, 0), B = mk<T>(0, 0);
-    if (ra + 1 < nrows) { A = H[ra * RS + k]; B = H[(ra + 1) * RS + k]; }
-    if (k == 0 || k == N / 2) {
-      sm[L::pos(p, k)] = mk<T>(A.x, B.x);
+    const bool ok = ra + 1 < nrows;
+    A[u] = ok ? H[ra * RS + k] : mk<T>(0, 0);
+    Bv[u] = ok ? H[(ra + 1) * RS + k] : mk<T>(0, 0);
+  }
+#pragma unroll
+  for (int u = 0; u < LPT; ++u) {
+    const int idx = tid + u * NT;
+    const int p = idx / (N / 2), k = idx - p * (N / 2);
+    if (k == 0) {
+      sm[L::pos(p, 0)] = mk<T>(A[u].x, Bv[u].x);
     } else {
-      sm[L::pos(p, k)] = mk<T>(A.x - B.y, A.y + B.x);
-      sm[L::pos(p, N - k)] = mk<T>(A.x + B.y, B.x - A.y);
+      sm[L::pos(p, k)] = mk<T>(A[u].x - Bv[u].y, A[u].y + Bv[u].x);
+      sm[L::pos(p, N - k)] = mk<T>(A[u].x + Bv[u].y, Bv[u].x - A[u].y);
     }
+  }
+  if (tid < XP) {  // Nyquist column k = N/2 (real parts only)
+    const int64_t ra = row0 + 2 * tid;
+    T ax = 0, bx = 0;
+    if (ra + 1 < nrows) { ax = H[ra * RS + N / 2].x; bx = H[(ra + 1) * RS + N / 2].x; }
+    sm[L::pos(tid, N / 2)] = mk<T>(ax, bx);
   }
   __syncthreads();
 
@@ -334,7 +354,14 @@ k_fft_c2r_x(const cpx<T>* __restrict__ H, T* __restrict__ J, int64_t nrows, int 
     for (int r = 0; r < R0; ++r) v[q * R0 + r] = sm[L::pos(p, j + r * (N / R0))];
     dft<R0, true>(v + q * R0);
   }
-  bool bad = false;
+  bool bad = false, nan = false;
+  K klo = ~K(0), khi = 0;
+  auto track = [&](T x) {
+    bad |= !isfinite(x);
+    const K kk = enc_desc(x, nan);
+    klo = kk < klo ? kk : klo;
+    khi = kk > khi ? kk : khi;
+  };
   if constexpr (R1 == 1) {
 #pragma unroll
     for (int q = 0; q < QA; ++q) {
@@ -346,7 +373,8 @@ k_fft_c2r_x(const cpx<T>* __restrict__ H, T* __restrict__ J, int64_t nrows, int 
         for (int r = 0; r < R0; ++r) {
           J[ra * N + r] = v[q * R0 + r].x;
           J[(ra + 1) * N + r] = v[q * R0 + r].y;
-          bad |= !isfinite(v[q * R0 + r].x) || !isfinite(v[q * R0 + r].y);
+          track(v[q * R0 + r].x);
+          track(v[q * R0 + r].y);
         }
       }
     }
@@ -378,12 +406,15 @@ k_fft_c2r_x(const cpx<T>* __restrict__ H, T* __restrict__ J, int64_t nrows, int 
           const int n = j + r * R0;
           J[ra * N + n] = v[q * R1 + r].x;
           J[(ra + 1) * N + n] = v[q * R1 + r].y;
-          bad |= !isfinite(v[q * R1 + r].x) || !isfinite(v[q * R1 + r].y);
+          track(v[q * R1 + r].x);
+          track(v[q * R1 + r].y);
         }
       }
     }
   }
   if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) raise_status(status, AMBER_ERR_NONFINITE);
+  // fold the intensities' key range into the sort's control block
+  if (krange) key_range_commit(klo, khi, krange);
 }
 
 // ---------------------------------------------------------------------------
@@ -400,7 +431,7 @@ enum ProfKind {
 
 template <typename T, int N>
 cudaError_t radiation_field_n(const T* src, T* J, cpx<T>* H, const cpx<T>* tw, double box, double l_mfp,
-                              unsigned int* status, cudaStream_t s, FftProfile* prof) {
+                              unsigned int* status, cudaStream_t s, FftProfile* prof, SortCtrl* krange) {
   using C = FftCfg<N>;
   const int RS = N / 2 + 2;
   const int ncol = N / 2 + 1;
@@ -440,7 +471,7 @@ cudaError_t radiation_field_n(const T* src, T* J, cpx<T>* H, const cpx<T>* tw, d
                                                                        kf, (T)l_mfp, norm);
   prof_end(prof, PK_FFT_Y_INV, s);
   prof_begin(prof, PK_C2R_X, s);
-  k_fft_c2r_x<T, N><<<xgrid, xpass_threads<N>(), xs, s>>>(H, J, nrows, RS, tw, status);
+  k_fft_c2r_x<T, N><<<xgrid, xpass_threads<N>(), xs, s>>>(H, J, nrows, RS, tw, status, krange);
   prof_end(prof, PK_C2R_X, s);
   return cudaGetLastError();
 }

@@ -4,19 +4,20 @@
 namespace amber {
 
 cudaError_t radiation_field_f32(int n, const float* src, float* J, void* H, const void* tw, double box, double l_mfp,
-                               unsigned int* status, cudaStream_t s, FftProfile* prof) {
+                               unsigned int* status, cudaStream_t s, FftProfile* prof,
+                               SortCtrl* krange) {
   auto* h = reinterpret_cast<cpx<float>*>(H);
   auto* w = reinterpret_cast<const cpx<float>*>(tw);
   switch (n) {
-    case 4: return radiation_field_n<float, 4>(src, J, h, w, box, l_mfp, status, s, prof);
-    case 8: return radiation_field_n<float, 8>(src, J, h, w, box, l_mfp, status, s, prof);
-    case 16: return radiation_field_n<float, 16>(src, J, h, w, box, l_mfp, status, s, prof);
-    case 32: return radiation_field_n<float, 32>(src, J, h, w, box, l_mfp, status, s, prof);
-    case 64: return radiation_field_n<float, 64>(src, J, h, w, box, l_mfp, status, s, prof);
-    case 128: return radiation_field_n<float, 128>(src, J, h, w, box, l_mfp, status, s, prof);
-    case 256: return radiation_field_n<float, 256>(src, J, h, w, box, l_mfp, status, s, prof);
-    case 512: return radiation_field_n<float, 512>(src, J, h, w, box, l_mfp, status, s, prof);
-    case 1024: return radiation_field_n<float, 1024>(src, J, h, w, box, l_mfp, status, s, prof);
+    case 4: return radiation_field_n<float, 4>(src, J, h, w, box, l_mfp, status, s, prof, krange);
+    case 8: return radiation_field_n<float, 8>(src, J, h, w, box, l_mfp, status, s, prof, krange);
+    case 16: return radiation_field_n<float, 16>(src, J, h, w, box, l_mfp, status, s, prof, krange);
+    case 32: return radiation_field_n<float, 32>(src, J, h, w, box, l_mfp, status, s, prof, krange);
+    case 64: return radiation_field_n<float, 64>(src, J, h, w, box, l_mfp, status, s, prof, krange);
+    case 128: return radiation_field_n<float, 128>(src, J, h, w, box, l_mfp, status, s, prof, krange);
+    case 256: return radiation_field_n<float, 256>(src, J, h, w, box, l_mfp, status, s, prof, krange);
+    case 512: return radiation_field_n<float, 512>(src, J, h, w, box, l_mfp, status, s, prof, krange);
+    case 1024: return radiation_field_n<float, 1024>(src, J, h, w, box, l_mfp, status, s, prof, krange);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -24,7 +24,9 @@ __global__ void __launch_bounds__(256) k_source_raw(const float* __restrict__ de
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
     const float d = delta[i];
-    const float m = 1.0f + fmaxf(d, -0.99f);
+    // 1 + max(d, -0.99) rounded once to float: 1 + d is exact before the
+    // rounding, and below the floor the value is 0.01 itself
+    const float m = fmaxf(1.0f + d, 0.01f);
     const float s = m * erfcf((delta_c - d) * inv_s2);
     S[i] = s;
     if (mass) mass[i] = m;
@@ -47,8 +49,8 @@ __global__ void __launch_bounds__(256) k_source_raw(const float* __restrict__ de
 
 __global__ void __launch_bounds__(256) k_source_scale(float* __restrict__ S, int64_t n,
                                                       const unsigned long long* __restrict__ total) {
-  const u128 T = ((u128)total[1] << 64) | (u128)total[0];
-  const float f = (float)((double)n / u128_to_double(T));
+  const u128 T = ((u128)total[1] << 64) | (u128)total[0];  // 2^-64 units
+  const float f = (float)((double)n / (u128_to_double(T) * 5.42101086242752217e-20));
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) S[i] *= f;
 }
