@@ -208,7 +208,27 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_assign(const ScanArgs a) 
   const int M = a.n_table;
 
   // bracket: cx = #{j : X_j >= M_n}; X is non-increasing in j and M_n grows
-  // along the thread's ranks, so one binary search then a short walk down.
+  // with rank.  Thread 0 brackets the whole tile (its first and last M), so
+  // each thread searches only that range once, then walks down.
+  __shared__ int s_cx[2];
+  if (tid == 0) {
+    const u128 m_first = s_excl, m_last = s_excl + tile_sum;  // M before / after the tile
+    int lo = 0, hi = M;
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (a.X[mid] >= m_first) lo = mid + 1; else hi = mid;
+    }
+    s_cx[0] = lo;
+    hi = lo;
+    lo = 0;
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (a.X[mid] >= m_last) lo = mid + 1; else hi = mid;
+    }
+    s_cx[1] = lo;
+  }
+  __syncthreads();
+  const int cx_hi = s_cx[0], cx_lo = s_cx[1];
   float zv[IT];
   uint32_t slot[IT];
   int cx = -1;
@@ -221,7 +241,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_assign(const ScanArgs a) 
     bool dummy = false;
     Mn += mass_q64(mv[i], dummy);
     if (cx < 0) {
-      int lo = 0, hi = M;
+      int lo = cx_lo, hi = cx_hi;
       while (lo < hi) {
         const int mid = (lo + hi) >> 1;
         if (a.X[mid] >= Mn) lo = mid + 1; else hi = mid;
@@ -241,7 +261,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_assign(const ScanArgs a) 
     }
     zv[i] = z;
     if (WANT_F) a.F[start + p] = u128_to_double(Mn) * invT;
-    slot[i] = atomicAdd(&scnt[cell[i] / a.bucket_w], 1u);
+    slot[i] = atomicAdd(&scnt[cell[i] >> a.bucket_shift], 1u);
   }
   __syncthreads();
   // tile-local bucket starts (exclusive scan over the buckets) and this
@@ -272,7 +292,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_assign(const ScanArgs a) 
 #pragma unroll
   for (int i = 0; i < IT; ++i) {
     if (slot[i] == 0xffffffffu) continue;
-    const uint32_t q = soff[cell[i] / a.bucket_w] + slot[i];
+    const uint32_t q = soff[cell[i] >> a.bucket_shift] + slot[i];
     scell[q + (q >> 5)] = cell[i];
     sz[q + (q >> 5)] = zv[i];
   }
@@ -310,13 +330,11 @@ __global__ void __launch_bounds__(256) k_scatter_back(const uint32_t* __restrict
 }
 
 // ---------------------------------------------------------------------------
-void bucket_plan(int64_t n, int* nbuckets, int64_t* width) {
-  // each bucket's cells span <= ~32 MB of z_re so the active bucket stays in L2
-  const int64_t target = (32ll << 20) / 4;
-  int nb = 1;
-  while ((int64_t)nb * target < n && nb < kMaxBuckets) nb *= 2;
-  *nbuckets = nb;
-  *width = (n + nb - 1) / nb;
+void bucket_plan(int64_t n, int* nbuckets, int* shift) {
+  // buckets of 2^23 consecutive cells: 32 MB of z_re each, so the active
+  // bucket stays in L2; at most 128 buckets for 2^30 cells
+  *shift = kBucketShift;
+  *nbuckets = (int)((n + ((int64_t)1 << kBucketShift) - 1) >> kBucketShift);
 }
 
 cudaError_t assign_impl(const AssignWork& w, const uint32_t* order, const float* mass, bool mass_in_rank_order,
@@ -366,9 +384,7 @@ cudaError_t assign_impl(const AssignWork& w, const uint32_t* order, const float*
   a.F = F;
   a.state = w.state;
   a.ticket = ticket;
-  int64_t bw;
-  bucket_plan(n, &a.nbuckets, &bw);
-  a.bucket_w = (uint32_t)bw;
+  bucket_plan(n, &a.nbuckets, &a.bucket_shift);
   a.bcell = w.bcell;
   a.bz = w.bz;
   a.btab = w.btab;

@@ -24,6 +24,7 @@ struct __align__(16) ScanTile {
 };
 
 constexpr int kBackTilesPerCta = 64;  // scan tiles one scatter-back CTA covers
+constexpr int kBucketShift = 23;      // 2^23 cells (32 MB of z_re) per bucket
 
 // ctrl: total mass (2 x u64) at 0, tile ticket (u32) at 16; zeroed per call
 constexpr size_t kAssignCtrlBytes = 256;
@@ -61,7 +62,7 @@ struct ScanArgs {
   ScanTile* state;
   uint32_t* ticket;
   int nbuckets;
-  uint32_t bucket_w;
+  int bucket_shift;  // bucket of a cell = cell >> bucket_shift
   uint32_t* bcell;
   float* bz;
   uint16_t* btab;
@@ -69,7 +70,7 @@ struct ScanArgs {
   unsigned int spin_limit;
 };
 
-void bucket_plan(int64_t n, int* nbuckets, int64_t* width);
+void bucket_plan(int64_t n, int* nbuckets, int* shift);
 
 // mass_in_rank_order: mass[n] belongs to rank n (sort payload) instead of to
 // cell n.  total_ready: the 128-bit mass total in w.ctrl was already summed

@@ -276,10 +276,15 @@ def test_source_field_vs_oracle(ctx, B, n):
     So, mo = O.source_field(d.astype(np.float64), 1.686, 0.7)
     np.testing.assert_array_equal(m.cpu().numpy(), mo.astype(np.float32))
     Sg = S.cpu().numpy().astype(np.float64)
-    # FP32 erfc (a few ulp) times a float mass, then one scale
+    # FP32 evaluation: erfc(x) amplifies the argument's rounding (~2u x) by
+    # |d ln erfc/dx| ~ 2x, so the relative error is ~4u(x^2 + 1) plus a few
+    # ulp for erfcf, the mass product and the scale (u = 2^-24)
+    u = 2.0 ** -24
+    x = (1.686 - d.astype(np.float64)) / (np.sqrt(2.0) * 0.7)
+    tol = 4 * u * (x * x + 1) + 8 * u
     big = So > 1e-30
-    assert np.max(np.abs(Sg[big] - So[big]) / So[big]) < 2e-6
-    assert np.max(np.abs(Sg - So)) < 1e-6 * max(So.max(), 1.0)
+    rel = np.abs(Sg - So) / np.maximum(So, 1e-300)
+    assert np.all(rel[big] <= tol[big]), float(np.max(rel[big] / tol[big]))
 
 
 # ---------------------------------------------------------------------------
