@@ -150,6 +150,39 @@ int amber_source_field(amber_ctx *ctx, const float *d_delta, int64_t ncells, dou
  * n^3 floats out with the intensity.  p->precision must be 32 here. */
 int amber_solve(amber_ctx *ctx, const float *d_src, const float *d_mass, const amber_params_t *p,
                 float *d_zre, float *d_J_opt, void *stream);
+/* amber_solve that also hands back what a parameter study reuses: the rank
+ * order (d_order_out, n^3 uint32) and the masses in rank order
+ * (d_mass_rank_out, n^3 floats), both caller-owned device buffers.  A later
+ * change of only (z_mid, dz, Az) reruns amber_assign_zre_ranked on them. */
+int amber_solve_ex(amber_ctx *ctx, const float *d_src, const float *d_mass, const amber_params_t *p,
+                   float *d_zre, float *d_J_opt, uint32_t *d_order_out, float *d_mass_rank_out, void *stream);
+
+/* amber_assign_zre with the masses already in rank order (d_mass_rank[n]
+ * belongs to the cell d_order[n]), as amber_solve_ex leaves them: the same
+ * abundance matching without the gather through the order. */
+int amber_assign_zre_ranked(amber_ctx *ctx, const uint32_t *d_order, const float *d_mass_rank, int64_t ncells,
+                            const amber_history_t *h, float *d_zre, double *d_F_opt, void *stream);
+
+/* Batched solves: one captured CUDA graph replays many amber_solve calls.
+ * Item i runs on ctxs[i % nctx], each context on its own stream forked from
+ * and joined into one origin, so small realisations overlap on the GPU and
+ * the whole batch costs one host launch.  Items are validated before the
+ * capture (same rules as amber_solve, precision 32).  The graph records the
+ * given device pointers and parameters: buffers and contexts must stay
+ * alive while the batch exists, and a context must not run other work while
+ * the batch runs. */
+typedef struct {
+  const float *d_src;
+  const float *d_mass;
+  amber_params_t params;
+  float *d_zre;
+} amber_batch_item;
+typedef struct amber_batch amber_batch;
+int amber_batch_create(amber_batch **batch, amber_ctx *const *ctxs, int nctx, const amber_batch_item *items,
+                       int nitems);
+int amber_batch_launch(amber_batch *batch, void *stream);
+int amber_batch_destroy(amber_batch *batch);
+
 /* FP64 intensity variant (p->precision == 64, n <= 256): d_src n^3 doubles,
  * d_J_opt n^3 doubles or NULL. */
 int amber_solve_f64(amber_ctx *ctx, const double *d_src, const float *d_mass, const amber_params_t *p,

@@ -29,6 +29,7 @@ EXPORTED = [
     "amber_rank_f64", "amber_assign_zre", "amber_solve", "amber_solve_f64", "amber_sync_status",
     "amber_status_string", "amber_profile_enable", "amber_profile_reset", "amber_profile_kinds",
     "amber_profile_read", "amber_sort_passes", "amber_test_wait_timeout", "amber_source_field",
+    "amber_solve_ex", "amber_assign_zre_ranked", "amber_batch_create", "amber_batch_launch", "amber_batch_destroy",
 ]
 
 
@@ -41,6 +42,10 @@ class amber_history_t(C.Structure):
 class amber_params_t(C.Structure):
     _fields_ = [("n", C.c_int), ("box", C.c_double), ("l_mfp", C.c_double),
                 ("hist", amber_history_t), ("precision", C.c_int)]
+
+
+class amber_batch_item(C.Structure):
+    _fields_ = [("d_src", C.c_void_p), ("d_mass", C.c_void_p), ("params", amber_params_t), ("d_zre", C.c_void_p)]
 
 
 class AmberError(RuntimeError):
@@ -77,6 +82,11 @@ def _load():
         "amber_profile_read": (i32, [vp, i32, C.POINTER(C.c_char_p), C.POINTER(dbl), C.POINTER(i64)]),
         "amber_sort_passes": (i32, [vp, C.POINTER(i32)]),
         "amber_source_field": (i32, [vp, vp, i64, dbl, dbl, vp, vp, vp]),
+        "amber_solve_ex": (i32, [vp, vp, vp, C.POINTER(amber_params_t), vp, vp, vp, vp, vp]),
+        "amber_assign_zre_ranked": (i32, [vp, vp, vp, i64, H, vp, vp, vp]),
+        "amber_batch_create": (i32, [C.POINTER(vp), C.POINTER(vp), i32, C.POINTER(amber_batch_item), i32]),
+        "amber_batch_launch": (i32, [vp, vp]),
+        "amber_batch_destroy": (i32, [vp]),
         "amber_test_wait_timeout": (i32, [vp, C.c_uint, vp]),
     }
     for name, (res, args) in sig.items():
@@ -136,6 +146,41 @@ def _stream(stream):
     import torch
     s = stream if stream is not None else torch.cuda.current_stream()
     return C.c_void_p(s.cuda_stream)
+
+
+def params(n: int, box: float, l_mfp: float, h: amber_history_t, precision: int = 32) -> amber_params_t:
+    p = amber_params_t()
+    p.n, p.box, p.l_mfp, p.hist, p.precision = n, box, l_mfp, h, precision
+    return p
+
+
+class Batch:
+    """One CUDA graph replaying many solves spread over several contexts."""
+
+    def __init__(self, ctxs, items):
+        """items: (S, mass, box, l_mfp, history, z_out) tuples of device tensors."""
+        self._keep = (list(ctxs), list(items))
+        arr = (amber_batch_item * len(items))()
+        for i, (S, m, box, l, h, z) in enumerate(items):
+            arr[i].d_src, arr[i].d_mass, arr[i].d_zre = S.data_ptr(), m.data_ptr(), z.data_ptr()
+            arr[i].params = params(S.shape[0], box, l, h)
+        hs = (C.c_void_p * len(ctxs))(*[c._h.value for c in ctxs])
+        self._h = C.c_void_p()
+        _check(lib.amber_batch_create(C.byref(self._h), hs, len(ctxs), arr, len(items)), "amber_batch_create")
+
+    def launch(self, stream=None):
+        _check(lib.amber_batch_launch(self._h, _stream(stream)), "amber_batch_launch")
+
+    def close(self):
+        if self._h:
+            lib.amber_batch_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Context:
@@ -213,6 +258,19 @@ class Context:
             out = torch.empty(S.shape, dtype=torch.float32, device=S.device)
         fn = lib.amber_solve_f64 if f64 else lib.amber_solve
         _check(fn(self._h, _ptr(S), _ptr(mass), C.byref(p), _ptr(out), _ptr(J_out), _stream(stream)), "amber_solve")
+        return out
+
+    def solve_ex(self, S, mass, box: float, l_mfp: float, h: amber_history_t, out, order_out, mass_rank_out,
+                 J_out=None, stream=None):
+        """Solve and keep the rank order and rank-order masses (for history-only reruns)."""
+        p = params(S.shape[0], box, l_mfp, h)
+        _check(lib.amber_solve_ex(self._h, _ptr(S), _ptr(mass), C.byref(p), _ptr(out), _ptr(J_out), _ptr(order_out),
+                                  _ptr(mass_rank_out), _stream(stream)), "amber_solve_ex")
+        return out
+
+    def assign_zre_ranked(self, order, mass_rank, h: amber_history_t, out, F=None, stream=None):
+        _check(lib.amber_assign_zre_ranked(self._h, _ptr(order), _ptr(mass_rank), order.numel(), C.byref(h),
+                                           _ptr(out), _ptr(F), _stream(stream)), "amber_assign_zre_ranked")
         return out
 
     def sync_status(self, stream=None) -> int:

@@ -451,15 +451,12 @@ static int solve_args(amber_ctx* c, const void* src, const float* mass, const am
   return history_coeffs(&p->hist, hc);
 }
 
-int amber_solve(amber_ctx* c, const float* d_src, const float* d_mass, const amber_params_t* p, float* d_zre,
-                float* d_J_opt, void* stream) {
-  HistoryCoeffs hc;
-  int st = solve_args(c, d_src, d_mass, p, d_zre, 32, c ? c->plan.n32 : 0, &hc);
-  if (st) return st;
-  std::lock_guard<std::mutex> lk(c->mu);
-  DeviceGuard g(c->device);
-  cudaStream_t s = (cudaStream_t)stream;
-  c->last_stream = s;
+// Enqueue one FP32 solve on s (no locking, no validation).  With order_out
+// (and mass_rank_out) the sort leaves the rank order and the rank-order
+// masses there for the caller; otherwise they stay in the workspace.
+static cudaError_t solve_f32_enqueue(amber_ctx* c, const float* d_src, const float* d_mass, const amber_params_t* p,
+                                     const HistoryCoeffs& hc, float* d_zre, float* d_J_opt, uint32_t* order_out,
+                                     float* mass_rank_out, cudaStream_t s) {
   const Plan& pl = c->plan;
   const int n = p->n;
   const int64_t C = (int64_t)n * n * n;
@@ -472,13 +469,148 @@ int amber_solve(amber_ctx* c, const float* d_src, const float* d_mass, const amb
   unsigned long long* total = reinterpret_cast<unsigned long long*>(c->assw.ctrl);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->assw.ctrl, 0, kAssignCtrlBytes, s);
   if (e == cudaSuccess)
-    e = rank_impl<float>(c->sortw, J, C, nullptr, d_mass, nullptr, total, true, c->status, s, &c->prof,
-                        kSpinLimit);
+    e = rank_impl<float>(c->sortw, J, C, order_out, d_mass, order_out ? mass_rank_out : nullptr, total, true,
+                         c->status, s, &c->prof, kSpinLimit);
+  if (e != cudaSuccess) return e;
+  if (order_out)
+    return assign_impl(c->assw, order_out, mass_rank_out, true, true, C, hc, d_zre, nullptr, c->status, s, &c->prof,
+                       kSpinLimit);
   // the order and rank-order masses sit on the A or B side by pass parity
-  if (e == cudaSuccess)
-    e = assign_impl(c->assw, c->sortw.idxA, c->sortw.massA, true, true, C, hc, d_zre, nullptr, c->status, s,
-                    &c->prof, kSpinLimit, c->sortw.idxB, c->sortw.massB, &c->sortw.ctrl->npasses);
-  return cuda_status(e);
+  return assign_impl(c->assw, c->sortw.idxA, c->sortw.massA, true, true, C, hc, d_zre, nullptr, c->status, s,
+                     &c->prof, kSpinLimit, c->sortw.idxB, c->sortw.massB, &c->sortw.ctrl->npasses);
+}
+
+int amber_solve(amber_ctx* c, const float* d_src, const float* d_mass, const amber_params_t* p, float* d_zre,
+                float* d_J_opt, void* stream) {
+  HistoryCoeffs hc;
+  int st = solve_args(c, d_src, d_mass, p, d_zre, 32, c ? c->plan.n32 : 0, &hc);
+  if (st) return st;
+  std::lock_guard<std::mutex> lk(c->mu);
+  DeviceGuard g(c->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  c->last_stream = s;
+  return cuda_status(solve_f32_enqueue(c, d_src, d_mass, p, hc, d_zre, d_J_opt, nullptr, nullptr, s));
+}
+
+int amber_solve_ex(amber_ctx* c, const float* d_src, const float* d_mass, const amber_params_t* p, float* d_zre,
+                   float* d_J_opt, uint32_t* d_order_out, float* d_mass_rank_out, void* stream) {
+  HistoryCoeffs hc;
+  int st = solve_args(c, d_src, d_mass, p, d_zre, 32, c ? c->plan.n32 : 0, &hc);
+  if (st) return st;
+  if (!d_order_out || !d_mass_rank_out) return AMBER_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(c->mu);
+  DeviceGuard g(c->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  c->last_stream = s;
+  return cuda_status(solve_f32_enqueue(c, d_src, d_mass, p, hc, d_zre, d_J_opt, d_order_out, d_mass_rank_out, s));
+}
+
+int amber_assign_zre_ranked(amber_ctx* c, const uint32_t* d_order, const float* d_mass_rank, int64_t ncells,
+                            const amber_history_t* h, float* d_zre, double* d_F_opt, void* stream) {
+  if (!c || !d_order || !d_mass_rank || !d_zre || ncells < 1) return AMBER_ERR_INVALID_ARG;
+  if (ncells > c->max_cells) return AMBER_ERR_CAPACITY;
+  HistoryCoeffs hc;
+  const int st = history_coeffs(h, &hc);
+  if (st) return st;
+  std::lock_guard<std::mutex> lk(c->mu);
+  DeviceGuard g(c->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  c->last_stream = s;
+  return cuda_status(assign_impl(c->assw, d_order, d_mass_rank, true, false, ncells, hc, d_zre, d_F_opt, c->status,
+                                 s, &c->prof, kSpinLimit));
+}
+
+// ---------------------------------------------------------------------------
+// Batched solves replayed from one captured CUDA graph.
+// ---------------------------------------------------------------------------
+struct amber_batch {
+  int device = 0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  std::vector<amber_ctx*> ctxs;
+};
+
+int amber_batch_create(amber_batch** out, amber_ctx* const* ctxs, int nctx, const amber_batch_item* items,
+                       int nitems) {
+  if (!out || !ctxs || nctx < 1 || !items || nitems < 1) return AMBER_ERR_INVALID_ARG;
+  *out = nullptr;
+  std::vector<HistoryCoeffs> hcs(nitems);
+  const int dev = ctxs[0] ? ctxs[0]->device : -1;
+  for (int k = 0; k < nctx; ++k)
+    if (!ctxs[k] || ctxs[k]->device != dev) return AMBER_ERR_INVALID_ARG;
+  for (int i = 0; i < nitems; ++i) {
+    amber_ctx* c = ctxs[i % nctx];
+    const int st = solve_args(c, items[i].d_src, items[i].d_mass, &items[i].params, items[i].d_zre, 32, c->plan.n32,
+                              &hcs[i]);
+    if (st) return st;
+  }
+  std::vector<std::unique_lock<std::mutex>> locks;
+  for (int k = 0; k < nctx; ++k) locks.emplace_back(ctxs[k]->mu);
+  DeviceGuard g(dev);
+  amber_batch* b = new (std::nothrow) amber_batch();
+  if (!b) return AMBER_ERR_OOM;
+  b->device = dev;
+  b->ctxs.assign(ctxs, ctxs + nctx);
+  std::vector<bool> prof_on(nctx);
+  for (int k = 0; k < nctx; ++k) { prof_on[k] = ctxs[k]->prof.on; ctxs[k]->prof.on = false; }
+  cudaStream_t origin = nullptr;
+  std::vector<cudaStream_t> ws(nctx, nullptr);
+  std::vector<cudaEvent_t> ev(nctx + 1, nullptr);
+  cudaError_t e = cudaStreamCreateWithFlags(&origin, cudaStreamNonBlocking);
+  for (int k = 0; k < nctx && e == cudaSuccess; ++k) e = cudaStreamCreateWithFlags(&ws[k], cudaStreamNonBlocking);
+  for (int k = 0; k <= nctx && e == cudaSuccess; ++k) e = cudaEventCreateWithFlags(&ev[k], cudaEventDisableTiming);
+  bool capturing = false;
+  if (e == cudaSuccess) {
+    e = cudaStreamBeginCapture(origin, cudaStreamCaptureModeRelaxed);
+    capturing = e == cudaSuccess;
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(ev[nctx], origin);
+  for (int k = 0; k < nctx && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(ws[k], ev[nctx], 0);
+  for (int i = 0; i < nitems && e == cudaSuccess; ++i) {
+    const int k = i % nctx;
+    e = solve_f32_enqueue(ctxs[k], items[i].d_src, items[i].d_mass, &items[i].params, hcs[i], items[i].d_zre, nullptr,
+                          nullptr, nullptr, ws[k]);
+  }
+  for (int k = 0; k < nctx && e == cudaSuccess; ++k) {
+    e = cudaEventRecord(ev[k], ws[k]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(origin, ev[k], 0);
+  }
+  if (capturing) {
+    const cudaError_t e2 = cudaStreamEndCapture(origin, &b->graph);
+    if (e == cudaSuccess) e = e2;
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+  for (int k = 0; k < nctx; ++k) ctxs[k]->prof.on = prof_on[k];
+  for (auto x : ev) if (x) cudaEventDestroy(x);
+  for (auto x : ws) if (x) cudaStreamDestroy(x);
+  if (origin) cudaStreamDestroy(origin);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    delete b;
+    return AMBER_ERR_CUDA;
+  }
+  *out = b;
+  return AMBER_OK;
+}
+
+int amber_batch_launch(amber_batch* b, void* stream) {
+  if (!b) return AMBER_ERR_INVALID_ARG;
+  DeviceGuard g(b->device);
+  for (auto* c : b->ctxs) c->last_stream = (cudaStream_t)stream;
+  return cuda_status(cudaGraphLaunch(b->exec, (cudaStream_t)stream));
+}
+
+int amber_batch_destroy(amber_batch* b) {
+  if (!b) return AMBER_ERR_INVALID_ARG;
+  {
+    DeviceGuard g(b->device);
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+  }
+  delete b;
+  return AMBER_OK;
 }
 
 int amber_solve_f64(amber_ctx* c, const double* d_src, const float* d_mass, const amber_params_t* p, float* d_zre,

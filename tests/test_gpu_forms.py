@@ -1,0 +1,131 @@
+"""Batched (graph-captured) and cached-rerun forms of the path (needs a GB300).
+
+Each form must reproduce the plain amber_solve result: the kernels are
+deterministic, so results are compared bit for bit, and one case per form is
+also checked against the FP64 oracle.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import amber_oracle as O
+from paper_2109_10375_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def B():
+    import __graft_entry__ as g
+    g.build()
+    from paper_2109_10375_gb300 import binding
+    return binding
+
+
+def test_solve_ex_keeps_order_and_rank_masses(B):
+    n, box, l = 64, 100.0, 3.0
+    S, m = synth.realisation(n, box, 3)
+    h = B.history(8.0, 4.0, 3.0)
+    with B.Context(n ** 3) as ctx:
+        Sd, md = S.cuda(), m.cuda()
+        J = torch.empty_like(Sd)
+        z1 = ctx.solve(Sd, md, box, l, h, J_out=J)
+        order = torch.empty(n ** 3, dtype=torch.int32, device="cuda")
+        mrank = torch.empty(n ** 3, device="cuda")
+        z2 = torch.empty_like(Sd)
+        ctx.solve_ex(Sd, md, box, l, h, z2, order, mrank)
+        assert ctx.sync_status() == 0
+        assert torch.equal(z1, z2)
+        o = order.cpu().numpy().astype(np.int64)
+        np.testing.assert_array_equal(o, np.argsort(-J.cpu().numpy().reshape(-1), kind="stable"))
+        np.testing.assert_array_equal(mrank.cpu().numpy(), m.numpy().reshape(-1)[o])
+
+
+def test_history_only_rerun_from_cached_order(B):
+    n, box, l = 64, 100.0, 3.0
+    S, m = synth.realisation(n, box, 4)
+    with B.Context(n ** 3) as ctx:
+        Sd, md = S.cuda(), m.cuda()
+        order = torch.empty(n ** 3, dtype=torch.int32, device="cuda")
+        mrank = torch.empty(n ** 3, device="cuda")
+        z = torch.empty_like(Sd)
+        ctx.solve_ex(Sd, md, box, l, B.history(8.0, 4.0, 3.0), z, order, mrank)
+        for hist in [(7.0, 3.0, 2.0), (9.0, 5.0, 4.0), (6.5, 6.0, 1.5)]:
+            h = B.history(*hist)
+            z_hit = ctx.assign_zre_ranked(order, mrank, h, torch.empty(n ** 3, device="cuda"))
+            z_full = ctx.solve(Sd, md, box, l, h)
+            assert ctx.sync_status() == 0
+            assert torch.equal(z_hit, z_full.reshape(-1))
+            zo = O.assign_zre(order.cpu().numpy().astype(np.int64), m.double().numpy().reshape(-1),
+                              O.history_table(*hist))
+            assert np.max(np.abs(z_hit.cpu().numpy() - zo)) < 5e-5
+
+
+def test_batch_graph_matches_individual_solves(B):
+    rng = np.random.default_rng(5)
+    specs = [(32, 50.0)] * 5 + [(64, 100.0)] * 3 + [(128, 100.0)] * 2
+    items, ref = [], []
+    ctxs = [B.Context(128 ** 3) for _ in range(3)]
+    try:
+        for i, (n, box) in enumerate(specs):
+            S, m = synth.realisation(n, box, 100 + i, device="cuda")
+            l = float(rng.uniform(1, 20))
+            hist = (float(rng.uniform(6.5, 9)), float(rng.uniform(2, 6)), float(rng.uniform(1.5, 5)))
+            h = B.history(*hist)
+            z = torch.full_like(S, -1.0)
+            items.append((S, m, box, l, h, z))
+            ref.append(ctxs[0].solve(S, m, box, l, h))
+        assert ctxs[0].sync_status() == 0
+        batch = B.Batch(ctxs, items)
+        for rep in range(2):  # replays give the same answer
+            for it in items:
+                it[5].fill_(-1.0)
+            batch.launch()
+            torch.cuda.synchronize()
+            for c in ctxs:
+                assert c.sync_status() == 0
+            for it, r in zip(items, ref):
+                assert torch.equal(it[5], r)
+        # one item against the oracle
+        S, m, box, l, h, z = items[-1]
+        hist = (h.z_mid, h.dz, h.Az)
+        _, _, zo = O.solve(S.double().cpu().numpy(), m.double().cpu().numpy(), box, l, *hist)
+        assert np.mean(np.abs(z.cpu().numpy().reshape(-1) - zo) > 1e-3) <= 1e-4
+        batch.close()
+    finally:
+        for c in ctxs:
+            c.close()
+
+
+def test_serving_results_same_alone_and_in_the_mix(B):
+    from paper_2109_10375_gb300 import serve
+    reqs = serve.poisson_requests(40, rate=2000.0, seed=11, sizes=(32, 64), size_p=(0.5, 0.5), n_realisations=4)
+
+    def clone(qs):
+        return [serve.Request(q.rid, q.arrival, q.realisation, q.n, q.l_mfp, q.delta_c, q.history) for q in qs]
+
+    alone = clone(reqs)
+    srv = serve.Server(n_slots=1, max_n=64, cache_bytes=1e9, hbm_reserve=0, keep_outputs=True)
+    srv.prepare(alone)
+    for q in alone:  # one at a time, nothing else on the GPU
+        srv.run([q], realtime=False)
+    srv.close()
+    mix = clone(reqs)
+    srv = serve.Server(n_slots=4, max_n=64, cache_bytes=1e9, hbm_reserve=0, keep_outputs=True)
+    srv.prepare(mix)
+    srv.run(mix, realtime=True)
+    stats = serve.summarize(mix)
+    srv.close()
+    assert stats["hit_rate"] > 0.3
+    overlapped = sum(1 for a in mix for b in mix if a is not b and a.start < b.done and b.start < a.done)
+    assert overlapped > 0  # requests really ran concurrently
+    for a, b in zip(alone, mix):
+        assert torch.equal(a.z, b.z), a.rid
+    # one request against the oracle
+    q = mix[-1]
+    box = serve.BOX_PER_CELL.get(q.n, 100.0 / 128) * q.n
+    from paper_2109_10375_gb300 import synth as sy
+    d = sy.gaussian_density(q.n, box, 1000 + q.realisation).float().double().numpy()
+    So, mo = O.source_field(d, q.delta_c, 0.7)
+    _, _, zo = O.solve(So, mo, box, q.l_mfp, *q.history)
+    assert np.mean(np.abs(q.z.cpu().numpy().reshape(-1) - zo) > 1e-3) <= 1e-3
