@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <utility>
 
 #include "../../include/amber.h"
@@ -110,6 +111,15 @@ __device__ __forceinline__ void dft(cpx<T>* v) {
     }
     bitrev_permute<R, T>(v, std::make_integer_sequence<int, R>{});
   }
+}
+
+// True the first time it is called with a given device current (per flag):
+// kernel attributes such as the dynamic shared-memory limit are set per device.
+inline bool first_use_on_device(std::atomic<unsigned long long>& mask) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const unsigned long long bit = 1ull << (dev & 63);
+  return (mask.fetch_or(bit) & bit) == 0;
 }
 
 // ---------------------------------------------------------------------------

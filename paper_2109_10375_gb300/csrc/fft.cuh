@@ -440,14 +440,13 @@ cudaError_t radiation_field_n(const T* src, T* J, cpx<T>* H, const cpx<T>* tw, d
   const T norm = (T)(1.0 / ((double)N * N * N));
   const size_t xs = XSmem<T, N>::elems * sizeof(cpx<T>);
   const size_t ss = StridedSmem<T, N>::elems * sizeof(cpx<T>);
-  static bool attr_done = false;  // per instantiation; device-independent attribute
-  if (!attr_done) {
+  static std::atomic<unsigned long long> attr_done{0};  // per instantiation and device
+  if (first_use_on_device(attr_done)) {
     cudaFuncSetAttribute(k_fft_r2c_x<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xs);
     cudaFuncSetAttribute(k_fft_c2r_x<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xs);
     cudaFuncSetAttribute(k_fft_strided<T, N, PASS_FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss);
     cudaFuncSetAttribute(k_fft_strided<T, N, PASS_INV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss);
     cudaFuncSetAttribute(k_fft_strided<T, N, PASS_CONV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss);
-    attr_done = true;
   }
   const int xgrid = (int)((nrows / 2 + C::XP - 1) / C::XP);
   const int ntx = (ncol + C::SB - 1) / C::SB;

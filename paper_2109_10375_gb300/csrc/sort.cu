@@ -380,11 +380,9 @@ size_t sort_lookback_words(int64_t n) { return (size_t)sort_tiles(n) * kMaxRadix
 template <typename SRC, bool FIRST, bool MASS>
 static void launch_pass(const PassArgs& a, int64_t tiles, cudaStream_t s) {
   const size_t smem = pass_smem<SRC>(MASS);
-  static bool attr = false;
-  if (!attr) {
+  static std::atomic<unsigned long long> attr{0};  // per instantiation and device
+  if (first_use_on_device(attr))
     cudaFuncSetAttribute(k_sort_pass<SRC, FIRST, MASS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    attr = true;
-  }
   k_sort_pass<SRC, FIRST, MASS><<<(unsigned)tiles, kSortThreads, smem, s>>>(a);
 }
 
