@@ -215,6 +215,28 @@ int amber_sort_passes(amber_ctx *ctx, int *out_passes);
  * latches AMBER_ERR_DEVICE_TIMEOUT.  No fault, no trap: the kernel returns. */
 int amber_test_wait_timeout(amber_ctx *ctx, unsigned int spin_limit, void *stream);
 
+/* Ranking without any device allocation, for callers that cannot allocate:
+ * a plug-in inside a framework that owns the whole device pool, a real-time
+ * loop that must never reach cudaMalloc (it can synchronise the device), or a
+ * process whose memory is already handed out.  The paper has no counterpart;
+ * this is an operational variant of amber_rank (same result, same order,
+ * same tie rule) that needs no context.
+ *  - Scratch: one fixed array of about 17 MB compiled into the library and
+ *    held on every GPU that loads it until the process exits; it fits
+ *    ncells <= 2^20.  Larger ncells return AMBER_ERR_CAPACITY and enqueue
+ *    nothing.
+ *  - The first call on each device (that device current) looks up the
+ *    array's device address; make that first call before any stream capture.
+ *  - Every call shares the one array and clears what must start at zero; calls
+ *    whose GPU work overlaps (other streams, other threads) race and must not
+ *    be issued.  Runs on the current device, asynchronously on `stream`.
+ *  - d_J: ncells floats; d_order: ncells uint32 out (caller-owned device
+ *    memory); d_status_opt: a caller-owned device word into which device errors
+ *    (AMBER_ERR_NONFINITE, AMBER_ERR_DEVICE_TIMEOUT) are ORed, or NULL to
+ *    drop them.  No cudaMalloc, cudaFree or allocating library call. */
+int amber_rank_noalloc(const float *d_J, int64_t ncells, uint32_t *d_order, unsigned int *d_status_opt,
+                       void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -30,6 +30,7 @@ EXPORTED = [
     "amber_status_string", "amber_profile_enable", "amber_profile_reset", "amber_profile_kinds",
     "amber_profile_read", "amber_sort_passes", "amber_test_wait_timeout", "amber_source_field",
     "amber_solve_ex", "amber_assign_zre_ranked", "amber_batch_create", "amber_batch_launch", "amber_batch_destroy",
+    "amber_rank_noalloc",
 ]
 
 
@@ -87,6 +88,7 @@ def _load():
         "amber_batch_create": (i32, [C.POINTER(vp), C.POINTER(vp), i32, C.POINTER(amber_batch_item), i32]),
         "amber_batch_launch": (i32, [vp, vp]),
         "amber_batch_destroy": (i32, [vp]),
+        "amber_rank_noalloc": (i32, [vp, i64, vp, vp, vp]),
         "amber_test_wait_timeout": (i32, [vp, C.c_uint, vp]),
     }
     for name, (res, args) in sig.items():
