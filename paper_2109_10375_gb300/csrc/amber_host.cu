@@ -155,7 +155,7 @@ struct Plan {
   int n32 = 0, n64 = 0;
   int64_t cells64 = 0;
   size_t off_spec, off_keysA, off_keysB, off_idxA, off_idxB, off_massA, off_massB, off_lb, off_sctrl, off_actrl, off_X, off_invdx,
-      off_state, off_btab, off_status, off_srcsum, off_tw32, off_tw64, total;
+      off_state, off_btab, off_tilemass, off_status, off_srcsum, off_tw32, off_tw64, total;
   size_t tw32_off[11] = {}, tw64_off[11] = {};
 };
 
@@ -188,6 +188,7 @@ static Plan make_plan(int64_t max_cells) {
   p.off_invdx = take((size_t)kMaxTable * sizeof(float));
   p.off_state = take(stt);
   p.off_btab = take((size_t)((max_cells + kScanTile - 1) / kScanTile) * (kMaxBuckets + 1) * sizeof(uint16_t));
+  p.off_tilemass = take((size_t)sort_tiles(max_cells) * 16);
   p.off_status = take(256);
   p.off_srcsum = take(256);
   size_t tw32 = 0, tw64 = 0;
@@ -438,7 +439,7 @@ int amber_assign_zre(amber_ctx* c, const uint32_t* d_order, const float* d_mass,
   DeviceGuard g(c->device);
   cudaStream_t s = (cudaStream_t)stream;
   c->last_stream = s;
-  return cuda_status(assign_impl(c->assw, d_order, d_mass, false, false, ncells, hc, d_zre, d_F_opt, c->status, s,
+  return cuda_status(assign_impl(c->assw, d_order, d_mass, false, nullptr, ncells, hc, d_zre, d_F_opt, c->status, s,
                                  &c->prof, kSpinLimit));
 }
 
@@ -465,18 +466,17 @@ static cudaError_t solve_f32_enqueue(amber_ctx* c, const float* d_src, const flo
   if (e == cudaSuccess)
     e = radiation_field_f32(n, d_src, J, c->ws + pl.off_spec, c->ws + pl.off_tw32 + pl.tw32_off[ilog2i(n)], p->box,
                            p->l_mfp, c->status, s, &c->prof, c->sortw.ctrl);
-  // the first sort pass sums the masses into the assignment's total
-  unsigned long long* total = reinterpret_cast<unsigned long long*>(c->assw.ctrl);
-  if (e == cudaSuccess) e = cudaMemsetAsync(c->assw.ctrl, 0, kAssignCtrlBytes, s);
+  // the first sort pass sums each tile's masses; the thresholds kernel adds them
+  unsigned long long* tile_mass = reinterpret_cast<unsigned long long*>(c->ws + pl.off_tilemass);
   if (e == cudaSuccess)
-    e = rank_impl<float>(c->sortw, J, C, order_out, d_mass, order_out ? mass_rank_out : nullptr, total, true,
+    e = rank_impl<float>(c->sortw, J, C, order_out, d_mass, order_out ? mass_rank_out : nullptr, tile_mass, true,
                          c->status, s, &c->prof, kSpinLimit);
   if (e != cudaSuccess) return e;
   if (order_out)
-    return assign_impl(c->assw, order_out, mass_rank_out, true, true, C, hc, d_zre, nullptr, c->status, s, &c->prof,
-                       kSpinLimit);
+    return assign_impl(c->assw, order_out, mass_rank_out, true, tile_mass, C, hc, d_zre, nullptr, c->status, s,
+                       &c->prof, kSpinLimit);
   // the order and rank-order masses sit on the A or B side by pass parity
-  return assign_impl(c->assw, c->sortw.idxA, c->sortw.massA, true, true, C, hc, d_zre, nullptr, c->status, s,
+  return assign_impl(c->assw, c->sortw.idxA, c->sortw.massA, true, tile_mass, C, hc, d_zre, nullptr, c->status, s,
                      &c->prof, kSpinLimit, c->sortw.idxB, c->sortw.massB, &c->sortw.ctrl->npasses);
 }
 
@@ -516,7 +516,7 @@ int amber_assign_zre_ranked(amber_ctx* c, const uint32_t* d_order, const float* 
   DeviceGuard g(c->device);
   cudaStream_t s = (cudaStream_t)stream;
   c->last_stream = s;
-  return cuda_status(assign_impl(c->assw, d_order, d_mass_rank, true, false, ncells, hc, d_zre, d_F_opt, c->status,
+  return cuda_status(assign_impl(c->assw, d_order, d_mass_rank, true, nullptr, ncells, hc, d_zre, d_F_opt, c->status,
                                  s, &c->prof, kSpinLimit));
 }
 
@@ -630,15 +630,13 @@ int amber_solve_f64(amber_ctx* c, const double* d_src, const float* d_mass, cons
   if (e == cudaSuccess)
     e = radiation_field_f64(n, d_src, J, c->ws + pl.off_spec, c->ws + pl.off_tw64 + pl.tw64_off[ilog2i(n)], p->box,
                            p->l_mfp, c->status, s, &c->prof, c->sortw.ctrl);
-  // the first sort pass sums the masses into the assignment's total
-  unsigned long long* total = reinterpret_cast<unsigned long long*>(c->assw.ctrl);
-  if (e == cudaSuccess) e = cudaMemsetAsync(c->assw.ctrl, 0, kAssignCtrlBytes, s);
+  unsigned long long* tile_mass = reinterpret_cast<unsigned long long*>(c->ws + pl.off_tilemass);
   if (e == cudaSuccess)
-    e = rank_impl<double>(c->sortw, J, C, nullptr, d_mass, nullptr, total, true, c->status, s, &c->prof,
-                        kSpinLimit);
+    e = rank_impl<double>(c->sortw, J, C, nullptr, d_mass, nullptr, tile_mass, true, c->status, s, &c->prof,
+                          kSpinLimit);
   // the order and rank-order masses sit on the A or B side by pass parity
   if (e == cudaSuccess)
-    e = assign_impl(c->assw, c->sortw.idxA, c->sortw.massA, true, true, C, hc, d_zre, nullptr, c->status, s,
+    e = assign_impl(c->assw, c->sortw.idxA, c->sortw.massA, true, tile_mass, C, hc, d_zre, nullptr, c->status, s,
                     &c->prof, kSpinLimit, c->sortw.idxB, c->sortw.massB, &c->sortw.ctrl->npasses);
   return cuda_status(e);
 }

@@ -19,6 +19,7 @@
 // only the final interpolation weight is rounded (FP32).
 #include "assign.cuh"
 #include "fixed128.cuh"
+#include "sort.cuh"
 
 namespace amber {
 
@@ -71,10 +72,35 @@ __device__ __forceinline__ u128 mul_floor(double x, u128 T) {
   return (top << (64 - s)) | (u128)(p0 >> s);
 }
 
-__global__ void __launch_bounds__(256) k_thresholds(const unsigned long long* __restrict__ total, int M,
-                                                    double a_w, double b_w, double c_w, double z_lo, double z_hi,
-                                                    u128* __restrict__ X, float* __restrict__ inv_dx) {
-  const u128 T = ((u128)total[1] << 64) | (u128)total[0];
+// tile_mass (optional): per-tile partial sums from the ranking; their total
+// is formed here (exact, order-free) and stored as the mass total.
+__global__ void __launch_bounds__(1024) k_thresholds(unsigned long long* __restrict__ total,
+                                                     const unsigned long long* __restrict__ tile_mass,
+                                                     int64_t ntiles, int M, double a_w, double b_w, double c_w,
+                                                     double z_lo, double z_hi, u128* __restrict__ X,
+                                                     float* __restrict__ inv_dx) {
+  __shared__ u128 ws[32];
+  __shared__ u128 sT;
+  if (tile_mass) {
+    u128 acc = 0;
+    for (int64_t t = threadIdx.x; t < ntiles; t += blockDim.x)
+      acc += ((u128)tile_mass[2 * t + 1] << 64) | (u128)tile_mass[2 * t];
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) acc += shfl_down_u128(acc, o);
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      u128 s = 0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += ws[w];
+      total[0] = (unsigned long long)s;
+      total[1] = (unsigned long long)(s >> 64);
+      sT = s;
+    }
+  } else if (threadIdx.x == 0) {
+    sT = ((u128)total[1] << 64) | (u128)total[0];
+  }
+  __syncthreads();
+  const u128 T = sT;
   for (int j = threadIdx.x; j < M; j += blockDim.x) {
     const double z = z_lo + (z_hi - z_lo) * (double)j / (double)(M - 1);
     const double u = fmax((z - a_w) / b_w, 0.0);
@@ -338,24 +364,19 @@ void bucket_plan(int64_t n, int* nbuckets, int* shift) {
 }
 
 cudaError_t assign_impl(const AssignWork& w, const uint32_t* order, const float* mass, bool mass_in_rank_order,
-                        bool total_ready, int64_t n, const HistoryCoeffs& hc, float* zre, double* F,
+                        const unsigned long long* tile_mass, int64_t n, const HistoryCoeffs& hc, float* zre, double* F,
                         unsigned int* status, cudaStream_t s, FftProfile* prof, unsigned int spin_limit,
                         const uint32_t* order_b, const float* mass_b, const int* pick) {
   const int64_t tiles = (n + kScanTile - 1) / kScanTile;
   cudaError_t e;
   unsigned long long* total = reinterpret_cast<unsigned long long*>(w.ctrl);
   uint32_t* ticket = reinterpret_cast<uint32_t*>(w.ctrl + 16);
-  if (!total_ready) {
-    e = cudaMemsetAsync(w.ctrl, 0, kAssignCtrlBytes, s);
-    if (e != cudaSuccess) return e;
-  } else {
-    e = cudaMemsetAsync(w.ctrl + 16, 0, kAssignCtrlBytes - 16, s);  // keep the total
-    if (e != cudaSuccess) return e;
-  }
+  e = cudaMemsetAsync(w.ctrl, 0, kAssignCtrlBytes, s);
+  if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(w.state, 0, (size_t)tiles * sizeof(ScanTile), s);
   if (e != cudaSuccess) return e;
 
-  if (!total_ready) {
+  if (!tile_mass) {  // masses in cell order: one exact reduction pass
     prof_begin(prof, PK_MASS_REDUCE, s);
     int grid = (int)std::min<int64_t>((n / 4 + 255) / 256, (int64_t)w.num_sms * 8);
     if (grid < 1) grid = 1;
@@ -364,7 +385,8 @@ cudaError_t assign_impl(const AssignWork& w, const uint32_t* order, const float*
   }
 
   prof_begin(prof, PK_THRESHOLDS, s);
-  k_thresholds<<<1, 256, 0, s>>>(total, hc.n_table, hc.a, hc.b, hc.c, hc.z_lo, hc.z_hi, w.X, w.inv_dx);
+  k_thresholds<<<1, 1024, 0, s>>>(total, tile_mass, tile_mass ? sort_tiles(n) : 0, hc.n_table, hc.a, hc.b, hc.c,
+                                   hc.z_lo, hc.z_hi, w.X, w.inv_dx);
   prof_end(prof, PK_THRESHOLDS, s);
 
   ScanArgs a;

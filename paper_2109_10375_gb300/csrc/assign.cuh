@@ -73,11 +73,11 @@ struct ScanArgs {
 void bucket_plan(int64_t n, int* nbuckets, int* shift);
 
 // mass_in_rank_order: mass[n] belongs to rank n (sort payload) instead of to
-// cell n.  total_ready: the 128-bit mass total in w.ctrl was already summed
-// (by the first sort pass) and must be kept.
+// cell n.  tile_mass: per-tile partial mass sums from the ranking (summed in
+// the thresholds kernel); null means one reduction pass over mass.
 // order_b/mass_b/pick: see ScanArgs (null for a caller-given order).
 cudaError_t assign_impl(const AssignWork& w, const uint32_t* order, const float* mass, bool mass_in_rank_order,
-                        bool total_ready, int64_t n, const HistoryCoeffs& hc, float* zre, double* F,
+                        const unsigned long long* tile_mass, int64_t n, const HistoryCoeffs& hc, float* zre, double* F,
                         unsigned int* status, cudaStream_t s, FftProfile* prof, unsigned int spin_limit,
                         const uint32_t* order_b = nullptr, const float* mass_b = nullptr, const int* pick = nullptr);
 

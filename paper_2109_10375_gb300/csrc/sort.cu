@@ -24,7 +24,7 @@
 //
 // The whole-path variant carries the cell mass as a second payload, so the
 // abundance matching reads masses in rank order without a random gather; its
-// first pass also sums the masses (exact 128-bit fixed point).
+// first pass also sums each tile's masses (exact 128-bit fixed point).
 //
 // Keys: descending float order maps to ascending uint32 (uint64 for double)
 // by flipping; -0.0 is folded into +0.0 and NaN latches AMBER_ERR_NONFINITE.
@@ -168,7 +168,7 @@ __global__ void __launch_bounds__(256) k_sort_offsets(SortCtrl* __restrict__ ctr
 // ---------------------------------------------------------------------------
 // One digit pass.  FIRST: keys come from the intensities (encoded, minus the
 // minimum key), payload = cell index, and (MASS) masses are read in cell
-// order, summed into mass_total and checked.  The last needed pass writes
+// order, summed per tile into tile_mass and checked.  The last needed pass writes
 // only the payloads (to the final arrays).
 // ---------------------------------------------------------------------------
 template <typename SRC, bool FIRST, bool MASS>
@@ -189,6 +189,7 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_sort_pass(const PassArgs a)
   uint32_t* gbase = dstart + R;                                              // [R]
   __shared__ uint32_t s_tile;
   __shared__ uint32_t wsum[NW];
+  __shared__ u128 wmass[NW];
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (tid == 0) s_tile = atomicAdd(&a.ctrl->ticket[a.pass], 1u);
@@ -298,7 +299,7 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_sort_pass(const PassArgs a)
   if constexpr (FIRST && MASS) {
 #pragma unroll
     for (int o = 16; o >= 1; o >>= 1) msum += shfl_down_u128(msum, o);
-    if (lane == 0 && msum != 0) atomic_add_u128(a.mass_total, msum);
+    if (lane == 0) wmass[warp] = msum;  // summed per tile after the next barrier
   }
 
   // ---- decoupled look-back per digit, kLookWindow predecessors per round
@@ -342,6 +343,15 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_sort_pass(const PassArgs a)
     gbase[d] = a.ctrl->offs[a.pass * R + d] + excl - dstart[d];
   }
   __syncthreads();
+  if constexpr (FIRST && MASS) {
+    if (tid == 0) {
+      u128 t = 0;
+#pragma unroll
+      for (int w = 0; w < NW; ++w) t += wmass[w];
+      a.tile_mass[2 * (int64_t)tile] = (unsigned long long)t;
+      a.tile_mass[2 * (int64_t)tile + 1] = (unsigned long long)(t >> 64);
+    }
+  }
 
   // ---- write out: consecutive positions of one digit go to consecutive addresses
   const int cnt_tile = (int)(n - start < (int64_t)kTile ? n - start : (int64_t)kTile);
@@ -394,7 +404,7 @@ cudaError_t sort_ctrl_reset(SortCtrl* ctrl, cudaStream_t s) {
 
 template <typename SRC>
 cudaError_t rank_impl(const SortWork& w, const SRC* J, int64_t n, uint32_t* order, const float* mass_in,
-                      float* mass_out, unsigned long long* mass_total, bool range_ready, unsigned int* status,
+                      float* mass_out, unsigned long long* tile_mass, bool range_ready, unsigned int* status,
                       cudaStream_t s, FftProfile* prof, unsigned int spin_limit) {
   using K = typename KeyOf<SRC>::K;
   constexpr int R = 1 << KeyOf<SRC>::RB, P = max_passes<SRC>();
@@ -441,7 +451,7 @@ cudaError_t rank_impl(const SortWork& w, const SRC* J, int64_t n, uint32_t* orde
     a.lb = (p & 1) ? lbB : lbA;
     a.lb_next = (p == P - 1) ? nullptr : ((p & 1) ? lbA : lbB);
     a.ctrl = ctrl;
-    a.mass_total = mass_total;
+    a.tile_mass = tile_mass;
     a.status = status;
     a.spin_limit = spin_limit;
     prof_begin(prof, PK_SORT_PASS, s);

@@ -45,7 +45,7 @@ struct PassArgs {
   uint32_t* lb;
   uint32_t* lb_next;
   SortCtrl* ctrl;
-  unsigned long long* mass_total;  // first pass with masses: 128-bit sum (lo, hi)
+  unsigned long long* tile_mass;   // first pass with masses: per-tile 128-bit sums (lo, hi)
   unsigned int* status;
   unsigned int spin_limit;
 };
@@ -56,14 +56,15 @@ cudaError_t sort_ctrl_reset(SortCtrl* ctrl, cudaStream_t s);
 
 // Stable descending rank of J into order.  With mass_in != NULL the masses
 // ride along as a payload: mass_out receives them in rank order and
-// mass_total (zeroed by the caller) their exact 128-bit sum.  With order (and
+// tile_mass[2t], [2t+1] the exact 128-bit sum of tile t's masses (no atomics;
+// the abundance matching adds the sort_tiles(n) partials).  With order (and
 // mass_out) NULL the results stay in idxA/massA when the needed pass count
 // is odd and in idxB/massB when it is even (read it from ctrl->npasses).  range_ready:
 // ctrl was reset and its key range already folded in (by the intensity
 // kernel), so the range pass is skipped.
 template <typename SRC>
 cudaError_t rank_impl(const SortWork& w, const SRC* J, int64_t n, uint32_t* order, const float* mass_in,
-                      float* mass_out, unsigned long long* mass_total, bool range_ready, unsigned int* status,
+                      float* mass_out, unsigned long long* tile_mass, bool range_ready, unsigned int* status,
                       cudaStream_t s, FftProfile* prof, unsigned int spin_limit);
 
 cudaError_t wait_timeout_test(uint32_t* zero_word, unsigned int* status, unsigned int spin_limit, cudaStream_t s);
