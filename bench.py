@@ -10,6 +10,11 @@ path), so value = all ranks' cells / max-over-ranks time.
 
 --impl reference times the FP64 CPU oracle (the only other implementation
 of the method) on a bounded sample of the same workload.
+
+At one GPU the line also carries "batched" (48 realisations of 128^3 and
+256^3 as a loop of plain solves vs one captured-graph launch) and "serving"
+(p50/p99 latency and cells/s of a Poisson request stream at 200 req/s over
+128^3/256^3/512^3 grids with cached rank orders); --no-extras skips both.
 """
 from __future__ import annotations
 
@@ -309,6 +314,15 @@ def run_amber(args):
         cpu = {"value": rate, "unit": "cells/s", "cores": 1, "kind": "oracle",
                "sample": f"{reps} x {ns}^3 realisation(s) of the same recipe and cell size, {el:.1f} s"}
 
+    extras = {}
+    if rank == 0 and ws == 1 and not args.no_extras:
+        ctx.close()
+        del z
+        torch.cuda.empty_cache()
+        extras["batched"] = run_batched(B, synth, torch)
+        torch.cuda.empty_cache()
+        extras["serving"] = run_serving(torch)
+
     if rank == 0:
         line = {"metric": METRIC, "value": C * ws / (ms_max / 1e3), "unit": "cells/s", "n_gpus": ws,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
@@ -327,11 +341,73 @@ def run_amber(args):
                 "kernels": kernels,
                 "clocks": clocks,
                 "cpu_baseline": cpu}
+        line.update(extras)
         print(json.dumps(line), flush=True)
     ctx.close()
     if dist is not None:
         dist.destroy_process_group()
     return 0
+
+
+def run_batched(B, synth, torch, reps: int = 3):
+    """48 realisations (32 x 128^3, 16 x 256^3): a loop of plain solves vs one graph launch."""
+    g = __import__("numpy").random.default_rng(2024)
+    specs = [(128, 100.0)] * 32 + [(256, 200.0)] * 16
+    items = []
+    for r, (n, box) in enumerate(specs):
+        S, m = synth.realisation(n, box, r, device="cuda")
+        hist = (float(g.uniform(6.5, 9.0)), float(g.uniform(2.0, 6.0)), float(g.uniform(1.5, 5.0)))
+        items.append((S, m, box, float(g.uniform(1.0, 20.0)), B.history(*hist), torch.empty_like(S)))
+    cells = sum(it[0].numel() for it in items)
+    ctxs = [B.Context(256 ** 3) for _ in range(8)]
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    # plain: the single-instance path, one call after another
+    for it in items:
+        ctxs[0].solve(*it[:5], out=it[5])
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        for it in items:
+            ctxs[0].solve(*it[:5], out=it[5])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    plain_ms = e0.elapsed_time(e1) / reps
+    batch = B.Batch(ctxs, items)
+    batch.launch()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        batch.launch()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    graph_ms = e0.elapsed_time(e1) / reps
+    st = max(c.sync_status() for c in ctxs)
+    batch.close()
+    for c in ctxs:
+        c.close()
+    return {"workload": "48 realisations: 32 x 128^3 (box 100) + 16 x 256^3 (box 200), l_mfp U[1,20], "
+                        "z_mid U[6.5,9], dz U[2,6], Az U[1.5,5]",
+            "cells": cells, "plain_loop_ms": plain_ms, "plain_loop_cells_per_s": cells / (plain_ms / 1e3),
+            "graph_ms": graph_ms, "graph_cells_per_s": cells / (graph_ms / 1e3), "speedup": plain_ms / graph_ms,
+            "contexts": len(ctxs), "status": st}
+
+
+def run_serving(torch, n_requests: int = 800, rate: float = 200.0):
+    """Poisson request stream over mixed grids with a cache of rank orders."""
+    from paper_2109_10375_gb300 import serve
+    reqs = serve.poisson_requests(n_requests, rate=rate, seed=7)
+    srv = serve.Server(n_slots=6, max_n=512, cache_bytes=40e9)
+    srv.prepare(reqs)
+    warm = serve.poisson_requests(60, rate=rate, seed=8)  # untimed: first launches, allocator
+    srv.run(warm, realtime=True)
+    srv.run(reqs, realtime=True)
+    out = serve.summarize(reqs)
+    out.update({"rate_per_s": rate, "mix": {"128^3": 0.6, "256^3": 0.3, "512^3": 0.1}, "realisations": 20,
+                "history_only_fraction": 0.7, "slots": len(srv.slots),
+                "waits_for_hbm": srv.waiting_hbm})
+    srv.close()
+    return out
 
 
 def main():
@@ -344,6 +420,7 @@ def main():
     ap.add_argument("--cpu-sample-n", type=int, default=128)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the batched and serving measurements")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "amber":
         args.warmup = 3

@@ -124,7 +124,7 @@ __device__ __forceinline__ void publish(ScanTile* st, u128 v, unsigned int flag)
 }
 
 template <bool GATHER, bool WANT_F>
-__global__ void __launch_bounds__(kScanThreads) k_scan_assign(const ScanArgs a) {
+__global__ void __launch_bounds__(kScanThreads, 3) k_scan_assign(const ScanArgs a) {
   constexpr int NT = kScanThreads, IT = kScanItems, TILE = kScanTile;
   __shared__ uint32_t sord[TILE + TILE / 32];
   __shared__ float smass[TILE + TILE / 32];
@@ -323,12 +323,14 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_assign(const ScanArgs a) 
     sz[q + (q >> 5)] = zv[i];
   }
   __syncthreads();
+  // the pairs are read back only after the whole scan: keep them out of L2
+  const unsigned long long pol = l2_evict_first();
 #pragma unroll
   for (int k = 0; k < IT; ++k) {
     const int p = k * NT + tid;
     if (p < cnt) {
-      a.bcell[start + p] = scell[p + (p >> 5)];
-      a.bz[start + p] = sz[p + (p >> 5)];
+      st_hint(a.bcell + start + p, scell[p + (p >> 5)], pol);
+      st_hint(a.bz + start + p, sz[p + (p >> 5)], pol);
     }
   }
   if (__any_sync(0xffffffffu, bad) && lane == 0) raise_status(a.status, AMBER_ERR_INVALID_MASS);
@@ -345,13 +347,17 @@ __global__ void __launch_bounds__(256) k_scatter_back(const uint32_t* __restrict
   const int b = blockIdx.x / groups;
   const int64_t g = blockIdx.x - (int64_t)b * groups;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  // the pairs stream through once; the bucket's z_re lines should stay in L2
+  // until all their cells are written, so the stores carry evict_last
+  const unsigned long long stream_pol = l2_evict_first(), keep_pol = l2_evict_last();
   for (int k = 0; k < kBackTilesPerCta / 8; ++k) {
     const int64_t t = g * kBackTilesPerCta + k * 8 + warp;
     if (t >= tiles) break;
     const uint16_t* row = btab + t * (nbuckets + 1);
     const int s = row[b], e = row[b + 1];
     const int64_t base = t * kScanTile;
-    for (int i = s + lane; i < e; i += 32) zre[bcell[base + i]] = bz[base + i];
+    for (int i = s + lane; i < e; i += 32)
+      st_hint(zre + ld_hint(bcell + base + i, stream_pol), ld_hint(bz + base + i, stream_pol), keep_pol);
   }
 }
 
