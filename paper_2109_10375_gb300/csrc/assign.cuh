@@ -13,7 +13,7 @@ constexpr int kScanThreads = 256;
 constexpr int kScanItems = 16;
 constexpr int kScanTile = kScanThreads * kScanItems;
 constexpr int kMaxTable = 1 << 16;
-constexpr int kMaxBuckets = 256;
+constexpr int kMaxBuckets = 1024;
 
 // Per-tile look-back record: flag (0 none, 1 aggregate, 2 inclusive) and the
 // two 128-bit values; the flag is released after the value is written.
@@ -23,8 +23,7 @@ struct __align__(16) ScanTile {
   unsigned long long agg_lo, agg_hi, inc_lo, inc_hi;
 };
 
-constexpr int kBackTilesPerCta = 64;  // scan tiles one scatter-back CTA covers
-constexpr int kBucketShift = 23;      // 2^23 cells (32 MB of z_re) per bucket
+constexpr int kBucketShift = 21;  // 2^21 cells (8 MB of z_re) per bucket by default
 
 // ctrl: total mass (2 x u64) at 0, tile ticket (u32) at 16; zeroed per call
 constexpr size_t kAssignCtrlBytes = 256;

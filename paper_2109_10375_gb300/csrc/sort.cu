@@ -28,6 +28,7 @@
 //
 // Keys: descending float order maps to ascending uint32 (uint64 for double)
 // by flipping; -0.0 is folded into +0.0 and NaN latches AMBER_ERR_NONFINITE.
+#include <cstdlib>
 #include <cstring>
 
 #include "fixed128.cuh"
@@ -171,7 +172,7 @@ __global__ void __launch_bounds__(256) k_sort_offsets(SortCtrl* __restrict__ ctr
 // order, summed per tile into tile_mass and checked.  The last needed pass writes
 // only the payloads (to the final arrays).
 // ---------------------------------------------------------------------------
-template <typename SRC, bool FIRST, bool MASS>
+template <typename SRC, bool FIRST, bool MASS, bool MATCH>
 __global__ void __launch_bounds__(kSortThreads, 3) k_sort_pass(const PassArgs a) {
   using K = typename KeyOf<SRC>::K;
   constexpr int RB = KeyOf<SRC>::RB, R = 1 << RB, DPT = R / kSortThreads;  // digits per thread
@@ -223,11 +224,18 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_sort_pass(const PassArgs a)
   for (int it = 0; it < kItems; ++it) {
     const bool ok = wbase + 32 * it < n;
     const unsigned d = (unsigned)(key[it] >> shift) & (R - 1);
-    unsigned peers = __ballot_sync(0xffffffffu, ok);
+    unsigned peers;
+    if constexpr (MATCH) {
+      // lanes holding the same digit (out-of-range lanes group apart)
+      peers = __match_any_sync(0xffffffffu, ok ? d : 0x10000u);
+    } else {
+      // the same set from one ballot per digit bit
+      peers = __ballot_sync(0xffffffffu, ok);
 #pragma unroll
-    for (int b = 0; b < RB; ++b) {
-      const unsigned bb = __ballot_sync(0xffffffffu, (d >> b) & 1u);
-      peers &= ((d >> b) & 1u) ? bb : ~bb;
+      for (int b = 0; b < RB; ++b) {
+        const unsigned bb = __ballot_sync(0xffffffffu, (d >> b) & 1u);
+        peers &= ((d >> b) & 1u) ? bb : ~bb;
+      }
     }
     uint32_t base = 0;
     if (ok) base = wh[d];
@@ -387,13 +395,30 @@ template <typename SRC> static size_t pass_smem(bool mass) {
 int64_t sort_tiles(int64_t n) { return (n + kTile - 1) / kTile; }
 size_t sort_lookback_words(int64_t n) { return (size_t)sort_tiles(n) * kMaxRadix; }
 
-template <typename SRC, bool FIRST, bool MASS>
-static void launch_pass(const PassArgs& a, int64_t tiles, cudaStream_t s) {
+template <typename SRC, bool FIRST, bool MASS, bool MATCH>
+static void launch_pass_v(const PassArgs& a, int64_t tiles, cudaStream_t s) {
   const size_t smem = pass_smem<SRC>(MASS);
   static std::atomic<unsigned long long> attr{0};  // per instantiation and device
   if (first_use_on_device(attr))
-    cudaFuncSetAttribute(k_sort_pass<SRC, FIRST, MASS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_sort_pass<SRC, FIRST, MASS><<<(unsigned)tiles, kSortThreads, smem, s>>>(a);
+    cudaFuncSetAttribute(k_sort_pass<SRC, FIRST, MASS, MATCH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+  k_sort_pass<SRC, FIRST, MASS, MATCH><<<(unsigned)tiles, kSortThreads, smem, s>>>(a);
+}
+
+// Digit peers by warp match (one instruction) or by ballots (one per digit
+// bit); AMBER_SORT_RANK=ballot|match picks, match by default.
+static bool rank_by_match() {
+  static const bool m = [] {
+    const char* v = getenv("AMBER_SORT_RANK");
+    return !(v && strcmp(v, "ballot") == 0);
+  }();
+  return m;
+}
+
+template <typename SRC, bool FIRST, bool MASS>
+static void launch_pass(const PassArgs& a, int64_t tiles, cudaStream_t s) {
+  if (rank_by_match()) launch_pass_v<SRC, FIRST, MASS, true>(a, tiles, s);
+  else launch_pass_v<SRC, FIRST, MASS, false>(a, tiles, s);
 }
 
 cudaError_t sort_ctrl_reset(SortCtrl* ctrl, cudaStream_t s) {

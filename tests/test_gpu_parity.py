@@ -339,3 +339,24 @@ def test_solve_256cube_fp32(ctx, B, l):
     np.testing.assert_array_equal(order, np.argsort(-Jg.reshape(-1), kind="stable"))
     # monotone: z non-increasing along descending J
     assert np.all(np.diff(zg.reshape(-1)[order]) <= 0)
+
+
+def test_rank_ballot_variant_bit_exact():
+    """The ballot-based digit ranking (AMBER_SORT_RANK=ballot) gives the same order."""
+    import os
+    import subprocess
+    import sys
+    code = (
+        "import numpy as np, torch\n"
+        "from paper_2109_10375_gb300 import binding as B\n"
+        "g = np.random.default_rng(3)\n"
+        "J = np.concatenate([g.normal(size=300001), np.full(5000, 2.5)]).astype(np.float32)\n"
+        "with B.Context(J.size) as ctx:\n"
+        "    o = ctx.rank(torch.from_numpy(J).cuda()).cpu().numpy().astype(np.int64)\n"
+        "    assert ctx.sync_status() == 0\n"
+        "assert (o == np.argsort(-J, kind='stable')).all()\n"
+        "print('ok')\n")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, AMBER_SORT_RANK="ballot", PYTHONPATH=root)
+    r = subprocess.run([sys.executable, "-c", code], cwd=root, env=env, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0 and "ok" in r.stdout, r.stderr[-2000:]
