@@ -339,26 +339,29 @@ __global__ void __launch_bounds__(kScanThreads, 3) k_scan_assign(const ScanArgs 
 }
 
 // z_re[cell] = z, bucket after bucket: CTA (bucket b, tile group g) copies
-// bucket b's run of every tile in its group, one thread per tile run.  A
-// bucket's cells span a region small enough to stay in L2, so while its CTAs
-// run the permuted writes merge there instead of reaching HBM one partial
-// sector at a time.
+// bucket b's run of every tile in its group, one warp per tile run (lanes
+// read the run coalesced).  A bucket's cells span a region small enough to
+// stay in L2, so while its CTAs run the permuted writes merge there instead
+// of reaching HBM one partial sector at a time.
 __global__ void __launch_bounds__(256) k_scatter_back(const uint32_t* __restrict__ bcell,
                                                       const float* __restrict__ bz,
                                                       const uint16_t* __restrict__ btab, int nbuckets,
                                                       int64_t tiles, int groups, float* __restrict__ zre) {
   const int b = blockIdx.x / groups;
   const int64_t g = blockIdx.x - (int64_t)b * groups;
-  const int64_t t = g * 256 + threadIdx.x;
-  if (t >= tiles) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   // the pairs stream through once; the bucket's z_re lines should stay in L2
   // until all their cells are written, so the stores carry evict_last
   const unsigned long long stream_pol = l2_evict_first(), keep_pol = l2_evict_last();
-  const uint16_t* row = btab + t * (nbuckets + 1);
-  const int s = row[b], e = row[b + 1];
-  const int64_t base = t * kScanTile;
-  for (int i = s; i < e; ++i)
-    st_hint(zre + ld_hint(bcell + base + i, stream_pol), ld_hint(bz + base + i, stream_pol), keep_pol);
+  for (int k = 0; k < kBackTilesPerCta / 8; ++k) {
+    const int64_t t = g * kBackTilesPerCta + k * 8 + warp;
+    if (t >= tiles) break;
+    const uint16_t* row = btab + t * (nbuckets + 1);
+    const int s = row[b], e = row[b + 1];
+    const int64_t base = t * kScanTile;
+    for (int i = s + lane; i < e; i += 32)
+      st_hint(zre + ld_hint(bcell + base + i, stream_pol), ld_hint(bz + base + i, stream_pol), keep_pol);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -429,7 +432,7 @@ cudaError_t assign_impl(const AssignWork& w, const uint32_t* order, const float*
   prof_end(prof, PK_SCAN_ASSIGN, s);
   prof_begin(prof, PK_SCATTER_BACK, s);
   {
-    const int groups = (int)((tiles + 255) / 256);
+    const int groups = (int)((tiles + kBackTilesPerCta - 1) / kBackTilesPerCta);
     k_scatter_back<<<(unsigned)(groups * a.nbuckets), 256, 0, s>>>(w.bcell, w.bz, w.btab, a.nbuckets, tiles, groups,
                                                                    zre);
   }

@@ -23,7 +23,8 @@ struct __align__(16) ScanTile {
   unsigned long long agg_lo, agg_hi, inc_lo, inc_hi;
 };
 
-constexpr int kBucketShift = 21;  // 2^21 cells (8 MB of z_re) per bucket by default
+constexpr int kBackTilesPerCta = 64;  // scan tiles one scatter-back CTA covers
+constexpr int kBucketShift = 23;  // 2^23 cells (32 MB of z_re) per bucket by default
 
 // ctrl: total mass (2 x u64) at 0, tile ticket (u32) at 16; zeroed per call
 constexpr size_t kAssignCtrlBytes = 256;

@@ -341,8 +341,8 @@ def test_solve_256cube_fp32(ctx, B, l):
     assert np.all(np.diff(zg.reshape(-1)[order]) <= 0)
 
 
-def test_rank_ballot_variant_bit_exact():
-    """The ballot-based digit ranking (AMBER_SORT_RANK=ballot) gives the same order."""
+def test_rank_match_variant_bit_exact():
+    """The warp-match digit ranking (AMBER_SORT_RANK=match) gives the same order."""
     import os
     import subprocess
     import sys
@@ -357,6 +357,6 @@ def test_rank_ballot_variant_bit_exact():
         "assert (o == np.argsort(-J, kind='stable')).all()\n"
         "print('ok')\n")
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-    env = dict(os.environ, AMBER_SORT_RANK="ballot", PYTHONPATH=root)
+    env = dict(os.environ, AMBER_SORT_RANK="match", PYTHONPATH=root)
     r = subprocess.run([sys.executable, "-c", code], cwd=root, env=env, capture_output=True, text=True, timeout=300)
     assert r.returncode == 0 and "ok" in r.stdout, r.stderr[-2000:]
