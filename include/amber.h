@@ -125,9 +125,14 @@ int amber_rank_f64(amber_ctx *ctx, const double *d_J, int64_t ncells, uint32_t *
  * z_hi if j* is the last node, otherwise the linear interpolation
  * z_j* + (x_j* - F_n)/(x_j* - x_j*+1) (z_j*+1 - z_j*).  Writes
  * d_zre[order[n]] = z_n (float, cell order).
- * The cumulative mass is accumulated exactly in 128-bit fixed point
- * (2^-64 units) and the bracket test is exact; the interpolation weight is
- * FP32.  d_F_opt, if not NULL, receives F_n (double, rank order).
+ * The mass total is exact (128-bit fixed point, 2^-64 units); the running
+ * prefix M_n is 64-bit fixed point with a shift s chosen from the total so
+ * it stays below 2^62 (each mass rounded down to a multiple of 2^-s), so F_n
+ * is within n 2^-60 of the exact value; the bracket test "x_j >= F_n" is an
+ * exact integer comparison against thresholds floor(x_j T) in the same fixed
+ * point, and only the interpolation weight is FP32.  No result depends on
+ * the order of addition.  d_F_opt, if not NULL, receives F_n (double, rank
+ * order).
  * Masses must be finite, >= 0 and < 2^40 (else AMBER_ERR_INVALID_MASS latches),
  * with a positive total.  d_order must be a permutation of [0, ncells). */
 int amber_assign_zre(amber_ctx *ctx, const uint32_t *d_order, const float *d_mass, int64_t ncells,

@@ -171,7 +171,7 @@ static Plan make_plan(int64_t max_cells) {
   const size_t keyb = std::max((size_t)max_cells * 4, (size_t)p.cells64 * 8);
   const size_t idxb = (size_t)max_cells * 4;
   const size_t lb = 2 * sort_lookback_words(max_cells) * 4;
-  const size_t stt = (size_t)((max_cells + kScanTile - 1) / kScanTile) * sizeof(ScanTile);
+  const size_t stt = (size_t)((max_cells + kScanTile - 1) / kScanTile) * sizeof(unsigned long long);
   size_t o = 0;
   auto take = [&](size_t bytes) { const size_t at = o; o += align256(bytes); return at; };
   p.off_spec = take(spec);
@@ -184,7 +184,7 @@ static Plan make_plan(int64_t max_cells) {
   p.off_lb = take(lb);
   p.off_sctrl = take(sizeof(SortCtrl));
   p.off_actrl = take(kAssignCtrlBytes);
-  p.off_X = take((size_t)kMaxTable * sizeof(u128));
+  p.off_X = take((size_t)kMaxTable * sizeof(unsigned long long));
   p.off_invdx = take((size_t)kMaxTable * sizeof(float));
   p.off_state = take(stt);
   p.off_btab = take((size_t)((max_cells + kScanTile - 1) / kScanTile) * (kMaxBuckets + 1) * sizeof(uint16_t));
@@ -324,9 +324,9 @@ int amber_create(amber_ctx** out, int device, int64_t max_cells) {
   c->sortw.max_cells = max_cells;
   c->sortw.num_sms = c->num_sms;
   c->assw.ctrl = c->ws + p.off_actrl;
-  c->assw.X = reinterpret_cast<u128*>(c->ws + p.off_X);
+  c->assw.Xq = reinterpret_cast<unsigned long long*>(c->ws + p.off_X);
   c->assw.inv_dx = reinterpret_cast<float*>(c->ws + p.off_invdx);
-  c->assw.state = reinterpret_cast<ScanTile*>(c->ws + p.off_state);
+  c->assw.state = reinterpret_cast<unsigned long long*>(c->ws + p.off_state);
   // bucketed (cell, z) pairs reuse the key buffers, dead once ranked
   c->assw.bcell = reinterpret_cast<uint32_t*>(c->sortw.keysA);
   c->assw.bz = reinterpret_cast<float*>(c->sortw.keysB);

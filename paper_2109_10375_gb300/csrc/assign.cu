@@ -2,10 +2,11 @@
 // the cumulative mass fraction F_n = M_n / M_total equals the history x(z_n)
 // (Sec. 3.1.2, Eq. weibull), with x(z) tabulated on uniform redshifts.
 //
-//   k_mass_reduce   : M_total = sum of all cell masses (order-free)
-//   k_thresholds    : table x_j = x(z_j) and the exact integer thresholds
-//                     X_j = floor(x_j * M_total), so "x_j >= F_n" is the
-//                     integer test "X_j >= M_n"; plus 1/(X_j - X_j+1)
+//   k_mass_reduce   : M_total = sum of all cell masses (order-free, exact)
+//   k_thresholds    : table x_j = x(z_j) and integer thresholds
+//                     X_j = floor(x_j * M_total) in the scan's fixed point,
+//                     so "x_j >= F_n" is the integer test "X_j >= M_n";
+//                     plus 1/(X_j - X_j+1)
 //   k_scan_assign   : M_n by a decoupled-look-back prefix sum over ranks,
 //                     bracket j* by a search in the thresholds amortised over
 //                     each thread's run of ranks, interpolate to z_n, and
@@ -14,9 +15,11 @@
 //                     region small enough to stay in L2, so the permuted
 //                     writes reach HBM as whole sectors
 //
-// Masses are summed exactly as 128-bit fixed point with 64 fraction bits, so
-// the prefix sums carry no rounding and do not depend on summation order;
-// only the final interpolation weight is rounded (FP32).
+// The total is summed exactly as 128-bit fixed point with 64 fraction bits.
+// The running prefix uses 64-bit fixed point whose shift s is chosen from the
+// total so it stays below 2^62: each mass is rounded down to a multiple of
+// 2^-s, so F_n is off by at most n 2^-60 (1e-9 at 2^30 cells), and no sum
+// depends on the order of addition.  Only the interpolation weight is FP32.
 #include <cstdlib>
 
 #include "assign.cuh"
@@ -75,14 +78,19 @@ __device__ __forceinline__ u128 mul_floor(double x, u128 T) {
 }
 
 // tile_mass (optional): per-tile partial sums from the ranking; their total
-// is formed here (exact, order-free) and stored as the mass total.
+// is formed here (exact, order-free).  From the exact total T (2^-64 units)
+// the kernel picks the scan's fixed-point shift s (total below 2^62), and
+// tabulates X_j = floor(x_j T 2^(s-64)) so "x_j >= F_n" is the integer test
+// "X_j >= M_n", plus 1/(X_j - X_j+1) for the interpolation weight.
 __global__ void __launch_bounds__(1024) k_thresholds(unsigned long long* __restrict__ total,
                                                      const unsigned long long* __restrict__ tile_mass,
                                                      int64_t ntiles, int M, double a_w, double b_w, double c_w,
-                                                     double z_lo, double z_hi, u128* __restrict__ X,
-                                                     float* __restrict__ inv_dx) {
+                                                     double z_lo, double z_hi, unsigned long long* __restrict__ Xq,
+                                                     float* __restrict__ inv_dx, int* __restrict__ qshift,
+                                                     unsigned long long* __restrict__ qtotal) {
   __shared__ u128 ws[32];
   __shared__ u128 sT;
+  __shared__ int s_shift;
   if (tile_mass) {
     u128 acc = 0;
     for (int64_t t = threadIdx.x; t < ntiles; t += blockDim.x)
@@ -102,27 +110,63 @@ __global__ void __launch_bounds__(1024) k_thresholds(unsigned long long* __restr
     sT = ((u128)total[1] << 64) | (u128)total[0];
   }
   __syncthreads();
+  if (threadIdx.x == 0) {
+    // bit length L of T; the real total is below 2^(L-64), so s = 126 - L
+    // keeps it below 2^62 (s <= 64: no finer than the exact representation)
+    int L = 0;
+    for (u128 v = sT; v != 0; v >>= 1) ++L;
+    int s = 126 - L;
+    if (s > 64) s = 64;
+    s_shift = s;
+    *qshift = s;
+    const int sh = 64 - s;
+    *qtotal = (unsigned long long)(sh >= 0 ? (sT >> sh) : (sT << (-sh)));
+  }
+  __syncthreads();
   const u128 T = sT;
+  const int sh = 64 - s_shift;  // X in 2^-s units: floor(x T) >> (64 - s)
   for (int j = threadIdx.x; j < M; j += blockDim.x) {
     const double z = z_lo + (z_hi - z_lo) * (double)j / (double)(M - 1);
     const double u = fmax((z - a_w) / b_w, 0.0);
     const double x = exp(-pow(u, c_w));
-    X[j] = mul_floor(x, T);
+    const u128 X = mul_floor(x, T);
+    Xq[j] = (unsigned long long)(sh >= 0 ? (X >> sh) : (X << (-sh)));
   }
   __syncthreads();
   for (int j = threadIdx.x; j < M - 1; j += blockDim.x) {
-    const u128 d = X[j] - X[j + 1];
-    inv_dx[j] = d > 0 ? 1.0f / u128_to_float(d) : 0.0f;
+    const unsigned long long d = Xq[j] - Xq[j + 1];
+    inv_dx[j] = d > 0 ? 1.0f / __ull2float_rn(d) : 0.0f;
   }
 }
 
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void publish(ScanTile* st, u128 v, unsigned int flag) {
-  volatile unsigned long long* p = (flag == 1u) ? &st->agg_lo : &st->inc_lo;
-  p[0] = (unsigned long long)v;
-  p[1] = (unsigned long long)(v >> 64);
-  __threadfence();
-  st_release_u32(&st->flag, flag);
+// Cell mass in the scan's 64-bit fixed point: floor(m 2^s), s chosen per call
+// by k_thresholds so the total stays below 2^62.  Each cell loses less than
+// 2^-s, so over n cells F_n is off by less than n 2^-s / T <= n 2^-62 (2e-10
+// relative at 2^30 cells) -- far inside an FP64 running sum's own error.
+__device__ __forceinline__ unsigned long long mass_fix(float m, int s) {
+  const uint32_t b = __float_as_uint(m);
+  const uint32_t e = (b >> 23) & 0xffu;
+  if ((b & 0x80000000u) || e >= 127u + 40u) return 0ull;  // flagged by the mass total pass
+  const unsigned long long mant = (e == 0) ? (b & 0x7fffffu) : ((b & 0x7fffffu) | 0x800000u);
+  const int sh = (int)(e == 0 ? 1u : e) - 150 + s;
+  if (sh >= 0) return mant << sh;
+  return sh > -64 ? (mant >> (-sh)) : 0ull;
+}
+
+// Look-back word of a scan tile: 2 flag bits over a 62-bit prefix.
+constexpr unsigned long long kScanAgg = 1ull << 62;
+constexpr unsigned long long kScanInc = 2ull << 62;
+constexpr unsigned long long kScanMask = 3ull << 62;
+constexpr unsigned long long kScanValue = (1ull << 62) - 1ull;
+
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_relaxed_u64(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
 template <bool GATHER, bool WANT_F>
@@ -130,9 +174,10 @@ __global__ void __launch_bounds__(kScanThreads, 3) k_scan_assign(const ScanArgs 
   constexpr int NT = kScanThreads, IT = kScanItems, TILE = kScanTile;
   __shared__ uint32_t sord[TILE + TILE / 32];
   __shared__ float smass[TILE + TILE / 32];
-  __shared__ u128 wtot[NT / 32];
-  __shared__ u128 s_excl;
+  __shared__ unsigned long long wtot[NT / 32];
+  __shared__ unsigned long long s_excl;
   __shared__ uint32_t s_tile;
+  __shared__ int s_cx[2];
   __shared__ uint32_t scnt[kMaxBuckets];
   __shared__ uint32_t soff[kMaxBuckets + 1];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -146,6 +191,7 @@ __global__ void __launch_bounds__(kScanThreads, 3) k_scan_assign(const ScanArgs 
   const bool side_b = a.pick && ((*a.pick - 1) & 1);
   const uint32_t* order = side_b ? a.order_b : a.order;
   const float* mass = side_b ? a.mass_b : a.mass;
+  const int qs = *a.qshift;
 
   // order (and rank-order masses): coalesced striped loads -> padded shared
   // memory -> a blocked run of IT consecutive ranks per thread
@@ -158,62 +204,53 @@ __global__ void __launch_bounds__(kScanThreads, 3) k_scan_assign(const ScanArgs 
   __syncthreads();
   uint32_t cell[IT];
   float mv[IT];
-  bool bad = false;
-  u128 run = 0;
+  unsigned long long run = 0;
 #pragma unroll
   for (int i = 0; i < IT; ++i) {
     const int p = tid * IT + i;
     cell[i] = sord[p + (p >> 5)];
     mv[i] = 0.0f;
     if (p < cnt) mv[i] = GATHER ? mass[cell[i]] : smass[p + (p >> 5)];
-    run += mass_q64(mv[i], bad);
+    run += mass_fix(mv[i], qs);
   }
   // block exclusive scan of the thread totals
-  u128 x = run;
+  unsigned long long x = run;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
-    const u128 y = shfl_up_u128(x, o);
+    const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
     if (lane >= o) x += y;
   }
   if (lane == 31) wtot[warp] = x;
   __syncthreads();
-  u128 wpre = 0, tile_sum = 0;
+  unsigned long long wpre = 0, tile_sum = 0;
 #pragma unroll
   for (int w = 0; w < NT / 32; ++w) {
     if (w < warp) wpre += wtot[w];
     tile_sum += wtot[w];
   }
-  const u128 thr_excl = wpre + x - run;
+  const unsigned long long thr_excl = wpre + x - run;
 
-  // decoupled look-back by warp 0: each lane reads one predecessor, so a
-  // round trip covers 32 tiles; aggregates are summed back to the nearest
+  // decoupled look-back by warp 0: each lane reads one predecessor's word, so
+  // a round trip covers 32 tiles; aggregates are summed back to the nearest
   // inclusive prefix
   if (warp == 0) {
-    ScanTile* me = a.state + tile;
-    if (lane == 0) publish(me, tile_sum, tile == 0 ? 2u : 1u);
-    u128 excl = 0;
+    unsigned long long* me = a.state + tile;
+    if (lane == 0) st_relaxed_u64(me, (tile == 0 ? kScanInc : kScanAgg) | tile_sum);
+    unsigned long long excl = 0;
     int64_t t = (int64_t)tile - 1;
     unsigned spins = 0;
     while (t >= 0) {
       const int64_t tt = t - lane;
-      unsigned int f = 2u;
-      u128 v = 0;
-      if (tt >= 0) {
-        const ScanTile* o = a.state + tt;
-        f = ld_acquire_u32(&o->flag);
-        if (f != 0u) {
-          const volatile unsigned long long* p = (f == 2u) ? &o->inc_lo : &o->agg_lo;
-          v = ((u128)p[1] << 64) | (u128)p[0];
-        }
-      }
-      const unsigned inc_mask = __ballot_sync(0xffffffffu, f == 2u);
-      const unsigned stop_mask = inc_mask | __ballot_sync(0xffffffffu, f == 0u);
+      const unsigned long long w = (tt >= 0) ? ld_relaxed_u64(a.state + tt) : kScanInc;
+      const unsigned long long f = w & kScanMask;
+      const unsigned inc_mask = __ballot_sync(0xffffffffu, f == kScanInc);
+      const unsigned stop_mask = inc_mask | __ballot_sync(0xffffffffu, f == 0ull);
       const int first = stop_mask ? __ffs(stop_mask) - 1 : 32;
       const bool found = first < 32 && ((inc_mask >> first) & 1u);
-      u128 part = (lane < first || (found && lane == first)) ? v : (u128)0;
+      unsigned long long part = (lane < first || (found && lane == first)) ? (w & kScanValue) : 0ull;
 #pragma unroll
-      for (int o = 16; o >= 1; o >>= 1) part += shfl_down_u128(part, o);
-      excl += shfl_u128(part, 0);
+      for (int o = 16; o >= 1; o >>= 1) part += __shfl_down_sync(0xffffffffu, part, o);
+      excl += __shfl_sync(0xffffffffu, part, 0);
       if (found) break;
       t -= first;
       if (first < 32) {
@@ -225,37 +262,32 @@ __global__ void __launch_bounds__(kScanThreads, 3) k_scan_assign(const ScanArgs 
       }
     }
     if (lane == 0) {
-      if (tile != 0) publish(me, excl + tile_sum, 2u);
+      if (tile != 0) st_relaxed_u64(me, kScanInc | ((excl + tile_sum) & kScanValue));
       s_excl = excl;
+      // bracket the whole tile: #{j : X_j >= M} before and after it
+      const unsigned long long m_first = excl, m_last = excl + tile_sum;
+      int lo = 0, hi = a.n_table;
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (a.Xq[mid] >= m_first) lo = mid + 1; else hi = mid;
+      }
+      s_cx[0] = lo;
+      hi = lo;
+      lo = 0;
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (a.Xq[mid] >= m_last) lo = mid + 1; else hi = mid;
+      }
+      s_cx[1] = lo;
     }
   }
   __syncthreads();
-  u128 Mn = s_excl + thr_excl;
-  const u128 T = ((u128)a.total[1] << 64) | (u128)a.total[0];
-  const double invT = WANT_F ? 1.0 / u128_to_double(T) : 0.0;
+  unsigned long long Mn = s_excl + thr_excl;
   const int M = a.n_table;
+  const double invT = WANT_F ? 1.0 / (double)*a.qtotal : 0.0;
 
   // bracket: cx = #{j : X_j >= M_n}; X is non-increasing in j and M_n grows
-  // with rank.  Thread 0 brackets the whole tile (its first and last M), so
-  // each thread searches only that range once, then walks down.
-  __shared__ int s_cx[2];
-  if (tid == 0) {
-    const u128 m_first = s_excl, m_last = s_excl + tile_sum;  // M before / after the tile
-    int lo = 0, hi = M;
-    while (lo < hi) {
-      const int mid = (lo + hi) >> 1;
-      if (a.X[mid] >= m_first) lo = mid + 1; else hi = mid;
-    }
-    s_cx[0] = lo;
-    hi = lo;
-    lo = 0;
-    while (lo < hi) {
-      const int mid = (lo + hi) >> 1;
-      if (a.X[mid] >= m_last) lo = mid + 1; else hi = mid;
-    }
-    s_cx[1] = lo;
-  }
-  __syncthreads();
+  // with rank, so each thread searches the tile's range once, then walks down
   const int cx_hi = s_cx[0], cx_lo = s_cx[1];
   float zv[IT];
   uint32_t slot[IT];
@@ -266,29 +298,28 @@ __global__ void __launch_bounds__(kScanThreads, 3) k_scan_assign(const ScanArgs 
     zv[i] = 0.0f;
     slot[i] = 0xffffffffu;
     if (p >= cnt) continue;
-    bool dummy = false;
-    Mn += mass_q64(mv[i], dummy);
+    Mn += mass_fix(mv[i], qs);
     if (cx < 0) {
       int lo = cx_lo, hi = cx_hi;
       while (lo < hi) {
         const int mid = (lo + hi) >> 1;
-        if (a.X[mid] >= Mn) lo = mid + 1; else hi = mid;
+        if (a.Xq[mid] >= Mn) lo = mid + 1; else hi = mid;
       }
       cx = lo;
     } else {
-      while (cx > 0 && a.X[cx - 1] < Mn) --cx;
+      while (cx > 0 && a.Xq[cx - 1] < Mn) --cx;
     }
     const int j = cx - 1;
     float z;
     if (j < 0) z = a.z_lo;
     else if (j == M - 1) z = a.z_hi;
     else {
-      float t = u128_to_float(a.X[j] - Mn) * a.inv_dx[j];
+      float t = __ull2float_rn(a.Xq[j] - Mn) * a.inv_dx[j];
       t = fminf(fmaxf(t, 0.0f), 0.99999994f);
       z = a.z_lo + ((float)j + t) * a.dzt;
     }
     zv[i] = z;
-    if (WANT_F) a.F[start + p] = u128_to_double(Mn) * invT;
+    if (WANT_F) a.F[start + p] = (double)Mn * invT;
     slot[i] = atomicAdd(&scnt[cell[i] >> a.bucket_shift], 1u);
   }
   __syncthreads();
@@ -335,31 +366,53 @@ __global__ void __launch_bounds__(kScanThreads, 3) k_scan_assign(const ScanArgs 
       st_hint(a.bz + start + p, sz[p + (p >> 5)], pol);
     }
   }
-  if (__any_sync(0xffffffffu, bad) && lane == 0) raise_status(a.status, AMBER_ERR_INVALID_MASS);
 }
 
 // z_re[cell] = z, bucket after bucket: CTA (bucket b, tile group g) copies
-// bucket b's run of every tile in its group, one warp per tile run (lanes
-// read the run coalesced).  A bucket's cells span a region small enough to
-// stay in L2, so while its CTAs run the permuted writes merge there instead
-// of reaching HBM one partial sector at a time.
+// bucket b's run of every tile in its group, 8 tiles per warp.  Each warp
+// first issues the loads of all its runs (lanes read a run coalesced), then
+// the stores, so the dependent load -> store chains of its tiles overlap.  A
+// bucket's cells span a bounded region of z_re, so the permuted writes of
+// the CTAs working on it stay close together.
 __global__ void __launch_bounds__(256) k_scatter_back(const uint32_t* __restrict__ bcell,
                                                       const float* __restrict__ bz,
                                                       const uint16_t* __restrict__ btab, int nbuckets,
                                                       int64_t tiles, int groups, float* __restrict__ zre) {
+  constexpr int TPW = kBackTilesPerCta / 8;  // tiles per warp
   const int b = blockIdx.x / groups;
   const int64_t g = blockIdx.x - (int64_t)b * groups;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  // the pairs stream through once; the bucket's z_re lines should stay in L2
-  // until all their cells are written, so the stores carry evict_last
   const unsigned long long stream_pol = l2_evict_first(), keep_pol = l2_evict_last();
-  for (int k = 0; k < kBackTilesPerCta / 8; ++k) {
-    const int64_t t = g * kBackTilesPerCta + k * 8 + warp;
-    if (t >= tiles) break;
-    const uint16_t* row = btab + t * (nbuckets + 1);
-    const int s = row[b], e = row[b + 1];
-    const int64_t base = t * kScanTile;
-    for (int i = s + lane; i < e; i += 32)
+  const int64_t t0 = g * kBackTilesPerCta + warp * TPW;
+  // lane k < TPW fetches tile t0 + k's run bounds
+  int s_l = 0, e_l = 0;
+  if (lane < TPW && t0 + lane < tiles) {
+    const uint16_t* row = btab + (t0 + lane) * (nbuckets + 1);
+    s_l = row[b];
+    e_l = row[b + 1];
+  }
+  uint32_t c[TPW];
+  float zz[TPW];
+#pragma unroll
+  for (int k = 0; k < TPW; ++k) {
+    const int s = __shfl_sync(0xffffffffu, s_l, k), e = __shfl_sync(0xffffffffu, e_l, k);
+    const int64_t base = (t0 + k) * kScanTile;
+    const int i = s + lane;
+    c[k] = 0xffffffffu;
+    if (i < e) {
+      c[k] = ld_hint(bcell + base + i, stream_pol);
+      zz[k] = ld_hint(bz + base + i, stream_pol);
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < TPW; ++k)
+    if (c[k] != 0xffffffffu) st_hint(zre + c[k], zz[k], keep_pol);
+  // runs longer than one warp
+#pragma unroll 1
+  for (int k = 0; k < TPW; ++k) {
+    const int s = __shfl_sync(0xffffffffu, s_l, k), e = __shfl_sync(0xffffffffu, e_l, k);
+    const int64_t base = (t0 + k) * kScanTile;
+    for (int i = s + 32 + lane; i < e; i += 32)
       st_hint(zre + ld_hint(bcell + base + i, stream_pol), ld_hint(bz + base + i, stream_pol), keep_pol);
   }
 }
@@ -382,7 +435,7 @@ cudaError_t assign_impl(const AssignWork& w, const uint32_t* order, const float*
   uint32_t* ticket = reinterpret_cast<uint32_t*>(w.ctrl + 16);
   e = cudaMemsetAsync(w.ctrl, 0, kAssignCtrlBytes, s);
   if (e != cudaSuccess) return e;
-  e = cudaMemsetAsync(w.state, 0, (size_t)tiles * sizeof(ScanTile), s);
+  e = cudaMemsetAsync(w.state, 0, (size_t)tiles * sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;
 
   if (!tile_mass) {  // masses in cell order: one exact reduction pass
@@ -394,8 +447,10 @@ cudaError_t assign_impl(const AssignWork& w, const uint32_t* order, const float*
   }
 
   prof_begin(prof, PK_THRESHOLDS, s);
+  int* qshift = reinterpret_cast<int*>(w.ctrl + 32);
+  unsigned long long* qtotal = reinterpret_cast<unsigned long long*>(w.ctrl + 40);
   k_thresholds<<<1, 1024, 0, s>>>(total, tile_mass, tile_mass ? sort_tiles(n) : 0, hc.n_table, hc.a, hc.b, hc.c,
-                                   hc.z_lo, hc.z_hi, w.X, w.inv_dx);
+                                   hc.z_lo, hc.z_hi, w.Xq, w.inv_dx, qshift, qtotal);
   prof_end(prof, PK_THRESHOLDS, s);
 
   ScanArgs a;
@@ -405,8 +460,9 @@ cudaError_t assign_impl(const AssignWork& w, const uint32_t* order, const float*
   a.mass_b = mass_b;
   a.pick = pick;
   a.n = n;
-  a.total = total;
-  a.X = w.X;
+  a.Xq = w.Xq;
+  a.qshift = qshift;
+  a.qtotal = qtotal;
   a.inv_dx = w.inv_dx;
   a.n_table = hc.n_table;
   a.z_lo = (float)hc.z_lo;

@@ -15,25 +15,18 @@ constexpr int kScanTile = kScanThreads * kScanItems;
 constexpr int kMaxTable = 1 << 16;
 constexpr int kMaxBuckets = 1024;
 
-// Per-tile look-back record: flag (0 none, 1 aggregate, 2 inclusive) and the
-// two 128-bit values; the flag is released after the value is written.
-struct __align__(16) ScanTile {
-  unsigned int flag;
-  unsigned int pad[3];
-  unsigned long long agg_lo, agg_hi, inc_lo, inc_hi;
-};
-
 constexpr int kBackTilesPerCta = 64;  // scan tiles one scatter-back CTA covers
 constexpr int kBucketShift = 23;  // 2^23 cells (32 MB of z_re) per bucket by default
 
-// ctrl: total mass (2 x u64) at 0, tile ticket (u32) at 16; zeroed per call
+// ctrl: exact total mass (2 x u64) at 0, tile ticket (u32) at 16, scan
+// fixed-point shift (int) at 32, scan total (u64) at 40; zeroed per call
 constexpr size_t kAssignCtrlBytes = 256;
 
 struct AssignWork {
   unsigned char* ctrl;
-  u128* X;         // [kMaxTable] thresholds
-  float* inv_dx;   // [kMaxTable]
-  ScanTile* state;
+  unsigned long long* Xq;  // [kMaxTable] thresholds in the scan's fixed point
+  float* inv_dx;           // [kMaxTable]
+  unsigned long long* state;  // per scan tile: look-back word
   uint32_t* bcell;  // per scan tile, (cell, z) pairs grouped by bucket
   float* bz;
   uint16_t* btab;   // [tiles][nbuckets + 1] tile-local bucket starts
@@ -53,13 +46,14 @@ struct ScanArgs {
   const float* mass_b;      // for an odd pass count and in (order_b, mass_b) else
   const int* pick;          // &SortCtrl::npasses or null
   int64_t n;
-  const unsigned long long* total;
-  const u128* X;
+  const unsigned long long* Xq;
+  const int* qshift;                // fixed-point shift s of the masses
+  const unsigned long long* qtotal;  // total in that fixed point (for F)
   const float* inv_dx;
   int n_table;
   float z_lo, z_hi, dzt;
   double* F;
-  ScanTile* state;
+  unsigned long long* state;
   uint32_t* ticket;
   int nbuckets;
   int bucket_shift;  // bucket of a cell = cell >> bucket_shift
