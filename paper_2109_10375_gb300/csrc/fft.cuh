@@ -56,11 +56,14 @@ template <typename T, int N> struct XSmem {
   static __device__ __forceinline__ int pos(int p, int n) { return p * LS + n + n / R0; }
 };
 
+// K(|k|)/C at lattice |k|^2 = k2 (an exact integer), |k| = kf sqrt(k2):
+// arctan(|k| l)/|k|, and l at k = 0.  FP32 uses one reciprocal square root
+// instead of a square root and a division.
 template <typename T> __device__ __forceinline__ T kernel_K(T k2, T l_mfp, T kf, T norm);
 template <> __device__ __forceinline__ float kernel_K<float>(float k2, float l, float kf, float norm) {
   if (k2 == 0.f) return l * norm;
-  const float k = kf * sqrtf(k2);
-  return atanf(k * l) / k * norm;
+  const float r = rsqrtf(k2);          // 1/sqrt(k2)
+  return atanf(kf * l * (k2 * r)) * (r * (norm / kf));
 }
 template <> __device__ __forceinline__ double kernel_K<double>(double k2, double l, double kf, double norm) {
   if (k2 == 0.0) return l * norm;

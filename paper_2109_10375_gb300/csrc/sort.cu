@@ -173,7 +173,7 @@ __global__ void __launch_bounds__(256) k_sort_offsets(SortCtrl* __restrict__ ctr
 // only the payloads (to the final arrays).
 // ---------------------------------------------------------------------------
 template <typename SRC, bool FIRST, bool MASS, bool MATCH>
-__global__ void __launch_bounds__(kSortThreads, 3) k_sort_pass(const PassArgs a) {
+__global__ void __launch_bounds__(kSortThreads, AMBER_SORT_MINB) k_sort_pass(const PassArgs a) {
   using K = typename KeyOf<SRC>::K;
   constexpr int RB = KeyOf<SRC>::RB, R = 1 << RB, DPT = R / kSortThreads;  // digits per thread
   constexpr int NW = kSortThreads / 32;

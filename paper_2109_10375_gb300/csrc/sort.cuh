@@ -9,8 +9,15 @@
 
 namespace amber {
 
+// Tile geometry (build-time tunables: the defaults were measured best).
+#ifndef AMBER_SORT_ITEMS
+#define AMBER_SORT_ITEMS 16
+#endif
+#ifndef AMBER_SORT_MINB
+#define AMBER_SORT_MINB 3
+#endif
 constexpr int kSortThreads = 256;
-constexpr int kItems = 16;
+constexpr int kItems = AMBER_SORT_ITEMS;
 constexpr int kTile = kSortThreads * kItems;  // 4096 keys per tile
 constexpr int kLookWindow = 8;                // predecessors read per look-back round trip
 constexpr int kMaxRadix = 512;                // 9-bit digits
