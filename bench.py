@@ -44,6 +44,21 @@ def _workload(n: int, box: float) -> dict:
             "parallelism": "replicas"}
 
 
+def reduce_max(x: float, dist, device) -> float:
+    """Max of a per-rank scalar over all ranks (the slowest rank sets the time)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(cells_per_rank: int, world_size: int, ms_max: float) -> float:
+    """Cells per second of the whole job: every rank's cells over the slowest rank's time."""
+    return cells_per_rank * world_size / (ms_max / 1e3)
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -263,10 +278,7 @@ def run_amber(args):
     st = ctx.sync_status()
     if st != 0:
         raise RuntimeError(f"device status after timed region: {B.status_string(st)}")
-    t = torch.tensor([ms], device="cuda")
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
+    ms_max = reduce_max(ms, dist, "cuda")
 
     # --- end to end through the public API with pinned host buffers
     S_h = S.cpu().pin_memory()
@@ -287,10 +299,7 @@ def run_amber(args):
     f1.record(stream)
     barrier()
     e2e_ms = f0.elapsed_time(f1) / e_steps
-    t2 = torch.tensor([e2e_ms], device="cuda")
-    if dist is not None:
-        dist.all_reduce(t2, op=dist.ReduceOp.MAX)
-    e2e_ms = float(t2.item())
+    e2e_ms = reduce_max(e2e_ms, dist, "cuda")
 
     launches_per_step = sum(v[1] for v in prof.values()) / args.steps
     passes = ctx.sort_passes()
@@ -324,11 +333,11 @@ def run_amber(args):
         extras["serving"] = run_serving(torch)
 
     if rank == 0:
-        line = {"metric": METRIC, "value": C * ws / (ms_max / 1e3), "unit": "cells/s", "n_gpus": ws,
+        line = {"metric": METRIC, "value": whole_job_rate(C, ws, ms_max), "unit": "cells/s", "n_gpus": ws,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": _workload(n, box),
-                "e2e": {"value": C * ws / (e2e_ms / 1e3), "unit": "cells/s", "h2d_bytes_per_step": 8 * C,
+                "e2e": {"value": whole_job_rate(C, ws, e2e_ms), "unit": "cells/s", "h2d_bytes_per_step": 8 * C,
                         "d2h_bytes_per_step": 4 * C},
                 "gpu_launches": int(round(launches_per_step * args.steps)),
                 "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peaks["hbm_gbs"],

@@ -16,7 +16,10 @@ namespace amber {
 #ifndef AMBER_SORT_MINB
 #define AMBER_SORT_MINB 3
 #endif
-constexpr int kSortThreads = 256;
+#ifndef AMBER_SORT_THREADS
+#define AMBER_SORT_THREADS 256
+#endif
+constexpr int kSortThreads = AMBER_SORT_THREADS;  // 256 or 512 (divides the radix)
 constexpr int kItems = AMBER_SORT_ITEMS;
 constexpr int kTile = kSortThreads * kItems;  // 4096 keys per tile
 constexpr int kLookWindow = 8;                // predecessors read per look-back round trip
