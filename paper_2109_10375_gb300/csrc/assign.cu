@@ -144,14 +144,11 @@ __global__ void __launch_bounds__(1024) k_thresholds(unsigned long long* __restr
 // by k_thresholds so the total stays below 2^62.  Each cell loses less than
 // 2^-s, so over n cells F_n is off by less than n 2^-s / T <= n 2^-62 (2e-10
 // relative at 2^30 cells) -- far inside an FP64 running sum's own error.
-__device__ __forceinline__ unsigned long long mass_fix(float m, int s) {
-  const uint32_t b = __float_as_uint(m);
-  const uint32_t e = (b >> 23) & 0xffu;
-  if ((b & 0x80000000u) || e >= 127u + 40u) return 0ull;  // flagged by the mass total pass
-  const unsigned long long mant = (e == 0) ? (b & 0x7fffffu) : ((b & 0x7fffffu) | 0x800000u);
-  const int sh = (int)(e == 0 ? 1u : e) - 150 + s;
-  if (sh >= 0) return mant << sh;
-  return sh > -64 ? (mant >> (-sh)) : 0ull;
+// scale = 2^s.  Scaling by a power of two is exact and the conversion
+// truncates, so this is floor(m 2^s) (below 2^62 for every valid mass, since
+// m <= T); masses the total pass flagged count as 0.
+__device__ __forceinline__ unsigned long long mass_fix(float m, float scale) {
+  return (m >= 0.0f && m < 1099511627776.0f) ? __float2ull_rz(m * scale) : 0ull;
 }
 
 // Look-back word of a scan tile: 2 flag bits over a 62-bit prefix.
@@ -191,7 +188,7 @@ __global__ void __launch_bounds__(kScanThreads, 3) k_scan_assign(const ScanArgs 
   const bool side_b = a.pick && ((*a.pick - 1) & 1);
   const uint32_t* order = side_b ? a.order_b : a.order;
   const float* mass = side_b ? a.mass_b : a.mass;
-  const int qs = *a.qshift;
+  const float qs = __int_as_float((127 + *a.qshift) << 23);  // 2^s, s in [-2, 64]
 
   // order (and rank-order masses): coalesced striped loads -> padded shared
   // memory -> a blocked run of IT consecutive ranks per thread

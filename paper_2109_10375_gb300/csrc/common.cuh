@@ -124,6 +124,16 @@ inline bool first_use_on_device(std::atomic<unsigned long long>& mask) {
 
 // L2 eviction-priority policies for loads and stores that should (evict_last)
 // or should not (evict_first) keep their lines in L2.
+// Bulk L2 prefetch of the 16-byte-aligned part of [p, p + bytes) (the bulk
+// copy engine takes only aligned addresses and sizes).  A hint only; nothing
+// waits for it.
+__device__ __forceinline__ void prefetch_l2_bulk(const void* p, uint32_t bytes) {
+  const unsigned long long b = ((unsigned long long)p + 15ull) & ~15ull;
+  const unsigned long long e = ((unsigned long long)p + bytes) & ~15ull;
+  if (e > b)
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(b), "r"((uint32_t)(e - b)) : "memory");
+}
+
 __device__ __forceinline__ unsigned long long l2_evict_last() {
   unsigned long long p;
   asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));

@@ -10,22 +10,21 @@ namespace amber {
 typedef unsigned __int128 u128;
 
 // mass -> round-down fixed point; flags negative, NaN/Inf and >= 2^40.
+// One float-to-integer conversion at the largest of three power-of-two scales
+// 2^k (k = 0, 40, 64) that keeps m 2^k below 2^64, then a constant shift by
+// 64 - k.  Scaling by 2^k is exact, and in each range the float is a whole
+// multiple of 2^-k (m >= 2^24: integral; m >= 1: ulp >= 2^-23; m >= 2^-41:
+// ulp >= 2^-64), so the result is floor(m 2^64) exactly -- the conversion runs
+// on the XU pipe instead of bit surgery on the integer ALU.
 __device__ __forceinline__ u128 mass_q64(float m, bool& bad) {
-  const uint32_t b = __float_as_uint(m);
-  if (b & 0x80000000u) {
-    if (b != 0x80000000u) bad = true;  // negative (but -0 is zero)
-    return 0;
-  }
-  const uint32_t e = b >> 23;
-  if (e >= 127u + 40u) {  // >= 2^40, Inf or NaN
-    bad = true;
-    return 0;
-  }
-  const uint64_t mant = (e == 0) ? (b & 0x7fffffu) : ((b & 0x7fffffu) | 0x800000u);
-  const int sh = (int)(e == 0 ? 1u : e) - 150 + 64;  // value = mant 2^(e-150), scaled by 2^64
-  if (sh >= 0) return (u128)mant << sh;
-  if (sh <= -24) return 0;
-  return (u128)(mant >> (-sh));
+  const bool ok = m >= 0.0f && m < 1099511627776.0f;  // [0, 2^40); false for NaN
+  bad |= !ok;
+  const float v = ok ? m : 0.0f;
+  const bool big = v >= 16777216.0f, mid = v >= 1.0f;
+  const unsigned long long x = __float2ull_rz(v * (big ? 1.0f : mid ? 1099511627776.0f : 18446744073709551616.0f));
+  const unsigned long long lo = big ? 0ull : mid ? (x << 24) : x;
+  const unsigned long long hi = big ? x : mid ? (x >> 40) : 0ull;
+  return ((u128)hi << 64) | (u128)lo;
 }
 
 __device__ __forceinline__ u128 shfl_u128(u128 v, int src) {

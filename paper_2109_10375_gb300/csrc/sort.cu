@@ -85,6 +85,13 @@ __global__ void __launch_bounds__(256) k_sort_histogram(const SRC* __restrict__ 
   for (int i = threadIdx.x; i < P * R; i += blockDim.x) (&h[0][0])[i] = 0;
   __syncthreads();
   const K kmin = (K)ctrl->kmin;
+  // digit positions the key range needs (the rest stay zero and are never read)
+  int np = 0;
+  {
+    const K range = (K)ctrl->kmax - kmin;
+    while (np < P && (RB * np >= (int)(8 * sizeof(K)) || (range >> (RB * np)) != 0)) ++np;
+    if (np < 1) np = 1;
+  }
   bool bad = false;
   const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
   const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -104,6 +111,7 @@ __global__ void __launch_bounds__(256) k_sort_histogram(const SRC* __restrict__ 
       const K key = ok ? K(enc_desc(x[e], bad) - kmin) : K(0);
 #pragma unroll
       for (int p = 0; p < P; ++p) {
+        if (p >= np) break;
         const unsigned d = (unsigned)(key >> (RB * p)) & (R - 1);
         if (all_ok) hist_add(h[p], d);
         else if (ok) atomicAdd(&h[p][d], 1u);
@@ -113,7 +121,8 @@ __global__ void __launch_bounds__(256) k_sort_histogram(const SRC* __restrict__ 
   for (int64_t i = nvec * V + gtid; i < n; i += nthreads) {  // ragged tail
     const K key = K(enc_desc(J[i], bad) - kmin);
 #pragma unroll
-    for (int p = 0; p < P; ++p) atomicAdd(&h[p][(unsigned)(key >> (RB * p)) & (R - 1)], 1u);
+    for (int p = 0; p < P; ++p)
+      if (p < np) atomicAdd(&h[p][(unsigned)(key >> (RB * p)) & (R - 1)], 1u);
   }
   __syncthreads();
   for (int i = threadIdx.x; i < P * R; i += blockDim.x) {
@@ -197,14 +206,21 @@ __global__ void __launch_bounds__(kSortThreads, AMBER_SORT_MINB) k_sort_pass(con
   for (int i = tid; i < NW * R; i += kSortThreads) whist[i] = 0;
   __syncthreads();
   const uint32_t tile = s_tile;
-  const int64_t start = (int64_t)tile * kTile;
-  const int64_t n = a.n;
+  // n <= 2^30, so every cell index and tile position fits 32 bits
+  const uint32_t start = tile * (uint32_t)kTile;
+  const uint32_t n = (uint32_t)a.n;
   const int shift = RB * a.pass;
+  if (tid == 0) {
+    // the payloads are read only after the ranking: start pulling them into L2
+    const uint32_t bytes = (n - start < (uint32_t)kTile ? n - start : (uint32_t)kTile) * 4u;
+    if constexpr (MASS) prefetch_l2_bulk(a.min + start, bytes);
+    if constexpr (!FIRST) prefetch_l2_bulk(a.vin + start, bytes);
+  }
   if (a.lb_next) {
 #pragma unroll
     for (int j = 0; j < DPT; ++j) a.lb_next[(int64_t)tile * R + j * kSortThreads + tid] = 0;
   }
-  const int64_t wbase = start + warp * kItems * 32 + lane;  // item it at wbase + 32 it
+  const uint32_t wbase = start + warp * kItems * 32 + lane;  // item it at wbase + 32 it
   const K kmin = FIRST ? (K)a.ctrl->kmin : K(0);
 
   // ---- keys (warp-striped) and their local ranks, packed rank | digit << 16
@@ -213,7 +229,7 @@ __global__ void __launch_bounds__(kSortThreads, AMBER_SORT_MINB) k_sort_pass(con
   bool bad = false;
 #pragma unroll
   for (int it = 0; it < kItems; ++it) {
-    const int64_t g = wbase + 32 * it;
+    const uint32_t g = wbase + 32 * it;
     const bool ok = g < n;
     if constexpr (FIRST) key[it] = ok ? K(enc_desc(reinterpret_cast<const SRC*>(a.J)[g], bad) - kmin) : K(0);
     else key[it] = ok ? reinterpret_cast<const K*>(a.kin)[g] : K(0);
@@ -229,12 +245,13 @@ __global__ void __launch_bounds__(kSortThreads, AMBER_SORT_MINB) k_sort_pass(con
       // lanes holding the same digit (out-of-range lanes group apart)
       peers = __match_any_sync(0xffffffffu, ok ? d : 0x10000u);
     } else {
-      // the same set from one ballot per digit bit
+      // the same set from one ballot per digit bit: keep the lanes whose bit
+      // agrees (bit - 1 is all ones exactly when the bit is clear)
       peers = __ballot_sync(0xffffffffu, ok);
 #pragma unroll
       for (int b = 0; b < RB; ++b) {
-        const unsigned bb = __ballot_sync(0xffffffffu, (d >> b) & 1u);
-        peers &= ((d >> b) & 1u) ? bb : ~bb;
+        const unsigned bit = (d >> b) & 1u;
+        peers &= __ballot_sync(0xffffffffu, bit) ^ (bit - 1u);
       }
     }
     uint32_t base = 0;
@@ -287,21 +304,33 @@ __global__ void __launch_bounds__(kSortThreads, AMBER_SORT_MINB) k_sort_pass(con
     }
   }
 
-  // ---- keys and payloads into shared memory in tile-sorted order; payloads
-  // are loaded here so they never occupy registers during the ranking
-  u128 msum = 0;
+  // ---- keys, then payloads, into shared memory in tile-sorted order.  The
+  // payloads are loaded only now (their L2 prefetch was issued at the start),
+  // all kItems at once into the registers the keys just freed.
 #pragma unroll
   for (int it = 0; it < kItems; ++it) {
     if (rd[it] == 0xffffffffu) continue;
     const unsigned dd = rd[it] >> 16;
-    const uint32_t p = dstart[dd] + whist[warp * R + dd] + (rd[it] & 0xffffu);
-    const int64_t g = wbase + 32 * it;
-    skey[p] = key[it];
-    sval[p] = FIRST ? (uint32_t)g : a.vin[g];
+    rd[it] = dstart[dd] + whist[warp * R + dd] + (rd[it] & 0xffffu);  // tile position
+    skey[rd[it]] = key[it];
+  }
+  uint32_t pv[kItems];
+  float pm[kItems];
+#pragma unroll
+  for (int it = 0; it < kItems; ++it) {
+    const uint32_t g = wbase + 32 * it;
+    const bool ok = rd[it] != 0xffffffffu;
+    pv[it] = FIRST ? g : (ok ? a.vin[g] : 0u);
+    if constexpr (MASS) pm[it] = ok ? a.min[g] : 0.0f;
+  }
+  u128 msum = 0;
+#pragma unroll
+  for (int it = 0; it < kItems; ++it) {
+    if (rd[it] == 0xffffffffu) continue;
+    sval[rd[it]] = pv[it];
     if constexpr (MASS) {
-      const float mv = a.min[g];
-      smass[p] = mv;
-      if constexpr (FIRST) msum += mass_q64(mv, bad);
+      smass[rd[it]] = pm[it];
+      if constexpr (FIRST) msum += mass_q64(pm[it], bad);
     }
   }
   if constexpr (FIRST && MASS) {
@@ -362,7 +391,7 @@ __global__ void __launch_bounds__(kSortThreads, AMBER_SORT_MINB) k_sort_pass(con
   }
 
   // ---- write out: consecutive positions of one digit go to consecutive addresses
-  const int cnt_tile = (int)(n - start < (int64_t)kTile ? n - start : (int64_t)kTile);
+  const int cnt_tile = (int)(n - start < (uint32_t)kTile ? n - start : (uint32_t)kTile);
   K* kout = reinterpret_cast<K*>(a.kout);
   // the last needed pass writes the order to vfinal when given, else to its
   // own parity's buffers (which it does not read)
