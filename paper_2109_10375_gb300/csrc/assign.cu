@@ -144,11 +144,17 @@ __global__ void __launch_bounds__(1024) k_thresholds(unsigned long long* __restr
 // by k_thresholds so the total stays below 2^62.  Each cell loses less than
 // 2^-s, so over n cells F_n is off by less than n 2^-s / T <= n 2^-62 (2e-10
 // relative at 2^30 cells) -- far inside an FP64 running sum's own error.
-// scale = 2^s.  Scaling by a power of two is exact and the conversion
-// truncates, so this is floor(m 2^s) (below 2^62 for every valid mass, since
-// m <= T); masses the total pass flagged count as 0.
+// scale = 2^s: scaling by a power of two is exact, so this is floor_u64 of
+// m 2^s (below 2^62 for every valid mass, since m <= T); masses the total pass
+// flagged count as 0.
 __device__ __forceinline__ unsigned long long mass_fix(float m, float scale) {
-  return (m >= 0.0f && m < 1099511627776.0f) ? __float2ull_rz(m * scale) : 0ull;
+  return (m >= 0.0f && m < 1099511627776.0f) ? floor_u64(m * scale) : 0ull;
+}
+
+// u64 -> float from its two 32-bit halves (within two roundings; only the
+// interpolation weight uses it)
+__device__ __forceinline__ float u64_to_float(unsigned long long x) {
+  return fmaf(__uint2float_rn((uint32_t)(x >> 32)), 4294967296.0f, __uint2float_rn((uint32_t)x));
 }
 
 // Look-back word of a scan tile: 2 flag bits over a 62-bit prefix.
@@ -166,15 +172,35 @@ __device__ __forceinline__ void st_relaxed_u64(unsigned long long* p, unsigned l
   asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
+// One round of a warp-wide 32-ary search for c = #{j : X_j >= v} (X
+// non-increasing), c known to lie in [lo, hi]: lane k probes lo + k step; the
+// probes that hold form a prefix, and the range shrinks below step.
+__device__ __forceinline__ void count_ge_round(const unsigned long long* __restrict__ X, unsigned long long v,
+                                               int& lo, int& hi, int lane) {
+  if (lo >= hi) return;  // warp-uniform
+  const int step = (hi - lo + 31) >> 5;
+  const int q = lo + lane * step;
+  const bool t = q < hi && X[q] >= v;
+  const int c = __popc(__ballot_sync(0xffffffffu, t));
+  const int nlo = c ? lo + (c - 1) * step + 1 : lo;
+  const int nhi = min(hi, lo + c * step);
+  lo = nlo;
+  hi = nhi;
+}
+
+constexpr int kScanWin = 64;  // thresholds one tile may span, staged in shared memory
+
 template <bool GATHER, bool WANT_F>
-__global__ void __launch_bounds__(kScanThreads, 3) k_scan_assign(const ScanArgs a) {
+__global__ void __launch_bounds__(kScanThreads, 4) k_scan_assign(const ScanArgs a) {
   constexpr int NT = kScanThreads, IT = kScanItems, TILE = kScanTile;
   __shared__ uint32_t sord[TILE + TILE / 32];
   __shared__ float smass[TILE + TILE / 32];
   __shared__ unsigned long long wtot[NT / 32];
   __shared__ unsigned long long s_excl;
   __shared__ uint32_t s_tile;
-  __shared__ int s_cx[2];
+  __shared__ int s_cx[3];  // c(M_last), c(M_first), first staged threshold (-1: none)
+  __shared__ unsigned long long sX[kScanWin];
+  __shared__ float sInv[kScanWin];
   __shared__ uint32_t scnt[kMaxBuckets];
   __shared__ uint32_t soff[kMaxBuckets + 1];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -182,13 +208,24 @@ __global__ void __launch_bounds__(kScanThreads, 3) k_scan_assign(const ScanArgs 
   for (int b = tid; b < a.nbuckets; b += NT) scnt[b] = 0;
   __syncthreads();
   const uint32_t tile = s_tile;
-  const int64_t start = (int64_t)tile * TILE;
-  const int64_t n = a.n;
-  const int cnt = (int)(n - start < (int64_t)TILE ? n - start : (int64_t)TILE);
+  // n <= 2^30: positions fit 32 bits
+  const uint32_t start = tile * (uint32_t)TILE;
+  const uint32_t n = (uint32_t)a.n;
+  const int cnt = (int)(n - start < (uint32_t)TILE ? n - start : (uint32_t)TILE);
   const bool side_b = a.pick && ((*a.pick - 1) & 1);
   const uint32_t* order = side_b ? a.order_b : a.order;
   const float* mass = side_b ? a.mass_b : a.mass;
+  if (tid == 0 && a.ahead) {
+    // order and masses of the tile about one resident wave ahead into L2
+    const uint32_t fs = (tile + a.ahead) * (uint32_t)TILE;
+    if (fs < n) {
+      const uint32_t fb = n - fs < (uint32_t)TILE ? n - fs : (uint32_t)TILE;
+      prefetch_l2_bulk(order + fs, fb * 4u);
+      if constexpr (!GATHER) prefetch_l2_bulk(mass + fs, fb * 4u);
+    }
+  }
   const float qs = __int_as_float((127 + *a.qshift) << 23);  // 2^s, s in [-2, 64]
+  const int M = a.n_table;
 
   // order (and rank-order masses): coalesced striped loads -> padded shared
   // memory -> a blocked run of IT consecutive ranks per thread
@@ -227,29 +264,38 @@ __global__ void __launch_bounds__(kScanThreads, 3) k_scan_assign(const ScanArgs 
   }
   const unsigned long long thr_excl = wpre + x - run;
 
-  // decoupled look-back by warp 0: each lane reads one predecessor's word, so
-  // a round trip covers 32 tiles; aggregates are summed back to the nearest
-  // inclusive prefix
+  // warp 0 publishes the tile's aggregate and starts its look-back load; the
+  // bucket slots of every cell (which need no prefix) are taken meanwhile
+  unsigned long long lbw = 0;
+  int64_t lbt = (int64_t)tile - 1;
   if (warp == 0) {
-    unsigned long long* me = a.state + tile;
-    if (lane == 0) st_relaxed_u64(me, (tile == 0 ? kScanInc : kScanAgg) | tile_sum);
+    if (lane == 0) st_relaxed_u64(a.state + tile, (tile == 0 ? kScanInc : kScanAgg) | tile_sum);
+    lbw = (lbt - lane >= 0) ? ld_relaxed_u64(a.state + lbt - lane) : kScanInc;
+  }
+  uint32_t slot[IT];
+#pragma unroll
+  for (int i = 0; i < IT; ++i)
+    slot[i] = (tid * IT + i < cnt) ? atomicAdd(&scnt[cell[i] >> a.bucket_shift], 1u) : 0xffffffffu;
+  __syncthreads();
+
+  if (warp == 0) {
+    // decoupled look-back: each lane holds one predecessor's word, so a round
+    // trip covers 32 tiles; aggregates are summed back to the nearest
+    // inclusive prefix
     unsigned long long excl = 0;
-    int64_t t = (int64_t)tile - 1;
     unsigned spins = 0;
-    while (t >= 0) {
-      const int64_t tt = t - lane;
-      const unsigned long long w = (tt >= 0) ? ld_relaxed_u64(a.state + tt) : kScanInc;
-      const unsigned long long f = w & kScanMask;
+    while (true) {
+      const unsigned long long f = lbw & kScanMask;
       const unsigned inc_mask = __ballot_sync(0xffffffffu, f == kScanInc);
       const unsigned stop_mask = inc_mask | __ballot_sync(0xffffffffu, f == 0ull);
       const int first = stop_mask ? __ffs(stop_mask) - 1 : 32;
       const bool found = first < 32 && ((inc_mask >> first) & 1u);
-      unsigned long long part = (lane < first || (found && lane == first)) ? (w & kScanValue) : 0ull;
+      unsigned long long part = (lane < first || (found && lane == first)) ? (lbw & kScanValue) : 0ull;
 #pragma unroll
       for (int o = 16; o >= 1; o >>= 1) part += __shfl_down_sync(0xffffffffu, part, o);
       excl += __shfl_sync(0xffffffffu, part, 0);
       if (found) break;
-      t -= first;
+      lbt -= first;
       if (first < 32) {
         if (++spins >= a.spin_limit) {
           if (lane == 0) raise_status(a.status, AMBER_ERR_DEVICE_TIMEOUT);
@@ -257,100 +303,101 @@ __global__ void __launch_bounds__(kScanThreads, 3) k_scan_assign(const ScanArgs 
         }
         __nanosleep(20);
       }
+      lbw = (lbt - lane >= 0) ? ld_relaxed_u64(a.state + lbt - lane) : kScanInc;
     }
     if (lane == 0) {
-      if (tile != 0) st_relaxed_u64(me, kScanInc | ((excl + tile_sum) & kScanValue));
+      if (tile != 0) st_relaxed_u64(a.state + tile, kScanInc | ((excl + tile_sum) & kScanValue));
       s_excl = excl;
-      // bracket the whole tile: #{j : X_j >= M} before and after it
-      const unsigned long long m_first = excl, m_last = excl + tile_sum;
-      int lo = 0, hi = a.n_table;
-      while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (a.Xq[mid] >= m_first) lo = mid + 1; else hi = mid;
+    }
+    // bracket the whole tile: c(M) = #{j : X_j >= M} at its first and last
+    // prefix, both searched at once (three round trips for 2000 thresholds)
+    int lo0 = 0, hi0 = M, lo1 = 0, hi1 = M;
+    while (lo0 < hi0 || lo1 < hi1) {
+      count_ge_round(a.Xq, excl, lo0, hi0, lane);
+      count_ge_round(a.Xq, excl + tile_sum, lo1, hi1, lane);
+    }
+    // thresholds the tile's cells can touch: X_j for j in [c_last - 1, c_first]
+    const int base = max(lo1 - 1, 0), L = min(lo0, M - 1) - base + 1;
+    const bool stage = L <= kScanWin;
+    if (stage) {
+      for (int i = lane; i < L; i += 32) {
+        sX[i] = a.Xq[base + i];
+        sInv[i] = (base + i < M - 1) ? a.inv_dx[base + i] : 0.0f;
       }
-      s_cx[0] = lo;
-      hi = lo;
-      lo = 0;
-      while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (a.Xq[mid] >= m_last) lo = mid + 1; else hi = mid;
+    }
+    if (lane == 0) {
+      s_cx[0] = lo1;
+      s_cx[1] = lo0;
+      s_cx[2] = stage ? base : -1;
+    }
+  } else if (warp == 1) {
+    // tile-local bucket starts (exclusive scan over the buckets) and this
+    // tile's row of the offset table
+    uint32_t carry = 0;
+    uint16_t* row = a.btab + (int64_t)tile * (a.nbuckets + 1);
+    for (int b0 = 0; b0 < a.nbuckets; b0 += 32) {
+      const int b = b0 + lane;
+      const uint32_t c = b < a.nbuckets ? scnt[b] : 0u;
+      uint32_t y = c;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t z = __shfl_up_sync(0xffffffffu, y, o);
+        if (lane >= o) y += z;
       }
-      s_cx[1] = lo;
+      if (b < a.nbuckets) {
+        soff[b] = carry + y - c;
+        row[b] = (uint16_t)(carry + y - c);
+      }
+      carry += __shfl_sync(0xffffffffu, y, 31);
+    }
+    if (lane == 0) {
+      soff[a.nbuckets] = carry;
+      row[a.nbuckets] = (uint16_t)carry;
     }
   }
   __syncthreads();
   unsigned long long Mn = s_excl + thr_excl;
-  const int M = a.n_table;
   const double invT = WANT_F ? 1.0 / (double)*a.qtotal : 0.0;
+  const int cx_lo = s_cx[0], cx_hi = s_cx[1], wb = s_cx[2];
+  // threshold j from the staged window when the tile fits it
+  auto Xj = [&](int j) -> unsigned long long { return wb >= 0 ? sX[j - wb] : a.Xq[j]; };
+  auto Ij = [&](int j) -> float { return wb >= 0 ? sInv[j - wb] : a.inv_dx[j]; };
 
   // bracket: cx = #{j : X_j >= M_n}; X is non-increasing in j and M_n grows
-  // with rank, so each thread searches the tile's range once, then walks down
-  const int cx_hi = s_cx[0], cx_lo = s_cx[1];
-  float zv[IT];
-  uint32_t slot[IT];
+  // with rank, so each thread searches the tile's range once, then walks
+  // down.  Each (cell, z) goes straight to its bucket-ordered staging slot
+  // (order and masses were consumed above, so their shared arrays are free).
+  uint32_t* scell = sord;
+  float* sz = smass;
   int cx = -1;
 #pragma unroll
   for (int i = 0; i < IT; ++i) {
     const int p = tid * IT + i;
-    zv[i] = 0.0f;
-    slot[i] = 0xffffffffu;
     if (p >= cnt) continue;
     Mn += mass_fix(mv[i], qs);
     if (cx < 0) {
       int lo = cx_lo, hi = cx_hi;
       while (lo < hi) {
         const int mid = (lo + hi) >> 1;
-        if (a.Xq[mid] >= Mn) lo = mid + 1; else hi = mid;
+        if (Xj(mid) >= Mn) lo = mid + 1; else hi = mid;
       }
       cx = lo;
     } else {
-      while (cx > 0 && a.Xq[cx - 1] < Mn) --cx;
+      while (cx > 0 && Xj(cx - 1) < Mn) --cx;
     }
     const int j = cx - 1;
     float z;
     if (j < 0) z = a.z_lo;
     else if (j == M - 1) z = a.z_hi;
     else {
-      float t = __ull2float_rn(a.Xq[j] - Mn) * a.inv_dx[j];
+      float t = u64_to_float(Xj(j) - Mn) * Ij(j);
       t = fminf(fmaxf(t, 0.0f), 0.99999994f);
       z = a.z_lo + ((float)j + t) * a.dzt;
     }
-    zv[i] = z;
     if (WANT_F) a.F[start + p] = (double)Mn * invT;
-    slot[i] = atomicAdd(&scnt[cell[i] >> a.bucket_shift], 1u);
-  }
-  __syncthreads();
-  // tile-local bucket starts (exclusive scan over the buckets) and this
-  // tile's row of the offset table
-  if (warp == 0) {
-    uint32_t carry = 0;
-    for (int b0 = 0; b0 < a.nbuckets; b0 += 32) {
-      const int b = b0 + lane;
-      const uint32_t c = b < a.nbuckets ? scnt[b] : 0u;
-      uint32_t x = c;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-      }
-      if (b < a.nbuckets) soff[b] = carry + x - c;
-      carry += __shfl_sync(0xffffffffu, x, 31);
-    }
-    if (lane == 0) soff[a.nbuckets] = carry;
-  }
-  __syncthreads();
-  uint16_t* row = a.btab + (int64_t)tile * (a.nbuckets + 1);
-  for (int b = tid; b <= a.nbuckets; b += NT) row[b] = (uint16_t)soff[b];
-  // stage (cell, z) in bucket order, then write the tile's segment contiguously
-  uint32_t* scell = sord;                       // order is no longer needed
-  float* sz = smass;
-  __syncthreads();
-#pragma unroll
-  for (int i = 0; i < IT; ++i) {
-    if (slot[i] == 0xffffffffu) continue;
     const uint32_t q = soff[cell[i] >> a.bucket_shift] + slot[i];
     scell[q + (q >> 5)] = cell[i];
-    sz[q + (q >> 5)] = zv[i];
+    sz[q + (q >> 5)] = z;
   }
   __syncthreads();
   // the pairs are read back only after the whole scan: keep them out of L2
@@ -474,6 +521,7 @@ cudaError_t assign_impl(const AssignWork& w, const uint32_t* order, const float*
   a.btab = w.btab;
   a.status = status;
   a.spin_limit = spin_limit;
+  a.ahead = (uint32_t)w.num_sms * 4;  // resident scan CTAs: 4 per SM
   prof_begin(prof, PK_SCAN_ASSIGN, s);
   if (mass_in_rank_order) {
     if (F) k_scan_assign<false, true><<<(unsigned)tiles, kScanThreads, 0, s>>>(a);

@@ -62,6 +62,7 @@ struct ScanArgs {
   uint16_t* btab;
   unsigned int* status;
   unsigned int spin_limit;
+  uint32_t ahead;  // tiles ahead whose order and masses are prefetched into L2 (0: none)
 };
 
 void bucket_plan(int64_t n, int* nbuckets, int* shift);

@@ -215,6 +215,16 @@ __global__ void __launch_bounds__(kSortThreads, AMBER_SORT_MINB) k_sort_pass(con
     const uint32_t bytes = (n - start < (uint32_t)kTile ? n - start : (uint32_t)kTile) * 4u;
     if constexpr (MASS) prefetch_l2_bulk(a.min + start, bytes);
     if constexpr (!FIRST) prefetch_l2_bulk(a.vin + start, bytes);
+    // and all inputs of the tile about one resident wave ahead, which the next
+    // CTA on this SM will most likely take (tiles go out in ticket order)
+    const uint32_t fs = (tile + a.ahead) * (uint32_t)kTile;
+    if (a.ahead && fs < n) {
+      const uint32_t fb = n - fs < (uint32_t)kTile ? n - fs : (uint32_t)kTile;
+      if constexpr (FIRST) prefetch_l2_bulk(reinterpret_cast<const SRC*>(a.J) + fs, fb * (uint32_t)sizeof(SRC));
+      else prefetch_l2_bulk(reinterpret_cast<const K*>(a.kin) + fs, fb * (uint32_t)sizeof(K));
+      if constexpr (MASS) prefetch_l2_bulk(a.min + fs, fb * 4u);
+      if constexpr (!FIRST) prefetch_l2_bulk(a.vin + fs, fb * 4u);
+    }
   }
   if (a.lb_next) {
 #pragma unroll
@@ -298,7 +308,10 @@ __global__ void __launch_bounds__(kSortThreads, AMBER_SORT_MINB) k_sort_pass(con
         wpre += (w < warp) ? wsum[w] : 0u;
         tot += wsum[w];
       }
-      dstart[j * kSortThreads + tid] = carry + wpre + x - cnt[j];
+      const uint32_t ds = carry + wpre + x - cnt[j];
+      dstart[j * kSortThreads + tid] = ds;
+#pragma unroll
+      for (int w = 0; w < NW; ++w) whist[w * R + j * kSortThreads + tid] += ds;
       carry += tot;
       __syncthreads();
     }
@@ -311,7 +324,7 @@ __global__ void __launch_bounds__(kSortThreads, AMBER_SORT_MINB) k_sort_pass(con
   for (int it = 0; it < kItems; ++it) {
     if (rd[it] == 0xffffffffu) continue;
     const unsigned dd = rd[it] >> 16;
-    rd[it] = dstart[dd] + whist[warp * R + dd] + (rd[it] & 0xffffu);  // tile position
+    rd[it] = whist[warp * R + dd] + (rd[it] & 0xffffu);  // tile position
     skey[rd[it]] = key[it];
   }
   uint32_t pv[kItems];
@@ -509,6 +522,7 @@ cudaError_t rank_impl(const SortWork& w, const SRC* J, int64_t n, uint32_t* orde
     a.tile_mass = tile_mass;
     a.status = status;
     a.spin_limit = spin_limit;
+    a.ahead = (uint32_t)w.num_sms * AMBER_SORT_MINB;
     prof_begin(prof, PK_SORT_PASS, s);
     if (p == 0) {
       if (with_mass) launch_pass<SRC, true, true>(a, tiles, s);

@@ -58,6 +58,7 @@ struct PassArgs {
   unsigned long long* tile_mass;   // first pass with masses: per-tile 128-bit sums (lo, hi)
   unsigned int* status;
   unsigned int spin_limit;
+  uint32_t ahead;  // tiles ahead whose inputs are prefetched into L2 (0: none)
 };
 
 int64_t sort_tiles(int64_t n);

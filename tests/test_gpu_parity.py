@@ -206,6 +206,24 @@ def test_assign_vs_oracle_given_order(ctx, B, n):
     np.testing.assert_allclose(F.cpu().numpy(), Fo, rtol=0, atol=n * 2.0 ** -60 + 1e-15)
 
 
+@pytest.mark.parametrize("n_table,n", [(2, 50_000), (3, 50_000), (2048, 200_000), (2049, 200_000),
+                                       (10_000, 200_000), (65_536, 100_000)])
+def test_assign_table_sizes(ctx, B, n_table, n):
+    # the scan stages the thresholds a tile spans in shared memory when they
+    # are at most 64 (2000-entry tables over 200000 cells: ~41 per tile), else
+    # reads the table in global memory (10000 and 65536 entries)
+    g = np.random.default_rng(n_table)
+    mass = g.uniform(0.01, 8.0, n).astype(np.float32)
+    order = g.permutation(n).astype(np.int32)
+    h = B.history(8.0, 4.0, 3.0, n_table=n_table)
+    z = ctx.assign_zre(torch.from_numpy(order).cuda(), torch.from_numpy(mass).cuda(), h)
+    check_status(ctx, B)
+    t = O.history_table(8.0, 4.0, 3.0, n_table=n_table)
+    zo = O.assign_zre(order, mass.astype(np.float64), t)
+    bad, dmax = zre_mismatch(z.cpu().numpy(), zo)
+    assert bad == 0.0 and dmax < 5e-5, (bad, dmax)
+
+
 def test_assign_equal_mass_closed_form(ctx, B):
     n = 300_000
     order = np.arange(n)[::-1].copy().astype(np.int32)
