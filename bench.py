@@ -12,9 +12,10 @@ path), so value = all ranks' cells / max-over-ranks time.
 of the method) on a bounded sample of the same workload.
 
 At one GPU the line also carries "batched" (48 realisations of 128^3 and
-256^3 as a loop of plain solves vs one captured-graph launch) and "serving"
+256^3 as a loop of plain solves vs one captured-graph launch), "serving"
 (p50/p99 latency and cells/s of a Poisson request stream at 200 req/s over
-128^3/256^3/512^3 grids with cached rank orders); --no-extras skips both.
+128^3/256^3/512^3 grids with cached rank orders) and "library_context"
+(cuFFT and CUB timings at the same size); --no-extras skips them.
 """
 from __future__ import annotations
 
@@ -70,20 +71,80 @@ def _dist():
 # Reference arm: the FP64 CPU oracle on bounded samples
 # ---------------------------------------------------------------------------
 
-def oracle_sample_rate(n_sample: int, box: float, min_seconds: float, max_reps: int = 50):
+_ORACLE_ARGS = None
+
+
+def _oracle_init(S, m, box):
+    global _ORACLE_ARGS
+    _ORACLE_ARGS = (S, m, box)
+
+
+def _oracle_solve(_):
     from oracle import amber_oracle as O
-    from paper_2109_10375_gb300 import synth
-    S, m = synth.realisation(n_sample, box, 0)
-    S, m = S.double().numpy(), m.double().numpy()
-    t0 = time.perf_counter()
-    reps = 0
-    while True:
-        O.solve(S, m, box, L_MFP, *HIST)
-        reps += 1
-        el = time.perf_counter() - t0
-        if el >= min_seconds or reps >= max_reps:
-            break
-    return reps * n_sample ** 3 / el, reps, el
+    S, m, box = _ORACLE_ARGS
+    O.solve(S, m, box, L_MFP, *HIST)
+    return 1
+
+
+class OraclePool:
+    """The FP64 oracle, as it stands, one realisation per process on every host core.
+
+    Processes are spawned (never forked after CUDA is initialised) and take the
+    sample's fields once; numpy's FFT in the oracle is single-threaded, so each
+    process is one core."""
+
+    def __init__(self, n_sample: int, box: float, workers: int | None = None):
+        import multiprocessing as mp
+        from paper_2109_10375_gb300 import synth
+        S, m = synth.realisation(n_sample, box, 0)
+        self.S, self.m = S.double().numpy(), m.double().numpy()
+        self.box, self.ns = box, n_sample
+        self.workers = workers or os.cpu_count() or 1
+        for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+            os.environ.setdefault(v, "1")
+        self.pool = mp.get_context("spawn").Pool(self.workers, initializer=_oracle_init,
+                                                  initargs=(self.S, self.m, self.box))
+        self.pool.map(_oracle_solve, range(self.workers))  # start-up and imports, untimed
+
+    def single(self, min_seconds: float, max_reps: int = 50):
+        """Cells/s of one process solving one realisation after another."""
+        from oracle import amber_oracle as O
+        t0 = time.perf_counter()
+        reps = 0
+        while True:
+            O.solve(self.S, self.m, self.box, L_MFP, *HIST)
+            reps += 1
+            el = time.perf_counter() - t0
+            if el >= min_seconds or reps >= max_reps:
+                return reps * self.ns ** 3 / el, reps, el
+
+    def parallel(self, tasks: int):
+        """Wall time of `tasks` realisations spread over all processes."""
+        t0 = time.perf_counter()
+        self.pool.map(_oracle_solve, range(tasks), chunksize=1)
+        return time.perf_counter() - t0
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
+def oracle_baseline(n_sample: int, box: float, seconds: float) -> dict:
+    """cpu_baseline: all-core oracle throughput on a bounded sample (single-core alongside)."""
+    pool = OraclePool(n_sample, box)
+    try:
+        one, reps1, el1 = pool.single(min(seconds / 3, 5.0))
+        per_task = n_sample ** 3 / one
+        rounds = max(1, int(round(seconds / per_task)))
+        tasks = rounds * pool.workers
+        el = pool.parallel(tasks)
+    finally:
+        pool.close()
+    return {"value": tasks * n_sample ** 3 / el, "unit": "cells/s", "cores": pool.workers, "kind": "oracle",
+            "sample": f"{tasks} x {n_sample}^3 realisation(s) of the same recipe and cell size on "
+                      f"{pool.workers} processes, {el:.1f} s",
+            "single_core_value": one,
+            "single_core_sample": f"{reps1} x {n_sample}^3 in one process, {el1:.1f} s"}
 
 
 def run_reference(args):
@@ -94,23 +155,25 @@ def run_reference(args):
     box = 1000.0 * n / 1024
     ns = args.cpu_sample_n
     box_s = box * ns / n  # same cell size as the workload
-    from oracle import amber_oracle as O
-    from paper_2109_10375_gb300 import synth
-    S, m = synth.realisation(ns, box_s, 0)
-    S, m = S.double().numpy(), m.double().numpy()
-    for _ in range(args.warmup):
-        O.solve(S, m, box_s, L_MFP, *HIST)
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        O.solve(S, m, box_s, L_MFP, *HIST)
-    el = time.perf_counter() - t0
-    value = args.steps * ns ** 3 / el
-    sample = f"{ns}^3 realisation per step (same recipe and cell size), {args.steps} steps"
+    pool = OraclePool(ns, box_s)
+    try:
+        # a step: one realisation of the sample per host core, all at once
+        for _ in range(args.warmup):
+            pool.parallel(pool.workers)
+        el = 0.0
+        for _ in range(args.steps):
+            el += pool.parallel(pool.workers)
+    finally:
+        pool.close()
+    value = args.steps * pool.workers * ns ** 3 / el
+    sample = (f"{pool.workers} x {ns}^3 realisations per step (same recipe and cell size), one per process, "
+              f"{args.steps} steps")
     line = {"metric": METRIC, "value": value, "unit": "cells/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": _workload(n, box), "impl": "reference",
-            "cpu_baseline": {"value": value, "unit": "cells/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": "cells/s", "cores": pool.workers, "kind": "oracle",
+                             "sample": sample},
             "e2e": {"value": value, "unit": "cells/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -280,26 +343,67 @@ def run_amber(args):
         raise RuntimeError(f"device status after timed region: {B.status_string(st)}")
     ms_max = reduce_max(ms, dist, "cuda")
 
-    # --- end to end through the public API with pinned host buffers
+    # --- end to end through the public API with pinned host buffers.  Every
+    # step copies its inputs in, solves and copies z_re out; two buffer sets
+    # let one step's copies overlap the neighbouring steps' solves (H2D and
+    # D2H on their own streams, ordered by events).
     S_h = S.cpu().pin_memory()
     m_h = m.cpu().pin_memory()
-    z_h = torch.empty(S.shape, dtype=torch.float32).pin_memory()
-    S_d, m_d = torch.empty_like(S), torch.empty_like(m)
     del S, m
     torch.cuda.empty_cache()
-    e_steps = max(1, min(args.steps, 5))
+    z_h = [torch.empty(z.shape, dtype=torch.float32).pin_memory() for _ in range(2)]
+    S_d = [torch.empty(z.shape, device="cuda") for _ in range(2)]
+    m_d = [torch.empty(z.shape, device="cuda") for _ in range(2)]
+    z_d = [z, torch.empty_like(z)]
+    s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
+    ev_in = [torch.cuda.Event() for _ in range(2)]
+    ev_done = [torch.cuda.Event() for _ in range(2)]
+    ev_out = [torch.cuda.Event() for _ in range(2)]
+    e_steps = max(2, min(args.steps, 8))
     barrier()
     f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     f0.record(stream)
-    for _ in range(e_steps):
-        S_d.copy_(S_h, non_blocking=True)
-        m_d.copy_(m_h, non_blocking=True)
-        ctx.solve(S_d, m_d, box, L_MFP, h, out=z)
-        z_h.copy_(z, non_blocking=True)
+    s_in.wait_event(f0)
+    for i in range(e_steps):
+        b = i & 1
+        if i >= 2:
+            s_in.wait_event(ev_done[b])  # the solve of step i-2 has read S_d[b], m_d[b]
+        with torch.cuda.stream(s_in):
+            S_d[b].copy_(S_h, non_blocking=True)
+            m_d[b].copy_(m_h, non_blocking=True)
+            ev_in[b].record(s_in)
+        stream.wait_event(ev_in[b])
+        if i >= 2:
+            stream.wait_event(ev_out[b])  # z_d[b] of step i-2 is on the host
+        ctx.solve(S_d[b], m_d[b], box, L_MFP, h, out=z_d[b], stream=stream)
+        ev_done[b].record(stream)
+        s_out.wait_event(ev_done[b])
+        with torch.cuda.stream(s_out):
+            z_h[b].copy_(z_d[b], non_blocking=True)
+            ev_out[b].record(s_out)
+    stream.wait_event(ev_out[(e_steps - 1) & 1])
+    stream.wait_event(ev_out[(e_steps - 2) & 1])
     f1.record(stream)
     barrier()
     e2e_ms = f0.elapsed_time(f1) / e_steps
     e2e_ms = reduce_max(e2e_ms, dist, "cuda")
+    # the copies alone, for context
+    c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    c0.record(stream)
+    S_d[0].copy_(S_h, non_blocking=True)
+    m_d[0].copy_(m_h, non_blocking=True)
+    c1.record(stream)
+    torch.cuda.synchronize()
+    h2d_gbps = 8 * C / (c0.elapsed_time(c1) / 1e3) / 1e9
+    c0.record(stream)
+    z_h[0].copy_(z_d[0], non_blocking=True)
+    c1.record(stream)
+    torch.cuda.synchronize()
+    d2h_gbps = 4 * C / (c0.elapsed_time(c1) / 1e3) / 1e9
+    st = ctx.sync_status()
+    if st != 0:
+        raise RuntimeError(f"device status after end-to-end steps: {B.status_string(st)}")
+    del S_d, m_d, z_d, z_h, S_h, m_h
 
     launches_per_step = sum(v[1] for v in prof.values()) / args.steps
     passes = ctx.sort_passes()
@@ -319,18 +423,17 @@ def run_amber(args):
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         ns = args.cpu_sample_n
-        rate, reps, el = oracle_sample_rate(ns, box * ns / n, args.cpu_seconds)
-        cpu = {"value": rate, "unit": "cells/s", "cores": 1, "kind": "oracle",
-               "sample": f"{reps} x {ns}^3 realisation(s) of the same recipe and cell size, {el:.1f} s"}
+        cpu = oracle_baseline(ns, box * ns / n, args.cpu_seconds)
 
     extras = {}
     if rank == 0 and ws == 1 and not args.no_extras:
         ctx.close()
-        del z
         torch.cuda.empty_cache()
         extras["batched"] = run_batched(B, synth, torch)
         torch.cuda.empty_cache()
         extras["serving"] = run_serving(torch)
+        torch.cuda.empty_cache()
+        extras["library_context"] = run_library_context(torch, synth, n, box)
 
     if rank == 0:
         line = {"metric": METRIC, "value": whole_job_rate(C, ws, ms_max), "unit": "cells/s", "n_gpus": ws,
@@ -338,7 +441,9 @@ def run_amber(args):
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": _workload(n, box),
                 "e2e": {"value": whole_job_rate(C, ws, e2e_ms), "unit": "cells/s", "h2d_bytes_per_step": 8 * C,
-                        "d2h_bytes_per_step": 4 * C},
+                        "d2h_bytes_per_step": 4 * C, "ms_per_step": e2e_ms, "steps": e_steps,
+                        "overlap": "double-buffered: H2D and D2H streams overlap the neighbouring steps' solves",
+                        "h2d_GBps_alone": h2d_gbps, "d2h_GBps_alone": d2h_gbps},
                 "gpu_launches": int(round(launches_per_step * args.steps)),
                 "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peaks["hbm_gbs"],
                              "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": _traffic(dom, n),
@@ -417,6 +522,49 @@ def run_serving(torch, n_requests: int = 800, rate: float = 200.0):
                 "waits_for_hbm": srv.waiting_hbm})
     srv.close()
     return out
+
+
+def run_library_context(torch, synth, n: int, box: float, reps: int = 3):
+    """Library routines at the workload's size, for context only (not on the path):
+    cuFFT R2C + C2R through torch.fft, and torch.sort (CUB radix sort) of the
+    intensity with its int64 permutation."""
+    S, _ = synth.realisation(n, box, 0, device="cuda")
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    fft_ms = timed(lambda: torch.fft.irfftn(torch.fft.rfftn(S), s=S.shape))
+    torch.cuda.empty_cache()
+    sort_ms = timed(lambda: torch.sort(S.view(-1), descending=True, stable=True))
+    torch.cuda.empty_cache()
+    # the store pattern of the scatter back to cell order: every cell written
+    # once, in random order within windows of 2^23 consecutive cells taken one
+    # after another (torch's scatter_, one 4-byte store per element)
+    C = n ** 3
+    W = min(1 << 23, C)
+    g = torch.Generator(device="cuda")
+    g.manual_seed(11)
+    idx = torch.empty(C, dtype=torch.int64, device="cuda")
+    for w0 in range(0, C, W):
+        idx[w0:w0 + W] = torch.randperm(W, device="cuda", generator=g) + w0
+    src = S.view(-1)
+    dst = torch.empty_like(src)
+    store_ms = timed(lambda: dst.scatter_(0, idx, src))
+    del S, idx, src, dst
+    torch.cuda.empty_cache()
+    return {"what": f"library routines at {n}^3 for context (not on the path)",
+            "cufft_rfftn_irfftn_ms": fft_ms, "torch_sort_stable_ms": sort_ms,
+            "random_store": {"ms": store_ms, "stores_per_s": C / (store_ms / 1e3),
+                             "pattern": "torch scatter_ of every cell once, random within 2^23-cell windows"}}
 
 
 def main():

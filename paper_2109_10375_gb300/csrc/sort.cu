@@ -47,7 +47,8 @@ __device__ __forceinline__ unsigned lanemask_lt() {
 }
 
 // Count digit d of this lane into h[d]: a single add when the whole warp
-// agrees (the high digits of a narrow intensity range), else one per lane.
+// agrees (the top digit of a spatially smooth intensity field often does),
+// else one per lane.
 __device__ __forceinline__ void hist_add(uint32_t* h, unsigned d) {
   const unsigned d0 = __shfl_sync(0xffffffffu, d, 0);
   if (__all_sync(0xffffffffu, d == d0)) {
@@ -113,7 +114,8 @@ __global__ void __launch_bounds__(256) k_sort_histogram(const SRC* __restrict__ 
       for (int p = 0; p < P; ++p) {
         if (p >= np) break;
         const unsigned d = (unsigned)(key >> (RB * p)) & (R - 1);
-        if (all_ok) hist_add(h[p], d);
+        // only the top digit of a smooth field tends to agree across a warp
+        if (all_ok && p == np - 1) hist_add(h[p], d);
         else if (ok) atomicAdd(&h[p][d], 1u);
       }
     }
