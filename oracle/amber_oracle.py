@@ -30,6 +30,13 @@ Steps and the passages they follow
   (ties: ascending cell index), F_n = sum_{m<=n} mass_m / sum_all mass, and z_n
   from the tabulated history x(z_j) by linear interpolation in z between the
   two table points that bracket F_n.
+* Weighted matching (Sec. 3.4.2, the cumulative-fraction equation with the
+  linearly grown overdensity delta_m(z) = D(z)/D(z_mid) delta_m(z_mid); the
+  volume-weighted fraction of Sec. 2.3 and 3.1.1): the weight of a cell at
+  redshift z is linear in its mass, the ionized set at each table redshift
+  is the ranks whose weighted cumulative fraction is at most x(z_j), and z_n
+  is interpolated where that margin changes sign.  D(z) of flat LCDM with
+  Omega_m = 0.3 (Sec. 2) by quadrature of its integral form.
 
 parity status: every function here is pinned by tests under tests/ (worked
 Table 1 values, closed forms, brute force on tiny grids, invariants).
@@ -267,6 +274,125 @@ def assign_zre(order, mass, table: HistoryTable):
     z_re = np.empty(order.shape[0], dtype=np.float64)
     z_re[order] = z_n
     return z_re
+
+
+# ---------------------------------------------------------------------------
+# Weighted abundance matching: the growth-rescaled equation and the
+# volume-weighted fraction (Sec. 3.4.2; Sec. 2.3 and 3.1.1 on the weightings)
+# ---------------------------------------------------------------------------
+
+WEIGHT_MASS, WEIGHT_MASS_GROWTH, WEIGHT_VOLUME = 0, 1, 2
+
+
+def growth_factor(z, omega_m: float = 0.3):
+    """Linear density growth factor D(z) of a flat universe of matter and a
+    cosmological constant (the simulations' Omega_m = 0.3, Omega_L = 0.7,
+    Sec. 2), normalised so that D = a = 1/(1+z) at early times:
+
+        D(a) = (5 Omega_m / 2) E(a) int_0^a da' / (a' E(a'))^3,
+        E(a) = sqrt(Omega_m a^-3 + 1 - Omega_m),
+
+    the growing solution of the linear growth equation for pressureless
+    matter.  The integral is evaluated with scipy's adaptive quadrature."""
+    from scipy import integrate
+    zs = np.atleast_1d(np.asarray(z, dtype=np.float64))
+    E = lambda a: math.sqrt(omega_m * a ** -3 + 1.0 - omega_m)
+    out = np.empty_like(zs)
+    for i, zz in enumerate(zs):
+        a = 1.0 / (1.0 + zz)
+        I = integrate.quad(lambda x: 1.0 / (x * E(x)) ** 3 if x > 0 else 0.0, 0.0, a,
+                           epsabs=0.0, epsrel=1e-13, limit=200)[0]
+        out[i] = 2.5 * omega_m * E(a) * I
+    return out if np.ndim(z) else float(out[0])
+
+
+def weight_coeffs(table: HistoryTable, weighting: int, z_mid: float = 8.0, omega_m: float = 0.3):
+    """(alpha_j, beta_j) with the weight of cell m at table redshift z_j equal
+    to alpha_j + beta_j mass_m:
+
+    * mass (the plain path): weight = mass_m                      -> (0, 1)
+    * mass with growth (Sec. 3.4.2): 1 + delta_m(z_j), delta_m(z) =
+      D(z)/D(z_mid) delta_m(z_mid) and delta_m(z_mid) = mass_m - 1 (the
+      mass field is 1 + delta at the midpoint)                     -> (1 - g_j, g_j)
+    * volume: every cell weighs 1                                  -> (1, 0)
+    """
+    M = len(table.z)
+    if weighting == WEIGHT_MASS:
+        return np.zeros(M), np.ones(M)
+    if weighting == WEIGHT_VOLUME:
+        return np.ones(M), np.zeros(M)
+    if weighting == WEIGHT_MASS_GROWTH:
+        g = growth_factor(table.z, omega_m) / growth_factor(z_mid, omega_m)
+        return 1.0 - g, g
+    raise ValueError("unknown weighting")
+
+
+def weighted_margins(order, mass, table: HistoryTable, alpha, beta):
+    """h[j, n] = x_j W_N(z_j) - W_n(z_j) for all table points and ranks, where
+    W_n(z) = sum_{m<=n} weight_m(z) (inclusive): the rank-n cell counts as
+    ionized at z_j when h >= 0, i.e. when its cumulative weighted fraction
+    W_n/W_N is at most x_j (small cases only: M x N values)."""
+    m = np.asarray(mass, dtype=np.float64).reshape(-1)[np.asarray(order)]
+    N = m.shape[0]
+    n = np.arange(1, N + 1, dtype=np.float64)
+    Mn = np.cumsum(m)
+    WN = alpha * N + beta * Mn[-1]
+    return table.x[:, None] * WN[:, None] - (alpha[:, None] * n[None, :] + beta[:, None] * Mn[None, :])
+
+
+def assign_zre_weighted(order, mass, table: HistoryTable, weighting: int = WEIGHT_MASS,
+                        z_mid: float = 8.0, omega_m: float = 0.3, coeffs=None):
+    """z_re in cell order for a weighted cumulative fraction (Sec. 3.4.2).
+
+    The rank-n cell is ionized at table redshift z_j when its cumulative
+    weighted fraction is at most x_j (h_j(n) >= 0, see weighted_margins).
+    z_n is the largest table z_j at which it is ionized, refined linearly in
+    z between z_j* and z_j*+1 where h crosses zero:
+    t = h_j*/(h_j* - h_j*+1) in [0, 1), z_n = z_j* + t (z_j*+1 - z_j*);
+    z_lo if it is ionized at no table point, z_hi if at the last one.
+    With the mass weighting h_j = x_j T - M_n and this is assign_zre.
+    The paper does not say which root to take when the fraction crosses x(z)
+    more than once (linearly grown weights can turn negative in deep voids):
+    the largest z, i.e. the cell's first ionization, is taken.
+    coeffs: explicit (alpha_j, beta_j) instead of the weighting's."""
+    order = np.asarray(order)
+    alpha, beta = coeffs if coeffs is not None else weight_coeffs(table, weighting, z_mid, omega_m)
+    m = np.asarray(mass, dtype=np.float64).reshape(-1)[order]
+    N = m.shape[0]
+    Mtab = len(table.z)
+    n = np.arange(1, N + 1, dtype=np.float64)
+    Mn = np.cumsum(m)
+    WN = alpha * N + beta * Mn[-1]
+    jstar = np.full(N, -1, dtype=np.int64)
+    for j in range(Mtab):  # the last assignment wins: the largest such j
+        jstar[table.x[j] * WN[j] - (alpha[j] * n + beta[j] * Mn) >= 0.0] = j
+    h = lambda j: table.x[j] * WN[j] - (alpha[j] * n_sel + beta[j] * M_sel)
+    z_n = np.empty(N, dtype=np.float64)
+    none, last = jstar < 0, jstar == Mtab - 1
+    mid = ~(none | last)
+    jm = jstar[mid]
+    n_sel, M_sel = n[mid], Mn[mid]
+    h0, h1 = h(jm), h(jm + 1)
+    t = np.minimum(np.maximum(h0 / (h0 - h1), 0.0), np.nextafter(1.0, 0.0))
+    z_n[mid] = table.z[jm] + t * (table.z[jm + 1] - table.z[jm])
+    z_n[none] = table.z[0]
+    z_n[last] = table.z[-1]
+    z_re = np.empty(N, dtype=np.float64)
+    z_re[order] = z_n
+    return z_re
+
+
+def non_prefix_cells(order, mass, table: HistoryTable, weighting: int, z_mid: float = 8.0,
+                     omega_m: float = 0.3) -> int:
+    """How many ranks have an ionized set {j : h_j(n) >= 0} that is not a
+    prefix of the table (more than one crossing in z).  The paper speaks of
+    the reionization redshift of a cell, i.e. assumes a single crossing;
+    tests check their inputs have none."""
+    alpha, beta = weight_coeffs(table, weighting, z_mid, omega_m)
+    ion = weighted_margins(order, mass, table, alpha, beta) >= 0.0
+    cnt = ion.sum(axis=0)
+    prefix = np.arange(len(table.z))[:, None] < cnt[None, :]
+    return int(np.sum(np.any(ion != prefix, axis=0)))
 
 
 def solve(S, mass, box: float, l_mfp: float, z_mid: float, dz: float, Az: float,

@@ -23,7 +23,29 @@ PINS = [
     lambda: pins.test_ionized_mass_fraction_follows_history_within_one_cell(),
     lambda: [pins.test_weibull_coeffs_match_table1(r) for r in pins._table1()],
     lambda: pins.test_table_interpolation_vs_analytic_inverse(),
+    lambda: pins.test_growth_factor_einstein_de_sitter(),
+    lambda: pins.test_growth_factor_matches_growth_ode(),
+    lambda: pins.test_growth_factor_hypergeometric_closed_form(),
+    lambda: pins.test_weighted_mass_weighting_is_the_plain_rule(),
+    lambda: pins.test_weighted_volume_is_rank_over_count(),
+    lambda: pins.test_weighted_growth_of_uniform_density_is_volume(),
+    lambda: pins.test_weighted_growth_matches_continuous_root(),
+    lambda: pins.test_weighted_takes_the_first_ionization_brute_force(),
 ]
+
+_weight_coeffs = o.weight_coeffs
+
+
+def _coeffs_swapped(table, weighting, z_mid=8.0, omega_m=0.3):
+    a, b = _weight_coeffs(table, weighting, z_mid, omega_m)
+    return (b, a) if weighting == o.WEIGHT_MASS_GROWTH else (a, b)
+
+
+def _coeffs_unpivoted(table, weighting, z_mid=8.0, omega_m=0.3):
+    if weighting != o.WEIGHT_MASS_GROWTH:
+        return _weight_coeffs(table, weighting, z_mid, omega_m)
+    g = o.growth_factor(table.z, omega_m)  # D(z) without dividing by D(z_mid)
+    return 1.0 - g, g
 
 
 def _kmag_transposed(n, box):
@@ -46,6 +68,10 @@ MUTATIONS = {
                                np.asarray(mass, dtype=np.float64).reshape(-1)[np.asarray(order)])),
     "zlat_printed_typo": ("ionization_redshifts",
                           lambda z_mid, dz, Az: (z_mid + dz * Az / (1 + Az), z_mid, z_mid - dz * Az / (1 + Az))),
+    "growth_einstein_de_sitter_always": ("growth_factor",
+                                         lambda z, omega_m=0.3: 1.0 / (1.0 + np.asarray(z, dtype=np.float64))),
+    "growth_weights_swapped": ("weight_coeffs", _coeffs_swapped),
+    "growth_not_pivoted_at_midpoint": ("weight_coeffs", _coeffs_unpivoted),
 }
 
 

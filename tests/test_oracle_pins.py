@@ -327,3 +327,145 @@ def test_solve_monotone_in_intensity():
     # J_a > J_b  =>  z(a) >= z(b): z along descending-J order is non-increasing
     assert np.all(np.diff(z[order]) <= 0)
     assert np.all(np.diff(Jf[order]) <= 0)
+
+
+# ---------------------------------------------------------------------------
+# Weighted abundance matching (Sec. 3.4.2 with linear growth; volume weighting)
+# ---------------------------------------------------------------------------
+
+def test_growth_factor_einstein_de_sitter():
+    # Omega_m = 1: the growing mode is exactly D = a
+    z = np.array([0.0, 0.5, 3.0, 8.0, 20.0])
+    np.testing.assert_allclose(o.growth_factor(z, 1.0), 1.0 / (1.0 + z), rtol=1e-12)
+
+
+def test_growth_factor_matches_growth_ode():
+    # D'' + (3/a + dlnE/da) D' - 3 Om / (2 a^5 E^2) D = 0 from the matter era
+    # (D = a, D' = 1 at a = 1e-3, where the Lambda term is ~1e-9 of the matter
+    # term), integrated independently of the quadrature form
+    from scipy.integrate import solve_ivp
+    om = 0.3
+    E2 = lambda a: om * a ** -3 + 1.0 - om
+    dlnE = lambda a: -1.5 * om * a ** -4 / E2(a)
+
+    def rhs(a, y):
+        D, dD = y
+        return [dD, -(3.0 / a + dlnE(a)) * dD + 1.5 * om / (a ** 5 * E2(a)) * D]
+
+    z = np.array([0.0, 1.0, 5.0, 8.0, 15.0])
+    a_eval = np.sort(1.0 / (1.0 + z))
+    sol = solve_ivp(rhs, (1e-3, 1.0), [1e-3, 1.0], t_eval=a_eval, rtol=1e-12, atol=1e-15, method="DOP853")
+    D_ode = dict(zip(np.round(sol.t, 12), sol.y[0]))
+    for zz in z:
+        a = round(1.0 / (1.0 + zz), 12)
+        assert abs(o.growth_factor(zz, om) / D_ode[a] - 1.0) < 1e-7, (zz, o.growth_factor(zz, om), D_ode[a])
+
+
+def test_growth_factor_hypergeometric_closed_form():
+    # flat LCDM: D(a) = a 2F1(1/3, 1; 11/6; -a^3 Omega_L / Omega_m)
+    from scipy.special import hyp2f1
+    for om in (0.3, 0.5):
+        for zz in (0.0, 2.0, 6.0, 12.0):
+            a = 1.0 / (1.0 + zz)
+            ref = a * hyp2f1(1.0 / 3.0, 1.0, 11.0 / 6.0, -a ** 3 * (1.0 - om) / om)
+            assert abs(o.growth_factor(zz, om) / ref - 1.0) < 1e-11
+
+
+def _weighted_case(n=3000, seed=5, lo=0.01, hi=8.0):
+    g = np.random.default_rng(seed)
+    return g.permutation(n), g.uniform(lo, hi, n)
+
+
+def test_weighted_mass_weighting_is_the_plain_rule():
+    order, mass = _weighted_case()
+    t = o.history_table(8.0, 4.0, 3.0)
+    np.testing.assert_allclose(o.assign_zre_weighted(order, mass, t, o.WEIGHT_MASS), o.assign_zre(order, mass, t),
+                               rtol=0, atol=1e-12)
+
+
+def test_weighted_volume_is_rank_over_count():
+    # every cell weighs 1: F_n = n / N exactly, whatever the masses
+    order, mass = _weighted_case()
+    t = o.history_table(7.5, 4.0, 3.0)
+    z = o.assign_zre_weighted(order, mass, t, o.WEIGHT_VOLUME)
+    n = len(order)
+    zo = o.assign_from_fraction(np.arange(1, n + 1) / n, t)
+    np.testing.assert_allclose(z[order], zo, rtol=0, atol=1e-12)
+
+
+def test_weighted_growth_of_uniform_density_is_volume():
+    # delta = 0 everywhere: every grown weight is 1 at every z
+    order, _ = _weighted_case()
+    t = o.history_table(8.0, 4.0, 3.0)
+    ones = np.ones(len(order))
+    np.testing.assert_allclose(o.assign_zre_weighted(order, ones, t, o.WEIGHT_MASS_GROWTH, 8.0),
+                               o.assign_zre_weighted(order, ones, t, o.WEIGHT_VOLUME), rtol=0, atol=1e-12)
+
+
+def test_weighted_growth_matches_continuous_root():
+    # modest overdensities (weights stay positive): solve the paper's equation
+    #   sum_{m<=n} (1 + g(z) d_m) / sum_m (1 + g(z) d_m) = x(z)
+    # per cell on continuous z (analytic Weibull x, quadrature g), taking the
+    # highest root; the table result must agree to the interpolation error
+    n = 400
+    order, mass = _weighted_case(n, seed=9, lo=0.8, hi=1.2)
+    z_mid, dz, Az = 8.0, 4.0, 3.0
+    t = o.history_table(z_mid, dz, Az)
+    z_tab = o.assign_zre_weighted(order, mass, t, o.WEIGHT_MASS_GROWTH, z_mid)[order]
+    d = mass[order] - 1.0
+    A = np.cumsum(d)
+    ranks = np.arange(1, n + 1)
+    Dmid = o.growth_factor(z_mid)
+
+    def margin(zz, k):
+        g = o.growth_factor(zz) / Dmid
+        F = (ranks[k] + g * A[k]) / (n + g * A[-1])
+        return o.weibull_x(zz, t.a_w, t.b_w, t.c_w) - F
+
+    grid = np.linspace(t.z[0], t.z[-1], 301)
+    checked = 0
+    for k in range(0, n, 7):
+        x_here = o.weibull_x(z_tab[k], t.a_w, t.b_w, t.c_w)
+        if not (0.02 < x_here < 0.98):
+            continue
+        vals = np.array([margin(zz, k) for zz in grid])
+        idx = np.nonzero(vals >= 0)[0]
+        top = idx.max()  # highest grid z still ionized
+        lo, hi = grid[top], grid[top + 1]
+        for _ in range(60):
+            mid = 0.5 * (lo + hi)
+            if margin(mid, k) >= 0:
+                lo = mid
+            else:
+                hi = mid
+        assert abs(z_tab[k] - lo) < 5e-4, (k, z_tab[k], lo)
+        checked += 1
+    assert checked > 20
+
+
+def test_weighted_takes_the_first_ionization_brute_force():
+    # six cells whose grown weights turn negative at low z: the margin is
+    # evaluated with explicit loops, and z_n must come from the largest table
+    # point that ionizes the cell, interpolated where its margin changes sign
+    mass = np.array([0.01, 0.01, 0.01, 0.01, 1.297, 0.01])
+    order = np.arange(6)
+    t = o.history_table(8.0, 4.0, 3.0, n_table=60)
+    g = o.growth_factor(t.z) / o.growth_factor(8.0)
+    z = o.assign_zre_weighted(order, mass, t, o.WEIGHT_MASS_GROWTH, 8.0)
+    for nn in range(6):
+        h = []
+        for j in range(len(t.z)):
+            w = [1.0 + g[j] * (mass[m] - 1.0) for m in range(6)]
+            h.append(t.x[j] * sum(w) - sum(w[: nn + 1]))
+        ion = [j for j in range(len(t.z)) if h[j] >= 0.0]
+        if not ion:
+            ref = t.z[0]
+        elif ion[-1] == len(t.z) - 1:
+            ref = t.z[-1]
+        else:
+            k = ion[-1]
+            tt = min(max(h[k] / (h[k] - h[k + 1]), 0.0), np.nextafter(1.0, 0.0))
+            ref = t.z[k] + tt * (t.z[k + 1] - t.z[k])
+        assert abs(z[nn] - ref) < 1e-12, (nn, z[nn], ref)
+    # the case does have a cell with more than one crossing
+    assert o.non_prefix_cells(order, mass, t, o.WEIGHT_MASS_GROWTH, 8.0) >= 1
