@@ -343,6 +343,31 @@ def run_amber(args):
         raise RuntimeError(f"device status after timed region: {B.status_string(st)}")
     ms_max = reduce_max(ms, dist, "cuda")
 
+    # --- the other weightings of the matched fraction (same step, same inputs)
+    weightings = {}
+    if rank == 0 and ws == 1 and not args.no_extras:
+        for name, wgt in (("mass_growth", B.AMBER_WEIGHT_MASS_GROWTH), ("volume", B.AMBER_WEIGHT_VOLUME)):
+            hw = B.history(*HIST, weighting=wgt)
+            for _ in range(2):
+                ctx.solve(S, m, box, L_MFP, hw, out=z)
+            ctx.profile(True)
+            ctx.profile_reset()
+            reps = 3
+            e0.record(stream)
+            for _ in range(reps):
+                ctx.solve(S, m, box, L_MFP, hw, out=z)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            pw = ctx.profile_read()
+            ctx.profile(False)
+            st = ctx.sync_status()
+            if st != 0:
+                raise RuntimeError(f"device status ({name}): {B.status_string(st)}")
+            wms = e0.elapsed_time(e1) / reps
+            weightings[name] = {"ms_per_step": wms, "cells_per_s": C / (wms / 1e3),
+                                "scan_assign_ms": pw["scan_assign"][0] / reps,
+                                "thresholds_ms": pw["thresholds"][0] / reps}
+
     # --- end to end through the public API with pinned host buffers.  Every
     # step copies its inputs in, solves and copies z_re out; two buffer sets
     # let one step's copies overlap the neighbouring steps' solves (H2D and
@@ -455,6 +480,8 @@ def run_amber(args):
                 "kernels": kernels,
                 "clocks": clocks,
                 "cpu_baseline": cpu}
+        if weightings:
+            line["weightings"] = weightings
         line.update(extras)
         print(json.dumps(line), flush=True)
     ctx.close()

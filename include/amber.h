@@ -49,15 +49,33 @@ typedef enum {
 
 typedef struct amber_ctx amber_ctx;
 
+/* Weighting of the cumulative ionized fraction that abundance matching
+ * equates with the history x(z) (Sec. 3.4.2):
+ *   AMBER_WEIGHT_MASS         cell weight = its mass, the same at every z (the
+ *                             plain path: no growth rescaling);
+ *   AMBER_WEIGHT_MASS_GROWTH  cell weight at redshift z = 1 + delta_m(z) with
+ *                             delta_m(z) = D(z)/D(z_mid) delta_m(z_mid) and
+ *                             delta_m(z_mid) = mass - 1 (the mass field read as
+ *                             1 + delta at the midpoint), D the linear growth
+ *                             factor of flat LCDM with Omega_m = omega_m (the
+ *                             full equation of Sec. 3.4.2);
+ *   AMBER_WEIGHT_VOLUME       every cell weighs 1 (the volume-weighted fraction,
+ *                             Sec. 2.3 and 3.1.1). */
+enum { AMBER_WEIGHT_MASS = 0, AMBER_WEIGHT_MASS_GROWTH = 1, AMBER_WEIGHT_VOLUME = 2 };
+
 /* Reionization history (Sec. 3.1.1): midpoint, duration dz = z_ear - z_lat,
  * asymmetry Az = (z_ear - z_mid)/(z_mid - z_lat); the ionized fractions at
- * the three points (default 0.05, 0.50, 0.95); and the table x(z_j) on
- * n_table uniform redshifts in [min(z_lo, a_w), z_hi] (default 5, 20, 2000). */
+ * the three points (default 0.05, 0.50, 0.95); the table x(z_j) on n_table
+ * uniform redshifts in [min(z_lo, a_w), z_hi] (default 5, 20, 2000); and the
+ * weighting of the matched fraction (default AMBER_WEIGHT_MASS) with the
+ * matter density parameter its growth factor uses (default 0.3, Sec. 2). */
 typedef struct {
   double z_mid, dz, Az;
   double x_ear, x_mid, x_lat;
   double z_lo, z_hi;
   int n_table;
+  int weighting;
+  double omega_m;
 } amber_history_t;
 
 /* One realisation's parameters.  precision: 32 (FP32 FFT and intensity) or
@@ -70,7 +88,8 @@ typedef struct {
   int precision;
 } amber_params_t;
 
-/* Fill *h with the paper's defaults (x points 0.05/0.50/0.95, table [5,20] x 2000). */
+/* Fill *h with the paper's defaults (x points 0.05/0.50/0.95, table [5,20] x 2000,
+ * mass weighting, Omega_m 0.3). */
 int amber_history_default(amber_history_t *h, double z_mid, double dz, double Az);
 
 /* Weibull coefficients (a_w, b_w, c_w) of x(z) = exp(-max((z-a)/b,0)^c) through
@@ -134,7 +153,18 @@ int amber_rank_f64(amber_ctx *ctx, const double *d_J, int64_t ncells, uint32_t *
  * the order of addition.  d_F_opt, if not NULL, receives F_n (double, rank
  * order).
  * Masses must be finite, >= 0 and < 2^40 (else AMBER_ERR_INVALID_MASS latches),
- * with a positive total.  d_order must be a permutation of [0, ncells). */
+ * with a total in (0, 2^63).  d_order must be a permutation of [0, ncells).
+ *
+ * Other weightings (h->weighting, see AMBER_WEIGHT_*): the weight of cell m
+ * at table redshift z_j is alpha_j + beta_j mass_m, so its cumulative sum is
+ * W_n(z_j) = alpha_j n + beta_j M_n with n counting ranks from 1.  The rank-n
+ * cell is ionized at z_j when W_n(z_j) <= x_j W_N(z_j); its redshift comes
+ * from the largest such j, call it k (the cell's first ionization: with
+ * grown weights that turn negative in deep voids the fraction can cross x(z)
+ * more than once), interpolated linearly where the margin
+ * h_j = x_j W_N(z_j) - W_n(z_j) changes sign: t = h_k / (h_k - h_k+1),
+ * z_n = z_k + t (z_k+1 - z_k).  The mass weighting reduces to the rule above.  These margins are evaluated in FP32 (about 1e-7 of W_N), and
+ * d_F_opt still receives the mass fraction M_n / M_total. */
 int amber_assign_zre(amber_ctx *ctx, const uint32_t *d_order, const float *d_mass, int64_t ncells,
                      const amber_history_t *h, float *d_zre, double *d_F_opt, void *stream);
 

@@ -34,10 +34,16 @@ EXPORTED = [
 ]
 
 
+AMBER_WEIGHT_MASS = 0
+AMBER_WEIGHT_MASS_GROWTH = 1
+AMBER_WEIGHT_VOLUME = 2
+
+
 class amber_history_t(C.Structure):
     _fields_ = [("z_mid", C.c_double), ("dz", C.c_double), ("Az", C.c_double),
                 ("x_ear", C.c_double), ("x_mid", C.c_double), ("x_lat", C.c_double),
-                ("z_lo", C.c_double), ("z_hi", C.c_double), ("n_table", C.c_int)]
+                ("z_lo", C.c_double), ("z_hi", C.c_double), ("n_table", C.c_int),
+                ("weighting", C.c_int), ("omega_m", C.c_double)]
 
 
 class amber_params_t(C.Structure):
@@ -111,11 +117,13 @@ def _check(code: int, what: str):
 
 
 def history(z_mid: float, dz: float, Az: float, x_points=(0.05, 0.5, 0.95), z_lo: float = 5.0,
-            z_hi: float = 20.0, n_table: int = 2000) -> amber_history_t:
+            z_hi: float = 20.0, n_table: int = 2000, weighting: int = AMBER_WEIGHT_MASS,
+            omega_m: float = 0.3) -> amber_history_t:
     h = amber_history_t()
     _check(lib.amber_history_default(C.byref(h), z_mid, dz, Az), "amber_history_default")
     h.x_ear, h.x_mid, h.x_lat = x_points
     h.z_lo, h.z_hi, h.n_table = z_lo, z_hi, n_table
+    h.weighting, h.omega_m = weighting, omega_m
     return h
 
 

@@ -79,6 +79,10 @@ static bool history_valid(const amber_history_t* h) {
   if (!(h->dz > 0.0 && h->Az > 0.0)) return false;
   if (!(h->z_hi > h->z_lo)) return false;
   if (h->n_table < 2 || h->n_table > kMaxTable) return false;
+  if (h->weighting != AMBER_WEIGHT_MASS && h->weighting != AMBER_WEIGHT_MASS_GROWTH &&
+      h->weighting != AMBER_WEIGHT_VOLUME)
+    return false;
+  if (h->weighting == AMBER_WEIGHT_MASS_GROWTH && !(h->omega_m > 0.0 && h->omega_m <= 1.0)) return false;
   return true;
 }
 
@@ -138,6 +142,9 @@ static int history_coeffs(const amber_history_t* h, HistoryCoeffs* hc) {
   hc->z_lo = std::fmin(h->z_lo, a);  // reach the fully ionized plateau
   hc->z_hi = h->z_hi;
   hc->n_table = h->n_table;
+  hc->weighting = h->weighting;
+  hc->omega_m = h->omega_m;
+  hc->z_mid = h->z_mid;
   return AMBER_OK;
 }
 
@@ -154,7 +161,7 @@ static int fft_nmax(int64_t cells) {
 struct Plan {
   int n32 = 0, n64 = 0;
   int64_t cells64 = 0;
-  size_t off_spec, off_keysA, off_keysB, off_idxA, off_idxB, off_massA, off_massB, off_lb, off_sctrl, off_actrl, off_X, off_invdx,
+  size_t off_spec, off_keysA, off_keysB, off_idxA, off_idxB, off_massA, off_massB, off_lb, off_sctrl, off_actrl, off_X, off_invdx, off_lin,
       off_state, off_btab, off_tilemass, off_status, off_srcsum, off_tw32, off_tw64, total;
   size_t tw32_off[11] = {}, tw64_off[11] = {};
 };
@@ -186,6 +193,7 @@ static Plan make_plan(int64_t max_cells) {
   p.off_actrl = take(kAssignCtrlBytes);
   p.off_X = take((size_t)kMaxTable * sizeof(unsigned long long));
   p.off_invdx = take((size_t)kMaxTable * sizeof(float));
+  p.off_lin = take((size_t)4 * kMaxTable * sizeof(float));
   p.off_state = take(stt);
   p.off_btab = take((size_t)((max_cells + kScanTile - 1) / kScanTile) * (kMaxBuckets + 1) * sizeof(uint16_t));
   p.off_tilemass = take((size_t)sort_tiles(max_cells) * 16);
@@ -252,6 +260,8 @@ int amber_history_default(amber_history_t* h, double z_mid, double dz, double Az
   h->z_mid = z_mid; h->dz = dz; h->Az = Az;
   h->x_ear = 0.05; h->x_mid = 0.50; h->x_lat = 0.95;
   h->z_lo = 5.0; h->z_hi = 20.0; h->n_table = 2000;
+  h->weighting = AMBER_WEIGHT_MASS;
+  h->omega_m = 0.3;
   return AMBER_OK;
 }
 
@@ -326,6 +336,7 @@ int amber_create(amber_ctx** out, int device, int64_t max_cells) {
   c->assw.ctrl = c->ws + p.off_actrl;
   c->assw.Xq = reinterpret_cast<unsigned long long*>(c->ws + p.off_X);
   c->assw.inv_dx = reinterpret_cast<float*>(c->ws + p.off_invdx);
+  c->assw.lin = reinterpret_cast<float*>(c->ws + p.off_lin);
   c->assw.state = reinterpret_cast<unsigned long long*>(c->ws + p.off_state);
   // bucketed (cell, z) pairs reuse the key buffers, dead once ranked
   c->assw.bcell = reinterpret_cast<uint32_t*>(c->sortw.keysA);

@@ -77,6 +77,38 @@ __device__ __forceinline__ u128 mul_floor(double x, u128 T) {
   return (top << (64 - s)) | (u128)(p0 >> s);
 }
 
+// Linear growth factor D(a) of flat LCDM (Omega_m = om, Omega_L = 1 - om),
+// normalised to D = a early on: D(a) = (5 om / 2) E(a) int_0^a da'/(a' E(a'))^3
+// with E(a) = sqrt(om a^-3 + 1 - om).  In closed form D(a) = a 2F1(1/3, 1;
+// 11/6; -x) with x = a^3 (1 - om)/om; its power series converges fast for
+// x <= 1/2 (every z above ~0.7 at om = 0.3).  Beyond that the integral is
+// taken by Simpson's rule after the substitution a' = s^2, which makes the
+// integrand 2 s^4 / (om + (1 - om) s^6)^(3/2) smooth at 0.
+__device__ double growth_D(double a, double om) {
+  const double ol = 1.0 - om;
+  const double x = a * a * a * ol / om;
+  if (x <= 0.5) {
+    double sum = 0.0, term = 1.0;
+    for (int k = 0; k < 200 && fabs(term) > 1e-18 * fabs(sum + 1.0); ++k) {
+      sum += term;
+      term *= -x * (1.0 / 3.0 + k) / (11.0 / 6.0 + k);
+    }
+    return a * sum;
+  }
+  const int S = 2048;  // even
+  const double s1 = sqrt(a), hs = s1 / S;
+  auto f = [&](double sv) {
+    const double s2 = sv * sv, s6 = s2 * s2 * s2;
+    const double d = om + ol * s6;
+    return 2.0 * s2 * s2 / (d * sqrt(d));
+  };
+  double acc = f(0.0) + f(s1);
+  for (int i = 1; i < S; ++i) acc += (i & 1 ? 4.0 : 2.0) * f(i * hs);
+  const double I = acc * hs / 3.0;
+  const double E = sqrt(om / (a * a * a) + ol);
+  return 2.5 * om * E * I;
+}
+
 // tile_mass (optional): per-tile partial sums from the ranking; their total
 // is formed here (exact, order-free).  From the exact total T (2^-64 units)
 // the kernel picks the scan's fixed-point shift s (total below 2^62), and
@@ -87,7 +119,9 @@ __global__ void __launch_bounds__(1024) k_thresholds(unsigned long long* __restr
                                                      int64_t ntiles, int M, double a_w, double b_w, double c_w,
                                                      double z_lo, double z_hi, unsigned long long* __restrict__ Xq,
                                                      float* __restrict__ inv_dx, int* __restrict__ qshift,
-                                                     unsigned long long* __restrict__ qtotal) {
+                                                     unsigned long long* __restrict__ qtotal, int weighting,
+                                                     double omega_m, double z_mid, int64_t ncells,
+                                                     float* __restrict__ lin) {
   __shared__ u128 ws[32];
   __shared__ u128 sT;
   __shared__ int s_shift;
@@ -131,6 +165,27 @@ __global__ void __launch_bounds__(1024) k_thresholds(unsigned long long* __restr
     const double x = exp(-pow(u, c_w));
     const u128 X = mul_floor(x, T);
     Xq[j] = (unsigned long long)(sh >= 0 ? (X >> sh) : (X << (-sh)));
+    if (weighting != AMBER_WEIGHT_MASS) {
+      // weight of a cell at z_j: alpha_j + beta_j mass; margin h_j(n) =
+      // x_j W_N - W_n.  Two equal forms keep the operands small at either end
+      // of the ranking: the head form x_j W_N - alpha_j n - beta_j M_n for the
+      // first half of the ranks, and the tail form (x_j - 1) W_N +
+      // alpha_j (N - n) + beta_j (T - M_n) for the second, where the weight
+      // after rank n (all that is left on the x = 1 plateau) comes from exact
+      // differences
+      double alpha = 1.0, beta = 0.0;  // volume
+      if (weighting == AMBER_WEIGHT_MASS_GROWTH) {
+        const double g = growth_D(1.0 / (1.0 + z), omega_m) / growth_D(1.0 / (1.0 + z_mid), omega_m);
+        alpha = 1.0 - g;
+        beta = g;
+      }
+      const double Treal = u128_to_double(T) * 5.421010862427522e-20;  // 2^-64
+      const double WN = alpha * (double)ncells + beta * Treal;
+      lin[j] = (float)(x * WN);
+      lin[kMaxTable + j] = (float)((x - 1.0) * WN);
+      lin[2 * kMaxTable + j] = (float)alpha;
+      lin[3 * kMaxTable + j] = (float)beta;
+    }
   }
   __syncthreads();
   for (int j = threadIdx.x; j < M - 1; j += blockDim.x) {
@@ -190,9 +245,19 @@ __device__ __forceinline__ void count_ge_round(const unsigned long long* __restr
 
 constexpr int kScanWin = 64;  // thresholds one tile may span, staged in shared memory
 
-template <bool GATHER, bool WANT_F>
+constexpr int kLinCand = 256;  // table points a tile's cells may straddle (linear weightings)
+
+// LIN: a linear weighting (growth or volume).  The exact-integer threshold
+// test of the mass weighting is replaced by the margins h_j(n) in FP32: per
+// tile, every table point is classified against the box of (n, M_n) the
+// tile's cells span -- ionized for all of them, for none, or straddling --
+// and each cell takes the largest point that ionizes it among
+// max{j : all ionized} and the straddling points above it.
+template <bool GATHER, bool WANT_F, bool LIN>
 __global__ void __launch_bounds__(kScanThreads, 4) k_scan_assign(const ScanArgs a) {
   constexpr int NT = kScanThreads, IT = kScanItems, TILE = kScanTile;
+  __shared__ int s_jall, s_ncand;
+  __shared__ int s_cand[LIN ? kLinCand : 1];
   __shared__ uint32_t sord[TILE + TILE / 32];
   __shared__ float smass[TILE + TILE / 32];
   __shared__ unsigned long long wtot[NT / 32];
@@ -204,7 +269,11 @@ __global__ void __launch_bounds__(kScanThreads, 4) k_scan_assign(const ScanArgs 
   __shared__ uint32_t scnt[kMaxBuckets];
   __shared__ uint32_t soff[kMaxBuckets + 1];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  if (tid == 0) s_tile = atomicAdd(a.ticket, 1u);
+  if (tid == 0) {
+    s_tile = atomicAdd(a.ticket, 1u);
+    s_jall = -1;
+    s_ncand = 0;
+  }
   for (int b = tid; b < a.nbuckets; b += NT) scnt[b] = 0;
   __syncthreads();
   const uint32_t tile = s_tile;
@@ -311,14 +380,14 @@ __global__ void __launch_bounds__(kScanThreads, 4) k_scan_assign(const ScanArgs 
     }
     // bracket the whole tile: c(M) = #{j : X_j >= M} at its first and last
     // prefix, both searched at once (three round trips for 2000 thresholds)
-    int lo0 = 0, hi0 = M, lo1 = 0, hi1 = M;
+    int lo0 = 0, hi0 = LIN ? 0 : M, lo1 = 0, hi1 = LIN ? 0 : M;
     while (lo0 < hi0 || lo1 < hi1) {
       count_ge_round(a.Xq, excl, lo0, hi0, lane);
       count_ge_round(a.Xq, excl + tile_sum, lo1, hi1, lane);
     }
     // thresholds the tile's cells can touch: X_j for j in [c_last - 1, c_first]
     const int base = max(lo1 - 1, 0), L = min(lo0, M - 1) - base + 1;
-    const bool stage = L <= kScanWin;
+    const bool stage = !LIN && L <= kScanWin;
     if (stage) {
       for (int i = lane; i < L; i += 32) {
         sX[i] = a.Xq[base + i];
@@ -358,6 +427,45 @@ __global__ void __launch_bounds__(kScanThreads, 4) k_scan_assign(const ScanArgs 
   __syncthreads();
   unsigned long long Mn = s_excl + thr_excl;
   const double invT = WANT_F ? 1.0 / (double)*a.qtotal : 0.0;
+  const float qinv = __int_as_float((127 - *a.qshift) << 23);  // 2^-s: fixed point -> mass units
+  const unsigned long long qT = LIN ? *a.qtotal : 0ull;  // total in the prefix's fixed point (>= every M_n)
+  // head form (ranks in the first half) or tail form, for the whole tile:
+  // h = C_j + sa alpha_j u + sa beta_j v with (C, u, v, sa) = (x W_N, n, M_n, -1)
+  // or ((x - 1) W_N, N - n, T - M_n, +1)
+  const bool head = start + (uint32_t)cnt / 2u <= n / 2u;
+  const float* linC = head ? a.linP : a.linQ;
+  const float sa = head ? -1.0f : 1.0f;
+  if constexpr (LIN) {
+    // (u, v) of the tile's cells lie in the box [u0, u1] x [v0, v1]; a linear
+    // margin takes its extremes at the corners
+    const float u0 = head ? (float)(start + 1u) : (float)(n - (start + (uint32_t)cnt));
+    const float u1 = head ? (float)(start + (uint32_t)cnt) : (float)(n - (start + 1u));
+    const float v0 = head ? u64_to_float(s_excl) * qinv : u64_to_float(qT - (s_excl + tile_sum)) * qinv;
+    const float v1 = head ? u64_to_float(s_excl + tile_sum) * qinv : u64_to_float(qT - s_excl) * qinv;
+    auto classify = [&](int j, float& hmin, float& hmax, float& tol) {
+      const float Cj = linC[j], al = sa * a.lina[j], be = sa * a.linb[j];
+      const float au0 = al * u0, au1 = al * u1, bv0 = be * v0, bv1 = be * v1;
+      hmin = Cj + fminf(au0, au1) + fminf(bv0, bv1);
+      hmax = Cj + fmaxf(au0, au1) + fmaxf(bv0, bv1);
+      tol = 4e-7f * (fabsf(Cj) + fmaxf(fabsf(au0), fabsf(au1)) + fmaxf(fabsf(bv0), fabsf(bv1)));
+    };
+    for (int j = tid; j < M; j += NT) {
+      float hmin, hmax, tol;
+      classify(j, hmin, hmax, tol);
+      if (hmin >= tol) atomicMax(&s_jall, j);
+    }
+    __syncthreads();
+    const int jall = s_jall;
+    for (int j = jall + 1 + tid; j < M; j += NT) {
+      float hmin, hmax, tol;
+      classify(j, hmin, hmax, tol);
+      if (hmax >= -tol) {
+        const int k = atomicAdd(&s_ncand, 1);
+        if (k < kLinCand) s_cand[k] = j;
+      }
+    }
+    __syncthreads();
+  }
   const int cx_lo = s_cx[0], cx_hi = s_cx[1], wb = s_cx[2];
   // threshold j from the staged window when the tile fits it
   auto Xj = [&](int j) -> unsigned long long { return wb >= 0 ? sX[j - wb] : a.Xq[j]; };
@@ -375,6 +483,37 @@ __global__ void __launch_bounds__(kScanThreads, 4) k_scan_assign(const ScanArgs 
     const int p = tid * IT + i;
     if (p >= cnt) continue;
     Mn += mass_fix(mv[i], qs);
+    if constexpr (LIN) {
+      const uint32_t rank1 = start + (uint32_t)p + 1u;
+      const float uu = sa * (head ? (float)rank1 : (float)(n - rank1));
+      const float vv = sa * (head ? u64_to_float(Mn) * qinv : u64_to_float(qT - Mn) * qinv);
+      auto h = [&](int j) { return fmaf(a.linb[j], vv, fmaf(a.lina[j], uu, linC[j])); };
+      int js = s_jall;
+      const int nc = s_ncand;
+      if (nc <= kLinCand) {
+        for (int k = 0; k < nc; ++k) {
+          const int c = s_cand[k];
+          if (c > js && h(c) >= 0.0f) js = c;
+        }
+      } else {
+        for (int c = M - 1; c > js; --c)
+          if (h(c) >= 0.0f) { js = c; break; }
+      }
+      float z;
+      if (js < 0) z = a.z_lo;
+      else if (js == M - 1) z = a.z_hi;
+      else {
+        const float h0 = h(js), h1 = h(js + 1);
+        float t = h0 / (h0 - h1);
+        t = fminf(fmaxf(t, 0.0f), 0.99999994f);
+        z = a.z_lo + ((float)js + t) * a.dzt;
+      }
+      if (WANT_F) a.F[start + p] = (double)Mn * invT;
+      const uint32_t q = soff[cell[i] >> a.bucket_shift] + slot[i];
+      scell[q + (q >> 5)] = cell[i];
+      sz[q + (q >> 5)] = z;
+      continue;
+    }
     if (cx < 0) {
       int lo = cx_lo, hi = cx_hi;
       while (lo < hi) {
@@ -494,7 +633,8 @@ cudaError_t assign_impl(const AssignWork& w, const uint32_t* order, const float*
   int* qshift = reinterpret_cast<int*>(w.ctrl + 32);
   unsigned long long* qtotal = reinterpret_cast<unsigned long long*>(w.ctrl + 40);
   k_thresholds<<<1, 1024, 0, s>>>(total, tile_mass, tile_mass ? sort_tiles(n) : 0, hc.n_table, hc.a, hc.b, hc.c,
-                                   hc.z_lo, hc.z_hi, w.Xq, w.inv_dx, qshift, qtotal);
+                                   hc.z_lo, hc.z_hi, w.Xq, w.inv_dx, qshift, qtotal, hc.weighting, hc.omega_m,
+                                   hc.z_mid, n, w.lin);
   prof_end(prof, PK_THRESHOLDS, s);
 
   ScanArgs a;
@@ -522,13 +662,23 @@ cudaError_t assign_impl(const AssignWork& w, const uint32_t* order, const float*
   a.status = status;
   a.spin_limit = spin_limit;
   a.ahead = (uint32_t)w.num_sms * 4;  // resident scan CTAs: 4 per SM
+  a.linP = w.lin;
+  a.linQ = w.lin + kMaxTable;
+  a.lina = w.lin + 2 * kMaxTable;
+  a.linb = w.lin + 3 * kMaxTable;
   prof_begin(prof, PK_SCAN_ASSIGN, s);
-  if (mass_in_rank_order) {
-    if (F) k_scan_assign<false, true><<<(unsigned)tiles, kScanThreads, 0, s>>>(a);
-    else k_scan_assign<false, false><<<(unsigned)tiles, kScanThreads, 0, s>>>(a);
-  } else {
-    if (F) k_scan_assign<true, true><<<(unsigned)tiles, kScanThreads, 0, s>>>(a);
-    else k_scan_assign<true, false><<<(unsigned)tiles, kScanThreads, 0, s>>>(a);
+  const unsigned g = (unsigned)tiles;
+  const bool gather = !mass_in_rank_order, lin = hc.weighting != AMBER_WEIGHT_MASS;
+  const int v = (gather ? 4 : 0) | (F ? 2 : 0) | (lin ? 1 : 0);
+  switch (v) {
+    case 0: k_scan_assign<false, false, false><<<g, kScanThreads, 0, s>>>(a); break;
+    case 1: k_scan_assign<false, false, true><<<g, kScanThreads, 0, s>>>(a); break;
+    case 2: k_scan_assign<false, true, false><<<g, kScanThreads, 0, s>>>(a); break;
+    case 3: k_scan_assign<false, true, true><<<g, kScanThreads, 0, s>>>(a); break;
+    case 4: k_scan_assign<true, false, false><<<g, kScanThreads, 0, s>>>(a); break;
+    case 5: k_scan_assign<true, false, true><<<g, kScanThreads, 0, s>>>(a); break;
+    case 6: k_scan_assign<true, true, false><<<g, kScanThreads, 0, s>>>(a); break;
+    default: k_scan_assign<true, true, true><<<g, kScanThreads, 0, s>>>(a); break;
   }
   prof_end(prof, PK_SCAN_ASSIGN, s);
   prof_begin(prof, PK_SCATTER_BACK, s);

@@ -26,6 +26,7 @@ struct AssignWork {
   unsigned char* ctrl;
   unsigned long long* Xq;  // [kMaxTable] thresholds in the scan's fixed point
   float* inv_dx;           // [kMaxTable]
+  float* lin;              // [4][kMaxTable]: P_j, Q_j, alpha_j, beta_j of the linear weightings
   unsigned long long* state;  // per scan tile: look-back word
   uint32_t* bcell;  // per scan tile, (cell, z) pairs grouped by bucket
   float* bz;
@@ -37,6 +38,9 @@ struct HistoryCoeffs {
   double a, b, c;
   double z_lo, z_hi;  // effective table range (z_lo lowered to a_w if needed)
   int n_table;
+  int weighting;      // AMBER_WEIGHT_*
+  double omega_m;     // growth factor's matter density (AMBER_WEIGHT_MASS_GROWTH)
+  double z_mid;       // growth pivot
 };
 
 struct ScanArgs {
@@ -63,6 +67,13 @@ struct ScanArgs {
   unsigned int* status;
   unsigned int spin_limit;
   uint32_t ahead;  // tiles ahead whose order and masses are prefetched into L2 (0: none)
+  // linear weightings: margin h_j(n) = P_j - alpha_j n - beta_j M_n
+  // = Q_j + alpha_j (N - n) + beta_j (T - M_n), P_j = x_j W_N(z_j),
+  // Q_j = (x_j - 1) W_N(z_j) (real units)
+  const float* linP;
+  const float* linQ;
+  const float* lina;
+  const float* linb;
 };
 
 void bucket_plan(int64_t n, int* nbuckets, int* shift);

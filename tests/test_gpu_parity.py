@@ -380,3 +380,68 @@ def test_rank_match_variant_bit_exact():
     env = dict(os.environ, AMBER_SORT_RANK="match", PYTHONPATH=root)
     r = subprocess.run([sys.executable, "-c", code], cwd=root, env=env, capture_output=True, text=True, timeout=300)
     assert r.returncode == 0 and "ok" in r.stdout, r.stderr[-2000:]
+
+
+# ---------------------------------------------------------------------------
+# Weighted abundance matching: growth-rescaled (Sec. 3.4.2) and volume
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("weighting", [1, 2])
+@pytest.mark.parametrize("n", [1, 5, 4097, 123_457])
+def test_assign_weighted_vs_oracle_given_order(ctx, B, weighting, n):
+    # masses 1 + delta with delta in [-0.99, 2]: grown weights turn negative at
+    # low z for the deepest voids, so some cells cross x(z) more than once
+    g = np.random.default_rng(100 + n)
+    mass = g.uniform(0.01, 3.0, n).astype(np.float32)
+    order = g.permutation(n).astype(np.int32)
+    h = B.history(8.0, 4.0, 3.0, weighting=weighting)
+    z = ctx.assign_zre(torch.from_numpy(order).cuda(), torch.from_numpy(mass).cuda(), h)
+    check_status(ctx, B)
+    t = O.history_table(8.0, 4.0, 3.0)
+    zo = O.assign_zre_weighted(order, mass.astype(np.float64), t, weighting, 8.0, 0.3)
+    d = np.abs(z.cpu().numpy().astype(np.float64) - zo)
+    # the margins are FP32 (about 1e-7 of the total weight)
+    assert np.mean(d > 1e-3) <= (0.0 if n < 10_000 else 1e-4), (np.mean(d > 1e-3), d.max())
+    assert np.quantile(d, 0.999) < 5e-5, np.quantile(d, 0.999)
+
+
+def test_assign_volume_equals_unit_masses(ctx, B):
+    n = 200_000
+    g = np.random.default_rng(4)
+    order = torch.from_numpy(g.permutation(n).astype(np.int32)).cuda()
+    mass = torch.from_numpy(g.uniform(0.01, 5.0, n).astype(np.float32)).cuda()
+    zv = ctx.assign_zre(order, mass, B.history(7.5, 4.0, 3.0, weighting=2))
+    zu = ctx.assign_zre(order, torch.ones(n, device="cuda"), B.history(7.5, 4.0, 3.0))
+    check_status(ctx, B)
+    assert float((zv - zu).abs().max()) < 5e-5
+
+
+def test_solve_growth_64cube_given_gpu_order(ctx, B):
+    # the whole FP32 path with growth rescaling; the assignment is compared
+    # against the oracle on the GPU's own rank order and rank-order masses
+    n, box, l = 64, 100.0, 3.0
+    S, m = synth.realisation(n, box, 0, device="cuda")
+    h = B.history(8.0, 4.0, 3.0, weighting=1)
+    z = torch.empty_like(S)
+    order = torch.empty(n ** 3, dtype=torch.int32, device="cuda")
+    mrank = torch.empty(n ** 3, device="cuda")
+    ctx.solve_ex(S, m, box, l, h, z, order, mrank)
+    check_status(ctx, B)
+    o_ = order.cpu().numpy().astype(np.int64)
+    mr = mrank.cpu().numpy().astype(np.float64)
+    np.testing.assert_array_equal(mr, m.cpu().numpy().reshape(-1)[o_].astype(np.float64))
+    t = O.history_table(8.0, 4.0, 3.0)
+    zo = O.assign_zre_weighted(o_, m.cpu().numpy().reshape(-1).astype(np.float64), t, 1, 8.0, 0.3)
+    d = np.abs(z.cpu().numpy().reshape(-1).astype(np.float64) - zo)
+    assert np.mean(d > 1e-3) <= 1e-4, (np.mean(d > 1e-3), d.max())
+    # the plain path's z differs: growth rescaling is in effect
+    z0 = ctx.solve(S, m, box, l, B.history(8.0, 4.0, 3.0))
+    assert float((z0.view(-1) - z.view(-1)).abs().max()) > 1e-2
+
+
+def test_history_rejects_bad_weighting(ctx, B):
+    order = torch.arange(100, dtype=torch.int32, device="cuda")
+    mass = torch.ones(100, device="cuda")
+    for w, om in ((3, 0.3), (1, 0.0), (1, 1.5)):
+        with pytest.raises(B.AmberError):
+            ctx.assign_zre(order, mass, B.history(8.0, 4.0, 3.0, weighting=w, omega_m=om))
