@@ -30,6 +30,10 @@ Steps and the passages they follow
   (ties: ascending cell index), F_n = sum_{m<=n} mass_m / sum_all mass, and z_n
   from the tabulated history x(z_j) by linear interpolation in z between the
   two table points that bracket F_n.
+* Analysis (Sec. 2.3, Eqs. epsz, deltaz, Pk, Dk, bias, rcc): the normalised
+  and fractional-difference redshift fields, and spherical-shell auto and
+  cross power spectra with the bias and cross-correlation built from them
+  (full complex FFT, every mode counted once).
 * Weighted matching (Sec. 3.4.2, the cumulative-fraction equation with the
   linearly grown overdensity delta_m(z) = D(z)/D(z_mid) delta_m(z_mid); the
   volume-weighted fraction of Sec. 2.3 and 3.1.1): the weight of a cell at
@@ -393,6 +397,77 @@ def non_prefix_cells(order, mass, table: HistoryTable, weighting: int, z_mid: fl
     cnt = ion.sum(axis=0)
     prefix = np.arange(len(table.z))[:, None] < cnt[None, :]
     return int(np.sum(np.any(ion != prefix, axis=0)))
+
+
+# ---------------------------------------------------------------------------
+# Analysis of z_re (Sec. 2.3: Eqs. epsz, deltaz, Pk, Dk, bias, rcc)
+# ---------------------------------------------------------------------------
+
+def delta_z(z_re):
+    """Normalised redshift field (Eq. deltaz): ((1 + z) - (1 + zbar)) / (1 + zbar)
+    with zbar the volume-weighted (per-cell) mean.  Returns (delta_z, zbar)."""
+    z = np.asarray(z_re, dtype=np.float64)
+    zbar = float(z.mean())
+    return ((1.0 + z) - (1.0 + zbar)) / (1.0 + zbar), zbar
+
+
+def epsilon_z(z_re, z_ref):
+    """Fractional difference field (Eq. epsz): ((1 + z) - (1 + z_ref)) / (1 + z_ref)."""
+    z = np.asarray(z_re, dtype=np.float64)
+    z1 = np.asarray(z_ref, dtype=np.float64)
+    return ((1.0 + z) - (1.0 + z1)) / (1.0 + z1)
+
+
+def power_bins(n: int) -> int:
+    """Number of spherical shells: shell b holds the integer wave vectors m
+    (components in [-n/2, n/2)) with round(|m|) = b, so b runs to
+    round(sqrt(3) n / 2)."""
+    return int(np.rint(math.sqrt(3.0) * n / 2.0)) + 1
+
+
+def power_spectrum(a, b, box: float):
+    """Auto and cross power spectra of real fields a, b on an n^3 periodic
+    grid of side box (Eqs. Pk, Dk): P_ij(k) = <delta_i(k) delta_j(k)*> over the
+    modes of a spherical shell, in the continuum normalisation
+    delta(k) = (box/n)^3 sum_x delta(x) exp(-i k.x), P = |delta(k)|^2 / box^3.
+    Shell b holds every wave vector m of the full n^3 transform with
+    round(|m|) = b (k = 2 pi m / box).  Returns (k_mean, P_aa, P_bb, P_ab,
+    modes) per shell, k_mean the mean |k| of the shell's modes."""
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    n = a.shape[0]
+    A = np.fft.fftn(a)
+    Bf = np.fft.fftn(b)
+    m = np.fft.fftfreq(n, 1.0 / n)  # integer frequencies in [-n/2, n/2)
+    mx, my, mz = np.meshgrid(m, m, m, indexing="ij")
+    mag = np.sqrt(mx ** 2 + my ** 2 + mz ** 2)
+    shell = np.rint(mag).astype(np.int64).reshape(-1)
+    nb = power_bins(n)
+    modes = np.bincount(shell, minlength=nb).astype(np.float64)
+    norm = box ** 3 / float(n) ** 6
+    Paa = np.bincount(shell, weights=(np.abs(A) ** 2).reshape(-1), minlength=nb)
+    Pbb = np.bincount(shell, weights=(np.abs(Bf) ** 2).reshape(-1), minlength=nb)
+    Pab = np.bincount(shell, weights=(A * np.conj(Bf)).real.reshape(-1), minlength=nb)
+    ksum = np.bincount(shell, weights=mag.reshape(-1), minlength=nb)
+    with np.errstate(invalid="ignore", divide="ignore"):
+        inv = np.where(modes > 0, 1.0 / modes, 0.0)
+    kf = 2.0 * math.pi / box
+    return kf * ksum * inv, norm * Paa * inv, norm * Pbb * inv, norm * Pab * inv, modes
+
+
+def dimensionless_power(k, P):
+    """Delta^2(k) = k^3 P(k) / (2 pi^2) (Eq. Dk)."""
+    return np.asarray(k) ** 3 * np.asarray(P) / (2.0 * math.pi ** 2)
+
+
+def bias(P_ii, P_jj):
+    """b_ij = sqrt(P_ii / P_jj) (Eq. bias)."""
+    return np.sqrt(np.asarray(P_ii) / np.asarray(P_jj))
+
+
+def cross_correlation(P_ij, P_ii, P_jj):
+    """r_ij = P_ij / sqrt(P_ii P_jj) (Eq. rcc)."""
+    return np.asarray(P_ij) / np.sqrt(np.asarray(P_ii) * np.asarray(P_jj))
 
 
 def solve(S, mass, box: float, l_mfp: float, z_mid: float, dz: float, Az: float,

@@ -31,7 +31,25 @@ PINS = [
     lambda: pins.test_weighted_growth_of_uniform_density_is_volume(),
     lambda: pins.test_weighted_growth_matches_continuous_root(),
     lambda: pins.test_weighted_takes_the_first_ionization_brute_force(),
+    lambda: pins.test_power_spectrum_parseval(),
+    lambda: [pins.test_power_spectrum_plane_wave(m) for m in [(1, 0, 0), (0, 3, 2), (2, -1, 4), (4, 4, 4)]],
+    lambda: pins.test_power_shell_counts_brute_force(),
+    lambda: pins.test_bias_and_cross_correlation_identities(),
+    lambda: pins.test_white_noise_power_is_flat(),
+    lambda: pins.test_delta_z_and_epsilon_z_closed_forms(),
 ]
+
+_power = o.power_spectrum
+
+
+def _power_no_volume(a, b, box):
+    k, Paa, Pbb, Pab, modes = _power(a, b, box)
+    return k, Paa / box ** 3, Pbb / box ** 3, Pab / box ** 3, modes
+
+
+def _power_cross_swapped(a, b, box):
+    k, Paa, Pbb, Pab, modes = _power(a, b, box)
+    return k, Paa, Pbb, np.sqrt(Paa * Pbb), modes
 
 _weight_coeffs = o.weight_coeffs
 
@@ -72,6 +90,10 @@ MUTATIONS = {
                                          lambda z, omega_m=0.3: 1.0 / (1.0 + np.asarray(z, dtype=np.float64))),
     "growth_weights_swapped": ("weight_coeffs", _coeffs_swapped),
     "growth_not_pivoted_at_midpoint": ("weight_coeffs", _coeffs_unpivoted),
+    "power_missing_volume": ("power_spectrum", _power_no_volume),
+    "power_cross_is_geometric_mean": ("power_spectrum", _power_cross_swapped),
+    "delta_z_not_normalised": ("delta_z", lambda z: (lambda zz: (zz - zz.mean(), float(zz.mean())))(
+        np.asarray(z, dtype=np.float64))),
 }
 
 

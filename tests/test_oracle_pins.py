@@ -469,3 +469,83 @@ def test_weighted_takes_the_first_ionization_brute_force():
         assert abs(z[nn] - ref) < 1e-12, (nn, z[nn], ref)
     # the case does have a cell with more than one crossing
     assert o.non_prefix_cells(order, mass, t, o.WEIGHT_MASS_GROWTH, 8.0) >= 1
+
+
+# ---------------------------------------------------------------------------
+# Analysis of z_re (Sec. 2.3): delta_z, epsilon_z, shell power spectra
+# ---------------------------------------------------------------------------
+
+def test_power_spectrum_parseval():
+    # sum over shells of modes x P equals box^3/n^6 sum_k |A_k|^2 = box^3/n^3 sum_x a^2
+    g = np.random.default_rng(21)
+    n, box = 12, 37.0
+    a = g.normal(size=(n, n, n))
+    k, Paa, Pbb, Pab, modes = o.power_spectrum(a, 2.0 * a, box)
+    assert modes.sum() == n ** 3
+    np.testing.assert_allclose(np.sum(modes * Paa), box ** 3 / n ** 3 * np.sum(a * a), rtol=1e-12)
+    np.testing.assert_allclose(Pbb, 4.0 * Paa, rtol=1e-12)
+    np.testing.assert_allclose(Pab, 2.0 * Paa, rtol=1e-12)
+
+
+@pytest.mark.parametrize("m0", [(1, 0, 0), (0, 3, 2), (2, -1, 4), (4, 4, 4)])
+def test_power_spectrum_plane_wave(m0):
+    # a = A cos(2 pi m0.x / n): modes +-m0 carry (A n^3 / 2)^2 each, all in shell round(|m0|)
+    n, box, A = 8, 20.0, 1.7
+    x = np.arange(n)
+    X, Y, Z = np.meshgrid(x, x, x, indexing="ij")
+    a = A * np.cos(2 * np.pi * (m0[0] * X + m0[1] * Y + m0[2] * Z) / n)
+    k, P, _, _, modes = o.power_spectrum(a, a, box)
+    mag = math.sqrt(sum(c * c for c in m0))
+    b = int(round(mag))
+    nyq = all(abs(c) == n // 2 for c in m0)  # the mode is its own conjugate
+    power = (A * n ** 3) ** 2 if nyq else 2 * (A * n ** 3 / 2) ** 2
+    assert abs(P[b] - box ** 3 / n ** 6 * power / modes[b]) <= 1e-9 * P[b]
+    others = np.delete(P, b)
+    assert np.all(np.abs(others) <= 1e-20 * P[b])
+    np.testing.assert_allclose(o.dimensionless_power(k[b], P[b]), k[b] ** 3 * P[b] / (2 * np.pi ** 2), rtol=1e-14)
+
+
+def test_power_shell_counts_brute_force():
+    # lattice points with round(|m|) = b, counted by explicit loops
+    n = 6
+    cnt = [0] * o.power_bins(n)
+    r = range(-n // 2, n // 2)
+    for i in r:
+        for j in r:
+            for l in r:
+                cnt[int(round(math.sqrt(i * i + j * j + l * l)))] += 1
+    _, _, _, _, modes = o.power_spectrum(np.ones((n, n, n)), np.ones((n, n, n)), 1.0)
+    np.testing.assert_array_equal(modes, np.array(cnt, dtype=np.float64))
+
+
+def test_bias_and_cross_correlation_identities():
+    g = np.random.default_rng(3)
+    a = g.normal(size=(8, 8, 8))
+    k, Paa, Pbb, Pab, modes = o.power_spectrum(a, -a, 10.0)
+    live = modes > 0
+    np.testing.assert_allclose(o.cross_correlation(Pab[live], Paa[live], Pbb[live]), -1.0, rtol=1e-12)
+    k, Paa, Pbb, Pab, modes = o.power_spectrum(3.0 * a, a, 10.0)
+    np.testing.assert_allclose(o.bias(Paa[live], Pbb[live]), 3.0, rtol=1e-12)
+    np.testing.assert_allclose(o.cross_correlation(Pab[live], Paa[live], Pbb[live]), 1.0, rtol=1e-12)
+
+
+def test_white_noise_power_is_flat():
+    # <|A_k|^2> = n^3 sigma^2 for white noise: P = sigma^2 box^3 / n^3 at every k
+    g = np.random.default_rng(8)
+    n, box, sig = 32, 50.0, 0.7
+    a = g.normal(scale=sig, size=(n, n, n))
+    k, P, _, _, modes = o.power_spectrum(a, a, box)
+    flat = sig ** 2 * box ** 3 / n ** 3
+    live = modes > 500
+    assert np.all(np.abs(P[live] / flat - 1.0) < 0.2)
+    assert abs(np.sum(modes[1:] * P[1:]) / np.sum(modes[1:]) / flat - 1.0) < 0.02
+
+
+def test_delta_z_and_epsilon_z_closed_forms():
+    g = np.random.default_rng(5)
+    z = g.uniform(5.0, 15.0, 1000)
+    d, zbar = o.delta_z(z)
+    assert abs(zbar - z.mean()) < 1e-12 and abs(d.mean()) < 1e-15
+    np.testing.assert_allclose((1.0 + zbar) * (1.0 + d), 1.0 + z, rtol=1e-14)
+    np.testing.assert_array_equal(o.epsilon_z(z, z), np.zeros_like(z))
+    np.testing.assert_allclose(o.epsilon_z(z + 0.5, z), 0.5 / (1.0 + z), rtol=1e-12)
