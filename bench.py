@@ -368,6 +368,39 @@ def run_amber(args):
                                 "scan_assign_ms": pw["scan_assign"][0] / reps,
                                 "thresholds_ms": pw["thresholds"][0] / reps}
 
+    # --- analysis of the z_re fields (Sec. 2.3) at the workload's size: the
+    # plain and growth-rescaled fields' normalised forms, their auto and cross
+    # shell spectra, and the PDF of their fractional difference
+    analysis = {}
+    if rank == 0 and ws == 1 and not args.no_extras:
+        za, zb = torch.empty_like(S), torch.empty_like(S)
+        ctx.solve(S, m, box, L_MFP, h, out=za)
+        ctx.solve(S, m, box, L_MFP, B.history(*HIST, weighting=B.AMBER_WEIGHT_MASS_GROWTH), out=zb)
+        da, _ = ctx.delta_z(za)
+        db, _ = ctx.delta_z(zb)
+        ps = ctx.power_spectrum(da, db, box)
+        ctx.epsilon_z_pdf(zb, za, -0.05, 0.05, 200)
+        torch.cuda.synchronize()
+
+        def timed(fn, reps=3):
+            e0.record(stream)
+            for _ in range(reps):
+                fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1) / reps
+
+        analysis = {"what": f"{n}^3 z_re fields, plain and growth-rescaled weighting",
+                    "delta_z_ms": timed(lambda: ctx.delta_z(za, out=da)),
+                    "power_spectrum_cross_ms": timed(lambda: ctx.power_spectrum(da, db, box)),
+                    "power_spectrum_auto_ms": timed(lambda: ctx.power_spectrum(da, None, box)),
+                    "epsilon_pdf_ms": timed(lambda: ctx.epsilon_z_pdf(zb, za, -0.05, 0.05, 200)),
+                    "shells": int(ps["modes"].numel())}
+        st = ctx.sync_status()
+        if st != 0:
+            raise RuntimeError(f"device status (analysis): {B.status_string(st)}")
+        del za, zb, da, db, ps
+
     # --- end to end through the public API with pinned host buffers.  Every
     # step copies its inputs in, solves and copies z_re out; two buffer sets
     # let one step's copies overlap the neighbouring steps' solves (H2D and
@@ -482,6 +515,8 @@ def run_amber(args):
                 "cpu_baseline": cpu}
         if weightings:
             line["weightings"] = weightings
+        if analysis:
+            line["analysis"] = analysis
         line.update(extras)
         print(json.dumps(line), flush=True)
     ctx.close()

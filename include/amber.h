@@ -245,6 +245,45 @@ int amber_profile_read(amber_ctx *ctx, int kind, const char **name, double *tota
  * so an intensity field spanning few octaves needs 3 passes, at most 4. */
 int amber_sort_passes(amber_ctx *ctx, int *out_passes);
 
+/* ---- Analysis of z_re fields (Sec. 2.3) -------------------------------- */
+
+/* Normalised redshift field (Eq. deltaz): d_out[x] = ((1 + z[x]) - (1 + zbar))
+ * / (1 + zbar) with zbar the volume-weighted (cell) mean of d_z, summed in
+ * FP64; the field itself is FP32.  d_z, d_out: ncells floats (may alias);
+ * d_zbar_opt: one device double out, or NULL. */
+int amber_delta_z(amber_ctx *ctx, const float *d_z, int64_t ncells, float *d_out, double *d_zbar_opt,
+                  void *stream);
+
+/* PDF of the fractional difference (Eq. epsz) eps = ((1 + z) - (1 + z_ref)) /
+ * (1 + z_ref), FP32 per cell: d_counts[0] counts eps < lo (and NaN),
+ * d_counts[1 + i] the bin [lo + i w, lo + (i+1) w), w = (hi - lo)/nbins, and
+ * d_counts[nbins + 1] eps >= hi (nbins + 2 uint64, device, zeroed here).
+ * d_moments_opt: two device doubles out, sum of eps and of eps^2 (FP64), for
+ * the mean and rms width.  nbins in [1, 16000], lo < hi finite. */
+int amber_epsilon_z_pdf(amber_ctx *ctx, const float *d_z, const float *d_zref, int64_t ncells, double lo,
+                        double hi, int nbins, unsigned long long *d_counts, double *d_moments_opt, void *stream);
+
+/* Number of spherical shells amber_power_spectrum returns for an n^3 grid:
+ * round(sqrt(3) n / 2) + 1 (n a power of two in [4, 1024]).  Host only. */
+int amber_power_bins(int n, int *nbins);
+
+/* Auto and cross power spectra (Eqs. Pk, Dk) of real n^3 fields a and b on a
+ * periodic box of side `box`: P_ij(k) = <delta_i(k) delta_j(k)*> over the
+ * modes of each spherical shell, in the continuum normalisation
+ * delta(k) = (box/n)^3 sum_x delta(x) e^{-i k.x}, P = |delta(k)|^2 / box^3.
+ * Shell b holds every wave vector of the full n^3 transform with integer
+ * components m in [-n/2, n/2) and round(|m|) = b (k = 2 pi m / box), decided
+ * exactly in integers; modes of the half spectrum with 0 < kx < n/2 count
+ * twice (their conjugates).  Outputs (device doubles, amber_power_bins(n)
+ * each, caller-owned): d_k mean |k| of the shell's modes, d_Paa, d_Pbb_opt,
+ * d_Pab_opt (Re P_ab; zero without b), d_modes the number of modes.  With
+ * these, Delta^2 = k^3 P / (2 pi^2), b_ab = sqrt(P_aa / P_bb) and
+ * r_ab = P_ab / sqrt(P_aa P_bb) (Eqs. bias, rcc).  FP32 transforms, FP64 shell
+ * sums.  d_b_opt may be NULL (auto spectrum of a only).  Uses the context's
+ * transform and sort buffers; n^3 <= max_cells (else AMBER_ERR_CAPACITY). */
+int amber_power_spectrum(amber_ctx *ctx, const float *d_a, const float *d_b_opt, int n, double box, double *d_k,
+                         double *d_Paa, double *d_Pbb_opt, double *d_Pab_opt, double *d_modes, void *stream);
+
 /* Test hook for failure detection: runs the production lookback wait on a
  * status array nothing ever publishes, with `spin_limit` iterations, and
  * latches AMBER_ERR_DEVICE_TIMEOUT.  No fault, no trap: the kernel returns. */

@@ -30,6 +30,7 @@ EXPORTED = [
     "amber_status_string", "amber_profile_enable", "amber_profile_reset", "amber_profile_kinds",
     "amber_profile_read", "amber_sort_passes", "amber_test_wait_timeout", "amber_source_field",
     "amber_solve_ex", "amber_assign_zre_ranked", "amber_batch_create", "amber_batch_launch", "amber_batch_destroy",
+    "amber_delta_z", "amber_epsilon_z_pdf", "amber_power_bins", "amber_power_spectrum",
     "amber_rank_noalloc",
 ]
 
@@ -94,6 +95,10 @@ def _load():
         "amber_batch_create": (i32, [C.POINTER(vp), C.POINTER(vp), i32, C.POINTER(amber_batch_item), i32]),
         "amber_batch_launch": (i32, [vp, vp]),
         "amber_batch_destroy": (i32, [vp]),
+        "amber_delta_z": (i32, [vp, vp, i64, vp, vp, vp]),
+        "amber_epsilon_z_pdf": (i32, [vp, vp, vp, i64, dbl, dbl, i32, vp, vp, vp]),
+        "amber_power_bins": (i32, [i32, C.POINTER(i32)]),
+        "amber_power_spectrum": (i32, [vp, vp, vp, i32, dbl, vp, vp, vp, vp, vp, vp]),
         "amber_rank_noalloc": (i32, [vp, i64, vp, vp, vp]),
         "amber_test_wait_timeout": (i32, [vp, C.c_uint, vp]),
     }
@@ -125,6 +130,22 @@ def history(z_mid: float, dz: float, Az: float, x_points=(0.05, 0.5, 0.95), z_lo
     h.z_lo, h.z_hi, h.n_table = z_lo, z_hi, n_table
     h.weighting, h.omega_m = weighting, omega_m
     return h
+
+
+def power_bins(n: int) -> int:
+    out = C.c_int()
+    _check(lib.amber_power_bins(n, C.byref(out)), "amber_power_bins")
+    return out.value
+
+
+def derived_spectra(s: dict) -> dict:
+    """Delta^2 (Eq. Dk), bias b_ab (Eq. bias) and cross-correlation r_ab (Eq. rcc)
+    from power_spectrum's output (host numpy; shells without modes give nan)."""
+    import numpy as np
+    k, Paa, Pbb, Pab = (s[key].cpu().numpy() for key in ("k", "Paa", "Pbb", "Pab"))
+    with np.errstate(invalid="ignore", divide="ignore"):
+        return {"k": k, "Delta2_aa": k ** 3 * Paa / (2 * np.pi ** 2), "Delta2_bb": k ** 3 * Pbb / (2 * np.pi ** 2),
+                "bias": np.sqrt(Paa / Pbb), "r": Pab / np.sqrt(Paa * Pbb)}
 
 
 def history_coeffs(h: amber_history_t):
@@ -308,3 +329,35 @@ class Context:
 
     def test_wait_timeout(self, spin_limit: int, stream=None):
         _check(lib.amber_test_wait_timeout(self._h, spin_limit, _stream(stream)), "amber_test_wait_timeout")
+
+    # --- analysis of z_re fields (Sec. 2.3) ----------------------------------
+    def delta_z(self, z, out=None, stream=None):
+        """(delta_z field, zbar tensor) of a float field (Eq. deltaz)."""
+        import torch
+        if out is None:
+            out = torch.empty_like(z)
+        zbar = torch.empty(1, dtype=torch.float64, device=z.device)
+        _check(lib.amber_delta_z(self._h, _ptr(z), z.numel(), _ptr(out), _ptr(zbar), _stream(stream)),
+               "amber_delta_z")
+        return out, zbar
+
+    def epsilon_z_pdf(self, z, z_ref, lo: float, hi: float, nbins: int, stream=None):
+        """(counts [nbins + 2] with under/overflow at the ends, [sum eps, sum eps^2]) (Eq. epsz)."""
+        import torch
+        counts = torch.empty(nbins + 2, dtype=torch.int64, device=z.device)
+        mom = torch.empty(2, dtype=torch.float64, device=z.device)
+        _check(lib.amber_epsilon_z_pdf(self._h, _ptr(z), _ptr(z_ref), z.numel(), lo, hi, nbins, _ptr(counts),
+                                       _ptr(mom), _stream(stream)), "amber_epsilon_z_pdf")
+        return counts, mom
+
+    def power_spectrum(self, a, b=None, box: float = 1.0, stream=None):
+        """Shell spectra (Eqs. Pk, Dk, bias, rcc) of n^3 float fields: dict of
+        device tensors k, Paa, Pbb, Pab, modes (per shell)."""
+        import torch
+        n = a.shape[0]
+        nb = power_bins(n)
+        out = {key: torch.empty(nb, dtype=torch.float64, device=a.device) for key in ("k", "Paa", "Pbb", "Pab", "modes")}
+        _check(lib.amber_power_spectrum(self._h, _ptr(a), _ptr(b), n, box, _ptr(out["k"]), _ptr(out["Paa"]),
+                                        _ptr(out["Pbb"]), _ptr(out["Pab"]), _ptr(out["modes"]), _stream(stream)),
+               "amber_power_spectrum")
+        return out

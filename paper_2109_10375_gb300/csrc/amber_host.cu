@@ -12,6 +12,7 @@
 #include "fft.cuh"
 #include "sort.cuh"
 #include "source.cuh"
+#include "spectra.cuh"
 
 namespace amber {
 // krange: if not null, the intensities' key range is folded into it (the
@@ -162,7 +163,7 @@ struct Plan {
   int n32 = 0, n64 = 0;
   int64_t cells64 = 0;
   size_t off_spec, off_keysA, off_keysB, off_idxA, off_idxB, off_massA, off_massB, off_lb, off_sctrl, off_actrl, off_X, off_invdx, off_lin,
-      off_state, off_btab, off_tilemass, off_status, off_srcsum, off_tw32, off_tw64, total;
+      off_state, off_btab, off_tilemass, off_status, off_srcsum, off_pow, off_tw32, off_tw64, total;
   size_t tw32_off[11] = {}, tw64_off[11] = {};
 };
 
@@ -199,6 +200,7 @@ static Plan make_plan(int64_t max_cells) {
   p.off_tilemass = take((size_t)sort_tiles(max_cells) * 16);
   p.off_status = take(256);
   p.off_srcsum = take(256);
+  p.off_pow = take((size_t)kPowerAcc * kMaxPowerBins * sizeof(double));
   size_t tw32 = 0, tw64 = 0;
   for (int l = 2, n = 4; n <= 1024; ++l, n *= 2) {
     if (n <= p.n32) { p.tw32_off[l] = tw32; tw32 += align256((size_t)n * 8); }
@@ -415,6 +417,57 @@ int amber_radiation_field_f64(amber_ctx* c, const double* d_src, int n, double b
   const int l = ilog2i(n);
   return cuda_status(radiation_field_f64(n, d_src, d_J, c->ws + p.off_spec, c->ws + p.off_tw64 + p.tw64_off[l], box,
                                          l_mfp, c->status, s, &c->prof, nullptr));
+}
+
+int amber_power_bins(int n, int* nbins) {
+  if (!nbins || !is_pow2_in(n, 4, 1024)) return AMBER_ERR_INVALID_ARG;
+  *nbins = power_bins(n);
+  return AMBER_OK;
+}
+
+int amber_delta_z(amber_ctx* c, const float* d_z, int64_t ncells, float* d_out, double* d_zbar_opt, void* stream) {
+  if (!c || !d_z || !d_out || ncells < 1) return AMBER_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(c->mu);
+  DeviceGuard g(c->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  c->last_stream = s;
+  double* acc = reinterpret_cast<double*>(c->ws + c->plan.off_pow);
+  return cuda_status(delta_z_impl(d_z, ncells, d_out, acc, d_zbar_opt, c->num_sms, s));
+}
+
+int amber_epsilon_z_pdf(amber_ctx* c, const float* d_z, const float* d_zref, int64_t ncells, double lo, double hi,
+                        int nbins, unsigned long long* d_counts, double* d_moments_opt, void* stream) {
+  if (!c || !d_z || !d_zref || !d_counts || ncells < 1) return AMBER_ERR_INVALID_ARG;
+  if (!std::isfinite(lo) || !std::isfinite(hi) || !(hi > lo) || nbins < 1 || nbins > 16000)
+    return AMBER_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(c->mu);
+  DeviceGuard g(c->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  c->last_stream = s;
+  return cuda_status(epsilon_pdf_impl(d_z, d_zref, ncells, lo, hi, nbins, d_counts, d_moments_opt, c->num_sms, s));
+}
+
+int amber_power_spectrum(amber_ctx* c, const float* d_a, const float* d_b_opt, int n, double box, double* d_k,
+                         double* d_Paa, double* d_Pbb_opt, double* d_Pab_opt, double* d_modes, void* stream) {
+  if (!c || !d_a || !d_k || !d_Paa || !d_modes) return AMBER_ERR_INVALID_ARG;
+  if (!is_pow2_in(n, 4, 1024) || !(box > 0.0) || !std::isfinite(box)) return AMBER_ERR_INVALID_ARG;
+  if (n > c->plan.n32) return AMBER_ERR_CAPACITY;
+  std::lock_guard<std::mutex> lk(c->mu);
+  DeviceGuard g(c->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  c->last_stream = s;
+  const Plan& p = c->plan;
+  const void* tw = c->ws + p.off_tw32 + p.tw32_off[ilog2i(n)];
+  // a's spectrum in the transform buffer; b's in the key buffers, which are
+  // contiguous and hold 8 bytes per cell (the half spectrum needs 4 + 16/n)
+  void* Ha = c->ws + p.off_spec;
+  void* Hb = d_b_opt ? static_cast<void*>(c->sortw.keysA) : nullptr;
+  cudaError_t e = forward_spectrum_f32(n, d_a, Ha, tw, s);
+  if (e == cudaSuccess && d_b_opt) e = forward_spectrum_f32(n, d_b_opt, Hb, tw, s);
+  if (e == cudaSuccess)
+    e = power_impl(Ha, Hb, n, box, reinterpret_cast<double*>(c->ws + p.off_pow), d_k, d_Paa, d_Pbb_opt, d_Pab_opt,
+                   d_modes, c->num_sms, s);
+  return cuda_status(e);
 }
 
 int amber_rank(amber_ctx* c, const float* d_J, int64_t ncells, uint32_t* d_order, void* stream) {

@@ -478,4 +478,32 @@ cudaError_t radiation_field_n(const T* src, T* J, cpx<T>* H, const cpx<T>* tw, d
   return cudaGetLastError();
 }
 
+// Forward transform only: H = DFT(src) as the half spectrum [n][n][n/2+2]
+// (x-pass R2C, then forward y and z passes, unnormalised), for the analysis
+// of fields (power spectra).
+template <typename T, int N>
+cudaError_t forward_spectrum_n(const T* src, cpx<T>* H, const cpx<T>* tw, cudaStream_t s) {
+  using C = FftCfg<N>;
+  const int RS = N / 2 + 2;
+  const int ncol = N / 2 + 1;
+  const int64_t nrows = (int64_t)N * N;
+  const size_t xs = XSmem<T, N>::elems * sizeof(cpx<T>);
+  const size_t ss = StridedSmem<T, N>::elems * sizeof(cpx<T>);
+  static std::atomic<unsigned long long> attr_done{0};  // per instantiation and device
+  if (first_use_on_device(attr_done)) {
+    cudaFuncSetAttribute(k_fft_r2c_x<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xs);
+    cudaFuncSetAttribute(k_fft_strided<T, N, PASS_FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss);
+  }
+  const int xgrid = (int)((nrows / 2 + C::XP - 1) / C::XP);
+  const int ntx = (ncol + C::SB - 1) / C::SB;
+  const int sgrid = N * ntx;
+  const T zero = (T)0;
+  k_fft_r2c_x<T, N><<<xgrid, xpass_threads<N>(), xs, s>>>(src, H, nrows, RS, tw);
+  k_fft_strided<T, N, PASS_FWD><<<sgrid, strided_threads<N>(), ss, s>>>(H, RS, (int64_t)N * RS, ncol, ntx, tw,
+                                                                       zero, zero, zero);
+  k_fft_strided<T, N, PASS_FWD><<<sgrid, strided_threads<N>(), ss, s>>>(H, (int64_t)N * RS, RS, ncol, ntx, tw,
+                                                                       zero, zero, zero);
+  return cudaGetLastError();
+}
+
 }  // namespace amber

@@ -22,4 +22,21 @@ cudaError_t radiation_field_f32(int n, const float* src, float* J, void* H, cons
   }
 }
 
+cudaError_t forward_spectrum_f32(int n, const float* src, void* H, const void* tw, cudaStream_t s) {
+  auto* h = reinterpret_cast<cpx<float>*>(H);
+  auto* w = reinterpret_cast<const cpx<float>*>(tw);
+  switch (n) {
+    case 4: return forward_spectrum_n<float, 4>(src, h, w, s);
+    case 8: return forward_spectrum_n<float, 8>(src, h, w, s);
+    case 16: return forward_spectrum_n<float, 16>(src, h, w, s);
+    case 32: return forward_spectrum_n<float, 32>(src, h, w, s);
+    case 64: return forward_spectrum_n<float, 64>(src, h, w, s);
+    case 128: return forward_spectrum_n<float, 128>(src, h, w, s);
+    case 256: return forward_spectrum_n<float, 256>(src, h, w, s);
+    case 512: return forward_spectrum_n<float, 512>(src, h, w, s);
+    case 1024: return forward_spectrum_n<float, 1024>(src, h, w, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 }  // namespace amber
