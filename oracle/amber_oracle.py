@@ -30,6 +30,11 @@ Steps and the passages they follow
   (ties: ascending cell index), F_n = sum_{m<=n} mass_m / sum_all mass, and z_n
   from the tabulated history x(z_j) by linear interpolation in z between the
   two table points that bracket F_n.
+* Source-field pipeline (Sec. 3.2, Eq. xlpt; Sec. 3.2.1, Eqs. interlace and
+  Wofk; Sec. 3.3, Eqs. fcoll and variance): second-order Lagrangian
+  displacements from spectral potentials, NGP/CIC/TSC assignment by plain
+  loops over particles, the interlaced and deconvolved mesh, and the ESF
+  collapsed fraction of a filtered linear field.
 * Analysis (Sec. 2.3, Eqs. epsz, deltaz, Pk, Dk, bias, rcc): the normalised
   and fractional-difference redshift fields, and spherical-shell auto and
   cross power spectra with the bias and cross-correlation built from them
@@ -468,6 +473,153 @@ def bias(P_ii, P_jj):
 def cross_correlation(P_ij, P_ii, P_jj):
     """r_ij = P_ij / sqrt(P_ii P_jj) (Eq. rcc)."""
     return np.asarray(P_ij) / np.sqrt(np.asarray(P_ii) * np.asarray(P_jj))
+
+
+# ---------------------------------------------------------------------------
+# Source-field pipeline (Sec. 3.2: 2LPT, mesh assignment with interlacing and
+# deconvolution; Sec. 3.3: ESF-L collapsed fraction)
+# ---------------------------------------------------------------------------
+
+def _int_freqs(n):
+    """Signed integer frequencies m in [-n/2, n/2) along one axis."""
+    return np.fft.fftfreq(n, 1.0 / n)
+
+
+def _kgrid(n, box):
+    """k components [z][y][x] for numpy's full fftn layout, and the Nyquist masks."""
+    m = _int_freqs(n)
+    kf = 2.0 * math.pi / box
+    mz, my, mx = np.meshgrid(m, m, m, indexing="ij")
+    nyq = -(n // 2)
+    return (kf * mx, kf * my, kf * mz), (mx == nyq, my == nyq, mz == nyq)
+
+
+def lpt_displacement(delta_lin, box: float, D1: float, D2: float):
+    """Second-order Lagrangian displacement psi(q) = x - q (Eq. xlpt):
+    x = q - D1 grad phi1 + D2 grad phi2 with
+      lap phi1 = delta_lin,
+      lap phi2 = sum_{i<j} [phi1,ii phi1,jj - (phi1,ij)^2],
+    derivatives taken spectrally on the periodic n^3 lattice of side box
+    (phi at k = 0 is 0).  A derivative along an axis whose wave number is the
+    Nyquist one is set to 0 for odd orders along that axis (it has no real
+    counterpart).  Returns (psi_x, psi_y, psi_z), arrays [z][y][x], in box
+    length units."""
+    d = np.asarray(delta_lin, dtype=np.float64)
+    n = d.shape[0]
+    (kx, ky, kz), (nx, ny, nz) = _kgrid(n, box)
+    k2 = kx * kx + ky * ky + kz * kz
+    D = np.fft.fftn(d)
+    inv_k2 = np.where(k2 > 0, 1.0 / np.where(k2 > 0, k2, 1.0), 0.0)
+    phi1 = -D * inv_k2
+    ks = (kx, ky, kz)
+    nq = (nx, ny, nz)
+
+    def deriv2(P, a, b):
+        out = -ks[a] * ks[b] * P
+        if a != b:
+            out = np.where(nq[a] | nq[b], 0.0, out)
+        return np.fft.ifftn(out).real
+
+    def grad(P, a):
+        return np.fft.ifftn(np.where(nq[a], 0.0, 1j * ks[a] * P)).real
+
+    p = {(a, b): deriv2(phi1, a, b) for a in range(3) for b in range(a, 3)}
+    src = (p[0, 0] * p[1, 1] + p[0, 0] * p[2, 2] + p[1, 1] * p[2, 2]
+           - p[0, 1] ** 2 - p[0, 2] ** 2 - p[1, 2] ** 2)
+    phi2 = -np.fft.fftn(src) * inv_k2
+    return tuple(-D1 * grad(phi1, a) + D2 * grad(phi2, a) for a in range(3))
+
+
+def assignment_weights_1d(d, p: int):
+    """Weights of the mesh points at offsets -1, 0, +1 (and the point itself
+    for NGP) from a particle at signed distance d in cells from its nearest
+    mesh point (|d| <= 1/2): NGP (p = 1), CIC (p = 2) and TSC (p = 3), the
+    assignment windows whose transforms are Eq. Wofk."""
+    if p == 1:
+        return {0: 1.0}
+    if p == 2:
+        return {0: 1.0 - abs(d), (1 if d >= 0 else -1): abs(d)}
+    return {-1: 0.5 * (0.5 - d) ** 2, 0: 0.75 - d * d, 1: 0.5 * (0.5 + d) ** 2}
+
+
+def mesh_assign(psi, mass, box: float, p: int, shift: float = 0.0):
+    """rho(x_n) / mean: particles at lattice points q_i = i dx displaced by psi
+    (box units, periodic), optionally all shifted by `shift` cells in each
+    direction, assigned to the mesh points x_n = n dx with the order-p window
+    (Sec. 3.2.1).  mass: per-particle masses [z][y][x] or None (all equal).
+    Plain loops over particles (small n only)."""
+    px, py, pz = (np.asarray(c, dtype=np.float64) for c in psi)
+    n = px.shape[0]
+    dx = box / n
+    m = np.ones((n, n, n)) if mass is None else np.asarray(mass, dtype=np.float64)
+    rho = np.zeros((n, n, n))
+    for iz in range(n):
+        for iy in range(n):
+            for ix in range(n):
+                pos = [ix + px[iz, iy, ix] / dx + shift, iy + py[iz, iy, ix] / dx + shift,
+                       iz + pz[iz, iy, ix] / dx + shift]
+                base = [int(math.floor(c + 0.5)) for c in pos]  # nearest mesh point
+                w = [assignment_weights_1d(pos[a] - base[a], p) for a in range(3)]
+                for oz, wz in w[2].items():
+                    for oy, wy in w[1].items():
+                        for ox, wx in w[0].items():
+                            rho[(base[2] + oz) % n, (base[1] + oy) % n, (base[0] + ox) % n] += \
+                                m[iz, iy, ix] * wx * wy * wz
+    return rho * (n ** 3 / m.sum())
+
+
+def interlace_deconvolve(rho1, rho2, box: float, p: int):
+    """Eqs. interlace and Wofk: rho(k) = [rho1(k) + e^{i k.dX} rho2(k)] / 2 /
+    W(k), dX = (dx/2)(1, 1, 1) the shift of the second mesh's particles, and
+    W(k) = [prod_a sin(k_a dx/2)/(k_a dx/2)]^p.  Modes with a Nyquist
+    component are set to 0: after the half-cell twiddle they have no real
+    counterpart.  Returns the real field."""
+    r1 = np.fft.fftn(np.asarray(rho1, dtype=np.float64))
+    r2 = np.fft.fftn(np.asarray(rho2, dtype=np.float64))
+    n = r1.shape[0]
+    dx = box / n
+    (kx, ky, kz), (nx, ny, nz) = _kgrid(n, box)
+    sinc = lambda t: np.where(t == 0, 1.0, np.sin(t) / np.where(t == 0, 1.0, t))
+    W = (sinc(kx * dx / 2) * sinc(ky * dx / 2) * sinc(kz * dx / 2)) ** p
+    tw = np.exp(1j * (kx + ky + kz) * dx / 2)
+    out = 0.5 * (r1 + tw * r2) / W
+    out = np.where(nx | ny | nz, 0.0, out)
+    return np.fft.ifftn(out).real
+
+
+def filter_field(delta, box: float, R: float, kind: str):
+    """delta_f(k) = delta(k) W_f(k) (Sec. 3.3): sharp k-space filter (W = 1
+    for k R <= 1, else 0) or spherical top hat W = 3 (sin x - x cos x)/x^3,
+    x = k R."""
+    D = np.fft.fftn(np.asarray(delta, dtype=np.float64))
+    n = D.shape[0]
+    (kx, ky, kz), _ = _kgrid(n, box)
+    kk = np.sqrt(kx * kx + ky * ky + kz * kz)
+    if kind == "sharpk":
+        W = (kk * R <= 1.0).astype(np.float64)
+    else:
+        x = kk * R
+        xs = np.where(x > 0, x, 1.0)
+        W = np.where(x > 0, 3.0 * (np.sin(xs) - xs * np.cos(xs)) / xs ** 3, 1.0)
+    return np.fft.ifftn(D * W).real
+
+
+def fcoll_esf(delta_f, delta_c: float, dsigma2: float):
+    """Collapsed fraction (Eq. fcoll): erfc[(delta_c - delta_f) / sqrt(2 dsigma2)],
+    dsigma2 = sigma^2(M_min) - sigma^2(M_s)."""
+    from scipy.special import erfc
+    return erfc((delta_c - np.asarray(delta_f, dtype=np.float64)) / math.sqrt(2.0 * dsigma2))
+
+
+def sigma2_tophat(k, Delta2, R: float):
+    """Eq. variance: sigma^2(R) = int Delta^2_lin(k) |W_th(kR)|^2 dln k by the
+    trapezoid rule over a tabulated Delta^2 on increasing k."""
+    k = np.asarray(k, dtype=np.float64)
+    x = k * R
+    W = 3.0 * (np.sin(x) - x * np.cos(x)) / x ** 3
+    f = np.asarray(Delta2, dtype=np.float64) * W * W
+    lk = np.log(k)
+    return float(np.sum(0.5 * (f[1:] + f[:-1]) * np.diff(lk)))
 
 
 def solve(S, mass, box: float, l_mfp: float, z_mid: float, dz: float, Az: float,

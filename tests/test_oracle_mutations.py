@@ -37,7 +37,40 @@ PINS = [
     lambda: pins.test_bias_and_cross_correlation_identities(),
     lambda: pins.test_white_noise_power_is_flat(),
     lambda: pins.test_delta_z_and_epsilon_z_closed_forms(),
+    lambda: pins.test_lpt_plane_wave_is_zeldovich(),
+    lambda: pins.test_lpt_two_orthogonal_waves_second_order(),
+    lambda: pins.test_assignment_weights_are_the_b_splines(),
+    lambda: [pins.test_mesh_assign_uniform_lattice_and_translation(p, sh) for p in (1, 2, 3) for sh in (0.0, 0.5)],
+    lambda: [pins.test_interlace_realigns_and_deconvolves_a_plane_wave(p) for p in (0, 2, 3)],
+    lambda: pins.test_filters_on_plane_waves(),
+    lambda: pins.test_fcoll_closed_forms(),
 ]
+
+_weights = o.assignment_weights_1d
+
+
+def _tsc_mirrored(d, p):
+    w = _weights(d, p)
+    return {-k: v for k, v in w.items()} if p == 3 else w
+
+
+def _interlace_wrong_twiddle(rho1, rho2, box, p):
+    # the half-cell twiddle applied with the opposite sign
+    r1, r2 = np.fft.fftn(rho1), np.fft.fftn(rho2)
+    n = r1.shape[0]
+    dx = box / n
+    (kx, ky, kz), (nx, ny, nz) = o._kgrid(n, box)
+    sinc = lambda t: np.where(t == 0, 1.0, np.sin(t) / np.where(t == 0, 1.0, t))
+    W = (sinc(kx * dx / 2) * sinc(ky * dx / 2) * sinc(kz * dx / 2)) ** p
+    out = 0.5 * (r1 + np.exp(-1j * (kx + ky + kz) * dx / 2) * r2) / W
+    return np.fft.ifftn(np.where(nx | ny | nz, 0.0, out)).real
+
+
+_lpt = o.lpt_displacement
+
+
+def _lpt_first_order_only(delta_lin, box, D1, D2):
+    return _lpt(delta_lin, box, D1, 0.0)
 
 _power = o.power_spectrum
 
@@ -94,6 +127,9 @@ MUTATIONS = {
     "power_cross_is_geometric_mean": ("power_spectrum", _power_cross_swapped),
     "delta_z_not_normalised": ("delta_z", lambda z: (lambda zz: (zz - zz.mean(), float(zz.mean())))(
         np.asarray(z, dtype=np.float64))),
+    "tsc_weights_mirrored": ("assignment_weights_1d", _tsc_mirrored),
+    "interlace_twiddle_sign": ("interlace_deconvolve", _interlace_wrong_twiddle),
+    "lpt_drops_second_order": ("lpt_displacement", _lpt_first_order_only),
 }
 
 

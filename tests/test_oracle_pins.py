@@ -549,3 +549,108 @@ def test_delta_z_and_epsilon_z_closed_forms():
     np.testing.assert_allclose((1.0 + zbar) * (1.0 + d), 1.0 + z, rtol=1e-14)
     np.testing.assert_array_equal(o.epsilon_z(z, z), np.zeros_like(z))
     np.testing.assert_allclose(o.epsilon_z(z + 0.5, z), 0.5 / (1.0 + z), rtol=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# Source-field pipeline (Sec. 3.2, 3.2.1, 3.3)
+# ---------------------------------------------------------------------------
+
+def _xyz(n, box):
+    x = np.arange(n) * box / n
+    Z, Y, X = np.meshgrid(x, x, x, indexing="ij")
+    return X, Y, Z
+
+
+def test_lpt_plane_wave_is_zeldovich():
+    # delta = A cos(k x): phi1 = -A cos(kx)/k^2, no second-order source, so
+    # psi_x = -D1 A sin(k x)/k exactly and psi_y = psi_z = 0
+    n, box, A, D1 = 16, 32.0, 0.3, 0.8
+    X, Y, Z = _xyz(n, box)
+    k = 2 * np.pi * 3 / box
+    px, py, pz = o.lpt_displacement(A * np.cos(k * X), box, D1, -3.0 / 7.0 * D1 ** 2)
+    np.testing.assert_allclose(px, -D1 * A * np.sin(k * X) / k, atol=1e-12)
+    assert np.max(np.abs(py)) < 1e-13 and np.max(np.abs(pz)) < 1e-13
+
+
+def test_lpt_two_orthogonal_waves_second_order():
+    # delta = A cos(k1 x) + B cos(k2 y): source = A B cos(k1 x) cos(k2 y) and
+    # phi2 = -A B cos(k1 x) cos(k2 y)/(k1^2 + k2^2)
+    n, box, A, Bm, D1 = 16, 20.0, 0.4, 0.25, 1.3
+    D2 = -3.0 / 7.0 * D1 ** 2
+    X, Y, Z = _xyz(n, box)
+    k1, k2 = 2 * np.pi * 2 / box, 2 * np.pi * 5 / box
+    px, py, pz = o.lpt_displacement(A * np.cos(k1 * X) + Bm * np.cos(k2 * Y), box, D1, D2)
+    c = A * Bm / (k1 ** 2 + k2 ** 2)
+    np.testing.assert_allclose(px, -D1 * A * np.sin(k1 * X) / k1 + D2 * c * k1 * np.sin(k1 * X) * np.cos(k2 * Y),
+                               atol=1e-12)
+    np.testing.assert_allclose(py, -D1 * Bm * np.sin(k2 * Y) / k2 + D2 * c * k2 * np.cos(k1 * X) * np.sin(k2 * Y),
+                               atol=1e-12)
+    assert np.max(np.abs(pz)) < 1e-13
+
+
+def test_assignment_weights_are_the_b_splines():
+    # B-spline windows of order 1, 2, 3 at a quarter-cell offset
+    assert o.assignment_weights_1d(0.25, 1) == {0: 1.0}
+    assert o.assignment_weights_1d(0.25, 2) == {0: 0.75, 1: 0.25}
+    assert o.assignment_weights_1d(-0.25, 2) == {0: 0.75, -1: 0.25}
+    w = o.assignment_weights_1d(0.25, 3)
+    assert abs(w[-1] - 0.03125) < 1e-15 and abs(w[0] - 0.6875) < 1e-15 and abs(w[1] - 0.28125) < 1e-15
+
+
+@pytest.mark.parametrize("p", [1, 2, 3])
+@pytest.mark.parametrize("shift", [0.0, 0.5])
+def test_mesh_assign_uniform_lattice_and_translation(p, shift):
+    n, box = 6, 12.0
+    zero = np.zeros((n, n, n))
+    rho = o.mesh_assign((zero, zero, zero), None, box, p, shift)
+    np.testing.assert_allclose(rho, 1.0, atol=1e-14)
+    # a whole-cell translation of every particle shifts the mesh exactly
+    g = np.random.default_rng(p)
+    psi = tuple(g.uniform(-0.4, 0.4, (n, n, n)) * box / n for _ in range(3))
+    m = g.uniform(0.5, 2.0, (n, n, n))
+    r0 = o.mesh_assign(psi, m, box, p, shift)
+    r1 = o.mesh_assign((psi[0] + box / n, psi[1], psi[2]), m, box, p, shift)
+    np.testing.assert_allclose(r1, np.roll(r0, 1, axis=2), atol=1e-12)
+    assert abs(r0.mean() - 1.0) < 1e-14
+
+
+@pytest.mark.parametrize("p", [0, 2, 3])
+def test_interlace_realigns_and_deconvolves_a_plane_wave(p):
+    # rho1 = f(x_n), rho2 = f(x_n - dX): the second mesh's particles moved
+    # by +dX, so its point x_n sees what sat at x_n - dX; the combination is
+    # f(x_n) with the mode divided by W(k)
+    n, box, eps = 16, 30.0, 0.2
+    X, Y, Z = _xyz(n, box)
+    m = np.array([2, -3, 5])
+    kv = 2 * np.pi * m / box
+    dx = box / n
+    f = lambda sx: 1 + eps * np.cos(kv[0] * (X - sx) + kv[1] * (Y - sx) + kv[2] * (Z - sx))
+    got = o.interlace_deconvolve(f(0.0), f(dx / 2), box, p)
+    W = np.prod([np.sin(k * dx / 2) / (k * dx / 2) for k in kv]) ** p
+    np.testing.assert_allclose(got, 1 + eps / W * np.cos(kv[0] * X + kv[1] * Y + kv[2] * Z), atol=1e-12)
+
+
+def test_filters_on_plane_waves():
+    n, box = 16, 40.0
+    X, Y, Z = _xyz(n, box)
+    k1, k2 = 2 * np.pi * 1 / box, 2 * np.pi * 4 / box
+    d = np.cos(k1 * X) + np.cos(k2 * Z)
+    R = 1.0 / (0.5 * (k1 + k2))  # between the two modes
+    np.testing.assert_allclose(o.filter_field(d, box, R, "sharpk"), np.cos(k1 * X), atol=1e-12)
+    th = lambda x: 3 * (np.sin(x) - x * np.cos(x)) / x ** 3
+    np.testing.assert_allclose(o.filter_field(d, box, R, "tophat"),
+                               th(k1 * R) * np.cos(k1 * X) + th(k2 * R) * np.cos(k2 * Z), atol=1e-12)
+
+
+def test_fcoll_closed_forms():
+    from scipy.special import erfc
+    dc, ds2 = 1.686 / 0.1, 4.0
+    np.testing.assert_allclose(o.fcoll_esf([dc, dc - math.sqrt(2 * ds2), -1e9], dc, ds2), [1.0, erfc(1.0), 0.0],
+                               atol=1e-15)
+
+
+def test_sigma2_tophat_small_radius_limit():
+    # Delta^2 = 1 on [k1, k2], R -> 0: W -> 1, sigma^2 -> ln(k2/k1)
+    k = np.geomspace(0.1, 10.0, 20001)
+    s2 = o.sigma2_tophat(k, np.ones_like(k), 1e-4)
+    assert abs(s2 / math.log(100.0) - 1.0) < 1e-6
