@@ -401,6 +401,40 @@ def run_amber(args):
             raise RuntimeError(f"device status (analysis): {B.status_string(st)}")
         del za, zb, da, db, ps
 
+    # --- the source-field pipeline that makes S and the mass field (Sec. 3.2,
+    # 3.3): 2LPT displacements of one particle per cell from a linear field,
+    # TSC matter density and ESF-L halo density (CIC), both interlaced
+    source_pipeline = {}
+    if rank == 0 and ws == 1 and not args.no_extras:
+        d_lin = synth.gaussian_density(n, box, 2000, sigma=1.0, device="cuda").float()
+        D1 = 0.25  # linear field scaled to sigma 0.25 at the target redshift
+        D2 = -3.0 / 7.0 * D1 ** 2
+        psi = ctx.lpt_displacement(d_lin, box, D1, D2)
+        rho_m = ctx.mesh_density(psi, box, 3, True)
+        f = ctx.esf_fcoll(d_lin, box, 2.0 * box / n, 1.686 / D1, 1.0)
+        rho_h = ctx.mesh_density(psi, box, 2, True, mass=f)
+        torch.cuda.synchronize()
+
+        def once(fn):
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1)
+
+        source_pipeline = {
+            "what": f"{n}^3 particles and mesh; linear field sigma 1 scaled by D1 = {D1}",
+            "lpt_2nd_order_ms": once(lambda: ctx.lpt_displacement(d_lin, box, D1, D2)),
+            "tsc_interlaced_ms": once(lambda: ctx.mesh_density(psi, box, 3, True, out=rho_m)),
+            "esf_fcoll_sharpk_ms": once(lambda: ctx.esf_fcoll(d_lin, box, 2.0 * box / n, 1.686 / D1, 1.0, out=f)),
+            "cic_interlaced_weighted_ms": once(lambda: ctx.mesh_density(psi, box, 2, True, mass=f, out=rho_h)),
+            "rho_m_mean": float(rho_m.double().mean()), "rho_h_mean": float(rho_h.double().mean())}
+        st = ctx.sync_status()
+        if st != 0:
+            raise RuntimeError(f"device status (source pipeline): {B.status_string(st)}")
+        del d_lin, psi, rho_m, f, rho_h
+        torch.cuda.empty_cache()
+
     # --- end to end through the public API with pinned host buffers.  Every
     # step copies its inputs in, solves and copies z_re out; two buffer sets
     # let one step's copies overlap the neighbouring steps' solves (H2D and
@@ -517,6 +551,8 @@ def run_amber(args):
             line["weightings"] = weightings
         if analysis:
             line["analysis"] = analysis
+        if source_pipeline:
+            line["source_pipeline"] = source_pipeline
         line.update(extras)
         print(json.dumps(line), flush=True)
     ctx.close()

@@ -245,6 +245,52 @@ int amber_profile_read(amber_ctx *ctx, int kind, const char **name, double *tota
  * so an intensity field spanning few octaves needs 3 passes, at most 4. */
 int amber_sort_passes(amber_ctx *ctx, int *out_passes);
 
+/* ---- Source-field pipeline (Sec. 3.2, 3.2.1, 3.3) ----------------------- */
+
+/* Second-order Lagrangian displacement (Sec. 3.2, Eq. xlpt) of one particle
+ * per lattice point q of an n^3 periodic box of side `box`:
+ *   psi = x - q = -D1 grad phi1 + D2 grad phi2,
+ *   lap phi1 = delta_lin,  lap phi2 = sum_{i<j} [phi1,ii phi1,jj - (phi1,ij)^2],
+ * derivatives spectral (phi at k = 0 is 0; an odd derivative along an axis
+ * at its Nyquist wave number is 0).  D1, D2: the first- and second-order
+ * growth factors at the target redshift (the usual D2 = -3/7 D1^2).
+ * d_delta_lin: n^3 floats [z][y][x], the linear overdensity the growth
+ * factors scale; d_psi_x/y/z: n^3 floats each out, box units (also used as
+ * scratch).  FP32 transforms.  Uses the context's transform, sort and mass
+ * buffers; n a power of two in [4, 1024] with n^3 <= max_cells. */
+int amber_lpt_displacement(amber_ctx *ctx, const float *d_delta_lin, int n, double box, double D1, double D2,
+                           float *d_psi_x, float *d_psi_y, float *d_psi_z, void *stream);
+
+/* Mesh density rho / <rho> (Sec. 3.2.1) from particles at q + psi (one per
+ * lattice point, periodic) with masses d_mass_opt (n^3 floats, NULL: all
+ * equal), assigned to the mesh points x_n = n dx with the order-`order`
+ * window: 1 NGP, 2 CIC, 3 TSC (particle at distance d in [-1/2, 1/2) cells
+ * from its nearest mesh point).  interlace = 1: a second mesh whose particles
+ * move by dx/2 on every axis, combined as [rho1(k) + e^{i k.dX} rho2(k)] / 2 /
+ * W(k) with W the window's transform [prod sin(k_a dx/2)/(k_a dx/2)]^order
+ * (Eqs. interlace, Wofk); modes with a Nyquist component are dropped (after
+ * the half-cell twiddle they have no real counterpart).  interlace = 0: the
+ * plain assignment, not deconvolved.  FP32 atomics (sums in any order).
+ * d_rho: n^3 floats out. */
+int amber_mesh_density(amber_ctx *ctx, const float *d_psi_x, const float *d_psi_y, const float *d_psi_z,
+                       const float *d_mass_opt, int n, double box, int order, int interlace, float *d_rho,
+                       void *stream);
+
+/* ESF collapsed fraction (Sec. 3.3, Eq. fcoll): delta_f = delta_lin filtered
+ * with a sharp k-space window (filter 0: W = 1 for k R <= 1, else 0) or a
+ * spherical top hat (filter 1: W = 3 (sin x - x cos x)/x^3, x = k R), then
+ * f_coll = erfc[(delta_c - delta_f) / sqrt(2 dsigma2)] with delta_c the
+ * barrier delta_crit / D(z) and dsigma2 = sigma^2(M_min) - sigma^2(M_s).
+ * In ESF-L the particles then carry f_coll m_p to amber_mesh_density.
+ * d_fcoll: n^3 floats out. */
+int amber_esf_fcoll(amber_ctx *ctx, const float *d_delta_lin, int n, double box, double R, int filter,
+                    double delta_c, double dsigma2, float *d_fcoll, void *stream);
+
+/* sigma^2(R) = int Delta^2_lin(k) |W_th(k R)|^2 dln k (Sec. 3.3, Eq. variance)
+ * by the trapezoid rule over a tabulated dimensionless linear power spectrum
+ * (k increasing and positive, nk >= 2).  Host only, FP64. */
+int amber_sigma2_tophat(const double *k, const double *Delta2, int nk, double R, double *out);
+
 /* ---- Analysis of z_re fields (Sec. 2.3) -------------------------------- */
 
 /* Normalised redshift field (Eq. deltaz): d_out[x] = ((1 + z[x]) - (1 + zbar))

@@ -31,6 +31,7 @@ EXPORTED = [
     "amber_profile_read", "amber_sort_passes", "amber_test_wait_timeout", "amber_source_field",
     "amber_solve_ex", "amber_assign_zre_ranked", "amber_batch_create", "amber_batch_launch", "amber_batch_destroy",
     "amber_delta_z", "amber_epsilon_z_pdf", "amber_power_bins", "amber_power_spectrum",
+    "amber_lpt_displacement", "amber_mesh_density", "amber_esf_fcoll", "amber_sigma2_tophat",
     "amber_rank_noalloc",
 ]
 
@@ -99,6 +100,10 @@ def _load():
         "amber_epsilon_z_pdf": (i32, [vp, vp, vp, i64, dbl, dbl, i32, vp, vp, vp]),
         "amber_power_bins": (i32, [i32, C.POINTER(i32)]),
         "amber_power_spectrum": (i32, [vp, vp, vp, i32, dbl, vp, vp, vp, vp, vp, vp]),
+        "amber_lpt_displacement": (i32, [vp, vp, i32, dbl, dbl, dbl, vp, vp, vp, vp]),
+        "amber_mesh_density": (i32, [vp, vp, vp, vp, vp, i32, dbl, i32, i32, vp, vp]),
+        "amber_esf_fcoll": (i32, [vp, vp, i32, dbl, dbl, i32, dbl, dbl, vp, vp]),
+        "amber_sigma2_tophat": (i32, [C.POINTER(dbl), C.POINTER(dbl), i32, dbl, C.POINTER(dbl)]),
         "amber_rank_noalloc": (i32, [vp, i64, vp, vp, vp]),
         "amber_test_wait_timeout": (i32, [vp, C.c_uint, vp]),
     }
@@ -130,6 +135,17 @@ def history(z_mid: float, dz: float, Az: float, x_points=(0.05, 0.5, 0.95), z_lo
     h.z_lo, h.z_hi, h.n_table = z_lo, z_hi, n_table
     h.weighting, h.omega_m = weighting, omega_m
     return h
+
+
+def sigma2_tophat(k, Delta2, R: float) -> float:
+    """Eq. variance by the trapezoid rule in ln k (host)."""
+    import numpy as np
+    k = np.ascontiguousarray(k, dtype=np.float64)
+    d = np.ascontiguousarray(Delta2, dtype=np.float64)
+    out = C.c_double()
+    _check(lib.amber_sigma2_tophat(k.ctypes.data_as(C.POINTER(C.c_double)), d.ctypes.data_as(C.POINTER(C.c_double)),
+                                   len(k), R, C.byref(out)), "amber_sigma2_tophat")
+    return out.value
 
 
 def power_bins(n: int) -> int:
@@ -329,6 +345,38 @@ class Context:
 
     def test_wait_timeout(self, spin_limit: int, stream=None):
         _check(lib.amber_test_wait_timeout(self._h, spin_limit, _stream(stream)), "amber_test_wait_timeout")
+
+    # --- source-field pipeline (Sec. 3.2, 3.2.1, 3.3) -------------------------
+    def lpt_displacement(self, delta_lin, box: float, D1: float, D2: float, stream=None):
+        """(psi_x, psi_y, psi_z) of the second-order displacement (Eq. xlpt), box units."""
+        import torch
+        n = delta_lin.shape[0]
+        psi = tuple(torch.empty_like(delta_lin) for _ in range(3))
+        _check(lib.amber_lpt_displacement(self._h, _ptr(delta_lin), n, box, D1, D2, _ptr(psi[0]), _ptr(psi[1]),
+                                          _ptr(psi[2]), _stream(stream)), "amber_lpt_displacement")
+        return psi
+
+    def mesh_density(self, psi, box: float, order: int = 3, interlace: bool = True, mass=None, out=None,
+                     stream=None):
+        """rho / <rho> from displaced lattice particles (Sec. 3.2.1, Eqs. interlace, Wofk)."""
+        import torch
+        n = psi[0].shape[0]
+        if out is None:
+            out = torch.empty_like(psi[0])
+        _check(lib.amber_mesh_density(self._h, _ptr(psi[0]), _ptr(psi[1]), _ptr(psi[2]), _ptr(mass), n, box, order,
+                                      1 if interlace else 0, _ptr(out), _stream(stream)), "amber_mesh_density")
+        return out
+
+    def esf_fcoll(self, delta_lin, box: float, R: float, delta_c: float, dsigma2: float, filter: str = "sharpk",
+                  out=None, stream=None):
+        """Collapsed fraction of the filtered linear field (Eq. fcoll)."""
+        import torch
+        n = delta_lin.shape[0]
+        if out is None:
+            out = torch.empty_like(delta_lin)
+        _check(lib.amber_esf_fcoll(self._h, _ptr(delta_lin), n, box, R, 0 if filter == "sharpk" else 1, delta_c,
+                                   dsigma2, _ptr(out), _stream(stream)), "amber_esf_fcoll")
+        return out
 
     # --- analysis of z_re fields (Sec. 2.3) ----------------------------------
     def delta_z(self, z, out=None, stream=None):

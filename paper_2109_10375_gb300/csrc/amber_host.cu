@@ -13,6 +13,7 @@
 #include "sort.cuh"
 #include "source.cuh"
 #include "spectra.cuh"
+#include "lpt.cuh"
 
 namespace amber {
 // krange: if not null, the intensities' key range is folded into it (the
@@ -468,6 +469,88 @@ int amber_power_spectrum(amber_ctx* c, const float* d_a, const float* d_b_opt, i
     e = power_impl(Ha, Hb, n, box, reinterpret_cast<double*>(c->ws + p.off_pow), d_k, d_Paa, d_Pbb_opt, d_Pab_opt,
                    d_modes, c->num_sms, s);
   return cuda_status(e);
+}
+
+static LptWork lpt_work(amber_ctx* c, int n) {
+  const Plan& p = c->plan;
+  LptWork w{};
+  // three half spectra (4 + 16/n bytes per cell each): the transform buffer
+  // and the key and index ping-pong pairs (8 bytes per cell each); two fields
+  // in the mass pair
+  w.H0 = c->ws + p.off_spec;
+  w.H1 = c->sortw.keysA;
+  w.H2 = c->sortw.idxA;
+  w.F0 = c->sortw.massA;
+  w.F1 = c->sortw.massB;
+  w.acc = reinterpret_cast<double*>(c->ws + p.off_pow);
+  w.tw = c->ws + p.off_tw32 + p.tw32_off[ilog2i(n)];
+  w.status = c->status;
+  w.num_sms = c->num_sms;
+  return w;
+}
+
+static int lpt_args_ok(amber_ctx* c, int n, double box) {
+  if (!c) return AMBER_ERR_INVALID_ARG;
+  if (!is_pow2_in(n, 4, 1024) || !(box > 0.0) || !std::isfinite(box)) return AMBER_ERR_INVALID_ARG;
+  if (n > c->plan.n32) return AMBER_ERR_CAPACITY;
+  return AMBER_OK;
+}
+
+int amber_lpt_displacement(amber_ctx* c, const float* d_delta_lin, int n, double box, double D1, double D2,
+                           float* d_psi_x, float* d_psi_y, float* d_psi_z, void* stream) {
+  int st = lpt_args_ok(c, n, box);
+  if (st) return st;
+  if (!d_delta_lin || !d_psi_x || !d_psi_y || !d_psi_z || !std::isfinite(D1) || !std::isfinite(D2))
+    return AMBER_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(c->mu);
+  DeviceGuard g(c->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  c->last_stream = s;
+  return cuda_status(lpt_impl(lpt_work(c, n), n, box, D1, D2, d_delta_lin, d_psi_x, d_psi_y, d_psi_z, s));
+}
+
+int amber_mesh_density(amber_ctx* c, const float* d_psi_x, const float* d_psi_y, const float* d_psi_z,
+                       const float* d_mass_opt, int n, double box, int order, int interlace, float* d_rho,
+                       void* stream) {
+  int st = lpt_args_ok(c, n, box);
+  if (st) return st;
+  if (!d_psi_x || !d_psi_y || !d_psi_z || !d_rho || order < 1 || order > 3 || (interlace != 0 && interlace != 1))
+    return AMBER_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(c->mu);
+  DeviceGuard g(c->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  c->last_stream = s;
+  return cuda_status(mesh_impl(lpt_work(c, n), n, box, order, interlace == 1, d_psi_x, d_psi_y, d_psi_z, d_mass_opt,
+                               d_rho, s));
+}
+
+int amber_esf_fcoll(amber_ctx* c, const float* d_delta_lin, int n, double box, double R, int filter, double delta_c,
+                    double dsigma2, float* d_fcoll, void* stream) {
+  int st = lpt_args_ok(c, n, box);
+  if (st) return st;
+  if (!d_delta_lin || !d_fcoll || !(R > 0.0) || !std::isfinite(R) || (filter != 0 && filter != 1) ||
+      !std::isfinite(delta_c) || !(dsigma2 > 0.0) || !std::isfinite(dsigma2))
+    return AMBER_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(c->mu);
+  DeviceGuard g(c->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  c->last_stream = s;
+  return cuda_status(fcoll_impl(lpt_work(c, n), n, box, R, filter, delta_c, dsigma2, d_delta_lin, d_fcoll, s));
+}
+
+int amber_sigma2_tophat(const double* k, const double* Delta2, int nk, double R, double* out) {
+  if (!k || !Delta2 || !out || nk < 2 || !(R > 0.0)) return AMBER_ERR_INVALID_ARG;
+  double acc = 0.0, prev = 0.0;
+  for (int i = 0; i < nk; ++i) {
+    if (!(k[i] > 0.0) || (i && !(k[i] > k[i - 1]))) return AMBER_ERR_INVALID_ARG;
+    const double x = k[i] * R;
+    const double W = x < 1e-3 ? 1.0 - x * x / 10.0 : 3.0 * (std::sin(x) - x * std::cos(x)) / (x * x * x);
+    const double f = Delta2[i] * W * W;
+    if (i) acc += 0.5 * (f + prev) * std::log(k[i] / k[i - 1]);
+    prev = f;
+  }
+  *out = acc;
+  return AMBER_OK;
 }
 
 int amber_rank(amber_ctx* c, const float* d_J, int64_t ncells, uint32_t* d_order, void* stream) {

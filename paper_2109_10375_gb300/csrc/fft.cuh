@@ -506,4 +506,32 @@ cudaError_t forward_spectrum_n(const T* src, cpx<T>* H, const cpx<T>* tw, cudaSt
   return cudaGetLastError();
 }
 
+// Inverse transform only: out = unnormalised inverse DFT of the half spectrum
+// H (z and y passes in place, then the C2R x-pass into out); the caller folds
+// 1/n^3 into the spectrum.  A non-finite output latches AMBER_ERR_NONFINITE.
+template <typename T, int N>
+cudaError_t inverse_spectrum_n(cpx<T>* H, T* out, const cpx<T>* tw, unsigned int* status, cudaStream_t s) {
+  using C = FftCfg<N>;
+  const int RS = N / 2 + 2;
+  const int ncol = N / 2 + 1;
+  const int64_t nrows = (int64_t)N * N;
+  const size_t xs = XSmem<T, N>::elems * sizeof(cpx<T>);
+  const size_t ss = StridedSmem<T, N>::elems * sizeof(cpx<T>);
+  static std::atomic<unsigned long long> attr_done{0};  // per instantiation and device
+  if (first_use_on_device(attr_done)) {
+    cudaFuncSetAttribute(k_fft_c2r_x<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xs);
+    cudaFuncSetAttribute(k_fft_strided<T, N, PASS_INV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss);
+  }
+  const int xgrid = (int)((nrows / 2 + C::XP - 1) / C::XP);
+  const int ntx = (ncol + C::SB - 1) / C::SB;
+  const int sgrid = N * ntx;
+  const T zero = (T)0;
+  k_fft_strided<T, N, PASS_INV><<<sgrid, strided_threads<N>(), ss, s>>>(H, (int64_t)N * RS, RS, ncol, ntx, tw,
+                                                                       zero, zero, zero);
+  k_fft_strided<T, N, PASS_INV><<<sgrid, strided_threads<N>(), ss, s>>>(H, RS, (int64_t)N * RS, ncol, ntx, tw,
+                                                                       zero, zero, zero);
+  k_fft_c2r_x<T, N><<<xgrid, xpass_threads<N>(), xs, s>>>(H, out, nrows, RS, tw, status, nullptr);
+  return cudaGetLastError();
+}
+
 }  // namespace amber

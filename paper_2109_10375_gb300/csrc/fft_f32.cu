@@ -39,4 +39,21 @@ cudaError_t forward_spectrum_f32(int n, const float* src, void* H, const void* t
   }
 }
 
+cudaError_t inverse_spectrum_f32(int n, void* H, float* out, const void* tw, unsigned int* status, cudaStream_t s) {
+  auto* h = reinterpret_cast<cpx<float>*>(H);
+  auto* w = reinterpret_cast<const cpx<float>*>(tw);
+  switch (n) {
+    case 4: return inverse_spectrum_n<float, 4>(h, out, w, status, s);
+    case 8: return inverse_spectrum_n<float, 8>(h, out, w, status, s);
+    case 16: return inverse_spectrum_n<float, 16>(h, out, w, status, s);
+    case 32: return inverse_spectrum_n<float, 32>(h, out, w, status, s);
+    case 64: return inverse_spectrum_n<float, 64>(h, out, w, status, s);
+    case 128: return inverse_spectrum_n<float, 128>(h, out, w, status, s);
+    case 256: return inverse_spectrum_n<float, 256>(h, out, w, status, s);
+    case 512: return inverse_spectrum_n<float, 512>(h, out, w, status, s);
+    case 1024: return inverse_spectrum_n<float, 1024>(h, out, w, status, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 }  // namespace amber

@@ -177,6 +177,13 @@ static int grid_for(int64_t n, int num_sms) {
   return (int)std::max<int64_t>(g, 1);
 }
 
+cudaError_t sum_f64_impl(const float* x, int64_t n, double* acc, int num_sms, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(acc, 0, sizeof(double), s);
+  if (e != cudaSuccess) return e;
+  k_sum_f64<<<grid_for(n, num_sms), 256, 0, s>>>(x, n, acc);
+  return cudaGetLastError();
+}
+
 cudaError_t delta_z_impl(const float* z, int64_t n, float* out, double* acc, double* zbar_out, int num_sms,
                          cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(acc, 0, sizeof(double), s);

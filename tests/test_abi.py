@@ -85,3 +85,14 @@ def test_create_without_gpu_reports_cuda_error(B):
         pytest.skip("a GPU is present")
     h = C.c_void_p()
     assert B.lib.amber_create(C.byref(h), 0, 4096) == B.AMBER_ERR_CUDA
+
+
+def test_sigma2_tophat_host_matches_oracle():
+    # Eq. variance on a tabulated power law (host FP64, no GPU)
+    import numpy as np
+    from oracle import amber_oracle as O
+    from paper_2109_10375_gb300 import binding as B
+    k = np.geomspace(1e-3, 1e3, 4001)
+    D2 = 0.3 * (k / 1.0) ** 1.5 * np.exp(-k / 50.0)
+    for R in (0.2, 0.5, 2.0):
+        assert abs(B.sigma2_tophat(k, D2, R) / O.sigma2_tophat(k, D2, R) - 1.0) < 1e-9
