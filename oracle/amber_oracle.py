@@ -35,6 +35,10 @@ Steps and the passages they follow
   displacements from spectral potentials, NGP/CIC/TSC assignment by plain
   loops over particles, the interlaced and deconvolved mesh, and the ESF
   collapsed fraction of a filtered linear field.
+* Tomographic matching (Sec. 3.4.2 mentions it without detail): one
+  correlated field per redshift interval, cells ionized in earlier intervals
+  ranked first, each still-neutral cell keeping the redshift the interval's
+  matching gives it when that redshift lies inside the interval.
 * Analysis (Sec. 2.3, Eqs. epsz, deltaz, Pk, Dk, bias, rcc): the normalised
   and fractional-difference redshift fields, and spherical-shell auto and
   cross power spectra with the bias and cross-correlation built from them
@@ -620,6 +624,39 @@ def sigma2_tophat(k, Delta2, R: float):
     f = np.asarray(Delta2, dtype=np.float64) * W * W
     lk = np.log(k)
     return float(np.sum(0.5 * (f[1:] + f[:-1]) * np.diff(lk)))
+
+
+# ---------------------------------------------------------------------------
+# Tomographic abundance matching (Sec. 3.4.2: "done tomographically using
+# multiple redshift intervals"; the paper gives no further detail)
+# ---------------------------------------------------------------------------
+
+def assign_zre_tomographic(J_list, z_bounds, mass, table: HistoryTable):
+    """z_re in cell order from one correlated field per redshift interval.
+
+    Intervals k = 0..K-1 run from high to low redshift, interval k covering
+    [z_bounds[k+1], z_bounds[k]).  In interval k the cells ionized in earlier
+    intervals rank first (they hold the earliest share of the ionized mass),
+    the rest follow by descending J_k (ties by cell index); abundance matching
+    over that order gives each still-neutral cell a redshift, which it keeps
+    if it falls inside the interval (always, in the last interval) and
+    otherwise carries over to the next interval.  With the same field in
+    every interval this is assign_zre of that field's ranking (up to the
+    rounding of summing the ionized prefix in another order)."""
+    K = len(J_list)
+    if len(z_bounds) != K + 1:
+        raise ValueError("need K+1 interval bounds")
+    m = np.asarray(mass, dtype=np.float64).reshape(-1)
+    z_re = np.full(m.shape[0], np.nan)
+    for k, J in enumerate(J_list):
+        Jk = np.asarray(J, dtype=np.float64).reshape(-1)
+        done = ~np.isnan(z_re)
+        key = np.where(done, np.inf, Jk)
+        order = np.argsort(-key, kind="stable")
+        z_tmp = assign_zre(order, m, table)
+        take = ~done & ((z_tmp >= z_bounds[k + 1]) | (k == K - 1))
+        z_re[take] = z_tmp[take]
+    return z_re
 
 
 def solve(S, mass, box: float, l_mfp: float, z_mid: float, dz: float, Az: float,

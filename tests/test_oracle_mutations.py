@@ -44,7 +44,26 @@ PINS = [
     lambda: [pins.test_interlace_realigns_and_deconvolves_a_plane_wave(p) for p in (0, 2, 3)],
     lambda: pins.test_filters_on_plane_waves(),
     lambda: pins.test_fcoll_closed_forms(),
+    lambda: pins.test_tomographic_with_one_field_is_the_plain_rule(),
+    lambda: pins.test_tomographic_follows_the_history_within_one_cell(),
+    lambda: pins.test_tomographic_two_interval_brute_force(),
 ]
+
+_tomo = o.assign_zre_tomographic
+
+
+def _tomo_ionized_last(J_list, z_bounds, mass, table):
+    # earlier-ionized cells ranked last instead of first
+    m = np.asarray(mass, dtype=np.float64).reshape(-1)
+    z_re = np.full(m.shape[0], np.nan)
+    K = len(J_list)
+    for k, J in enumerate(J_list):
+        done = ~np.isnan(z_re)
+        order = np.argsort(-np.where(done, -np.inf, np.asarray(J, dtype=np.float64).reshape(-1)), kind="stable")
+        z_tmp = o.assign_zre(order, m, table)
+        take = ~done & ((z_tmp >= z_bounds[k + 1]) | (k == K - 1))
+        z_re[take] = z_tmp[take]
+    return z_re
 
 _weights = o.assignment_weights_1d
 
@@ -130,6 +149,7 @@ MUTATIONS = {
     "tsc_weights_mirrored": ("assignment_weights_1d", _tsc_mirrored),
     "interlace_twiddle_sign": ("interlace_deconvolve", _interlace_wrong_twiddle),
     "lpt_drops_second_order": ("lpt_displacement", _lpt_first_order_only),
+    "tomographic_ionized_ranked_last": ("assign_zre_tomographic", _tomo_ionized_last),
 }
 
 

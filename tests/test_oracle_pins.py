@@ -654,3 +654,63 @@ def test_sigma2_tophat_small_radius_limit():
     k = np.geomspace(0.1, 10.0, 20001)
     s2 = o.sigma2_tophat(k, np.ones_like(k), 1e-4)
     assert abs(s2 / math.log(100.0) - 1.0) < 1e-6
+
+
+# ---------------------------------------------------------------------------
+# Tomographic abundance matching
+# ---------------------------------------------------------------------------
+
+def test_tomographic_with_one_field_is_the_plain_rule():
+    g = np.random.default_rng(31)
+    C = 5000
+    mass = g.uniform(0.01, 3.0, C)
+    J = g.normal(size=C)
+    t = o.history_table(8.0, 4.0, 3.0, n_table=400)
+    plain = o.assign_zre(o.rank(J), mass, t)
+    for bounds in ([20.0, 5.0], [20.0, 9.0, 7.5, 5.0], [20.0, 12.0, 8.0, 7.9, 6.0, 5.0]):
+        z = o.assign_zre_tomographic([J] * (len(bounds) - 1), bounds, mass, t)
+        # the ionized prefix is summed in cell order rather than rank order
+        np.testing.assert_allclose(z, plain, rtol=0, atol=1e-12)
+
+
+def test_tomographic_follows_the_history_within_one_cell():
+    # fields that decorrelate from interval to interval: at every table
+    # redshift the ionized mass fraction still matches x(z) to one cell
+    g = np.random.default_rng(32)
+    C = 20000
+    mass = g.uniform(0.01, 3.0, C)
+    base = g.normal(size=C)
+    fields = [base + s * g.normal(size=C) for s in (0.0, 0.7, 1.5)]
+    t = o.history_table(7.5, 4.0, 3.0, n_table=300)
+    z = o.assign_zre_tomographic(fields, [20.0, 8.5, 7.0, 5.0], mass, t)
+    assert not np.any(np.isnan(z))
+    _fraction_invariant(z, mass, t)
+    # every cell's redshift lies in the interval that assigned it, and the
+    # first interval follows the first field's ranking alone
+    early = z >= 8.5
+    first = o.assign_zre(o.rank(fields[0]), mass, t)
+    np.testing.assert_array_equal(z[early], first[early])
+
+
+def test_tomographic_two_interval_brute_force():
+    # eight cells, two intervals, the second field reversing the ranking: the
+    # cells left neutral after the first interval are matched in reversed
+    # order after the ionized ones (explicit loops)
+    mass = np.array([1.0, 2.0, 0.5, 1.5, 1.0, 3.0, 0.25, 0.75])
+    J1 = np.arange(8, 0, -1, dtype=np.float64)  # cell 0 brightest
+    J2 = -J1
+    t = o.history_table(8.0, 4.0, 3.0, n_table=200)
+    z = o.assign_zre_tomographic([J1, J2], [20.0, 8.0, 5.0], mass, t)
+    T = mass.sum()
+    z1 = [None] * 8
+    acc = 0.0
+    for c in range(8):  # first interval: ranking 0, 1, ..., 7
+        acc += mass[c]
+        z1[c] = float(o.assign_from_fraction(np.array([acc / T]), t)[0])
+    ref = [zz if zz >= 8.0 else None for zz in z1]
+    acc = sum(mass[c] for c in range(8) if ref[c] is not None)
+    for c in range(7, -1, -1):  # second interval: the neutral cells by J2, cell 7 first
+        if ref[c] is None:
+            acc += mass[c]
+            ref[c] = float(o.assign_from_fraction(np.array([acc / T]), t)[0])
+    np.testing.assert_allclose(z, ref, rtol=0, atol=1e-12)
