@@ -368,6 +368,28 @@ def run_amber(args):
                                 "scan_assign_ms": pw["scan_assign"][0] / reps,
                                 "thresholds_ms": pw["thresholds"][0] / reps}
 
+    # --- tomographic matching: three redshift intervals, each with its own
+    # source field (here the workload's source and two drifted copies)
+    tomographic = {}
+    if rank == 0 and ws == 1 and not args.no_extras:
+        S1 = (0.7 * S + 0.3 * torch.roll(S, 7, dims=0)).contiguous()
+        S2 = (0.4 * S + 0.6 * torch.roll(S, 7, dims=0)).contiguous()
+        zt = torch.empty_like(S)
+        bounds = [20.0, 8.6, 7.2, 5.0]
+        ctx.solve_tomographic([S, S1, S2], bounds, m, box, L_MFP, h, out=zt)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        ctx.solve_tomographic([S, S1, S2], bounds, m, box, L_MFP, h, out=zt)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        st = ctx.sync_status()
+        if st != 0:
+            raise RuntimeError(f"device status (tomographic): {B.status_string(st)}")
+        tms = e0.elapsed_time(e1)
+        tomographic = {"intervals": len(bounds) - 1, "bounds": bounds, "ms": tms, "cells_per_s": C / (tms / 1e3)}
+        del S1, S2, zt
+        torch.cuda.empty_cache()
+
     # --- analysis of the z_re fields (Sec. 2.3) at the workload's size: the
     # plain and growth-rescaled fields' normalised forms, their auto and cross
     # shell spectra, and the PDF of their fractional difference
@@ -549,6 +571,8 @@ def run_amber(args):
                 "cpu_baseline": cpu}
         if weightings:
             line["weightings"] = weightings
+        if tomographic:
+            line["tomographic"] = tomographic
         if analysis:
             line["analysis"] = analysis
         if source_pipeline:

@@ -245,6 +245,23 @@ int amber_profile_read(amber_ctx *ctx, int kind, const char **name, double *tota
  * so an intensity field spanning few octaves needs 3 passes, at most 4. */
 int amber_sort_passes(amber_ctx *ctx, int *out_passes);
 
+/* Tomographic abundance matching (Sec. 3.4.2 names it, "using multiple
+ * redshift intervals", without further detail).  Interval k = 0..nint-1
+ * covers [z_bounds[k+1], z_bounds[k]) (host array, strictly decreasing, nint
+ * in [1, 64]) and has its own source field d_src_list[k] (n^3 floats each,
+ * e.g. the sources at the interval's redshift).  For each interval, from high
+ * to low redshift: J_k = the radiation field of d_src_list[k]; cells that
+ * already have a redshift rank first (intensity +inf: they hold the earliest
+ * share of the ionized mass), the rest by descending J_k; abundance matching
+ * over that ranking (the plain mass weighting of p->hist) gives each
+ * still-neutral cell a redshift, which it keeps if it is at or above
+ * z_bounds[k+1] (always, in the last interval).  With the same source in
+ * every interval the result equals amber_solve's exactly (the prefix sums
+ * are exact, so their order does not matter).  Costs one radiation field,
+ * one ranking and one matching per interval.  d_zre: n^3 floats out. */
+int amber_solve_tomographic(amber_ctx *ctx, const float *const *d_src_list, int nint, const double *z_bounds,
+                            const float *d_mass, const amber_params_t *p, float *d_zre, void *stream);
+
 /* ---- Source-field pipeline (Sec. 3.2, 3.2.1, 3.3) ----------------------- */
 
 /* Second-order Lagrangian displacement (Sec. 3.2, Eq. xlpt) of one particle

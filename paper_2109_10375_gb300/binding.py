@@ -32,6 +32,7 @@ EXPORTED = [
     "amber_solve_ex", "amber_assign_zre_ranked", "amber_batch_create", "amber_batch_launch", "amber_batch_destroy",
     "amber_delta_z", "amber_epsilon_z_pdf", "amber_power_bins", "amber_power_spectrum",
     "amber_lpt_displacement", "amber_mesh_density", "amber_esf_fcoll", "amber_sigma2_tophat",
+    "amber_solve_tomographic",
     "amber_rank_noalloc",
 ]
 
@@ -104,6 +105,8 @@ def _load():
         "amber_mesh_density": (i32, [vp, vp, vp, vp, vp, i32, dbl, i32, i32, vp, vp]),
         "amber_esf_fcoll": (i32, [vp, vp, i32, dbl, dbl, i32, dbl, dbl, vp, vp]),
         "amber_sigma2_tophat": (i32, [C.POINTER(dbl), C.POINTER(dbl), i32, dbl, C.POINTER(dbl)]),
+        "amber_solve_tomographic": (i32, [vp, C.POINTER(vp), i32, C.POINTER(dbl), vp, C.POINTER(amber_params_t), vp,
+                                          vp]),
         "amber_rank_noalloc": (i32, [vp, i64, vp, vp, vp]),
         "amber_test_wait_timeout": (i32, [vp, C.c_uint, vp]),
     }
@@ -345,6 +348,21 @@ class Context:
 
     def test_wait_timeout(self, spin_limit: int, stream=None):
         _check(lib.amber_test_wait_timeout(self._h, spin_limit, _stream(stream)), "amber_test_wait_timeout")
+
+    def solve_tomographic(self, sources, z_bounds, mass, box: float, l_mfp: float, h: amber_history_t, out=None,
+                          stream=None):
+        """z_re from one source field per redshift interval (intervals from z_bounds, decreasing)."""
+        import torch
+        S0 = sources[0]
+        n = S0.shape[0]
+        if out is None:
+            out = torch.empty(S0.shape, dtype=torch.float32, device=S0.device)
+        srcs = (C.c_void_p * len(sources))(*[_ptr(x) for x in sources])
+        zb = (C.c_double * len(z_bounds))(*z_bounds)
+        p = params(n, box, l_mfp, h)
+        _check(lib.amber_solve_tomographic(self._h, srcs, len(sources), zb, _ptr(mass), C.byref(p), _ptr(out),
+                                           _stream(stream)), "amber_solve_tomographic")
+        return out
 
     # --- source-field pipeline (Sec. 3.2, 3.2.1, 3.3) -------------------------
     def lpt_displacement(self, delta_lin, box: float, D1: float, D2: float, stream=None):

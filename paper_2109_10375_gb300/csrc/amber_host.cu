@@ -639,6 +639,43 @@ int amber_solve(amber_ctx* c, const float* d_src, const float* d_mass, const amb
   return cuda_status(solve_f32_enqueue(c, d_src, d_mass, p, hc, d_zre, d_J_opt, nullptr, nullptr, s));
 }
 
+int amber_solve_tomographic(amber_ctx* c, const float* const* d_src_list, int nint, const double* z_bounds,
+                            const float* d_mass, const amber_params_t* p, float* d_zre, void* stream) {
+  if (!d_src_list || !z_bounds || nint < 1 || nint > 64) return AMBER_ERR_INVALID_ARG;
+  for (int k = 0; k < nint; ++k)
+    if (!d_src_list[k]) return AMBER_ERR_INVALID_ARG;
+  for (int k = 0; k <= nint; ++k)
+    if (!std::isfinite(z_bounds[k]) || (k && !(z_bounds[k] < z_bounds[k - 1]))) return AMBER_ERR_INVALID_ARG;
+  HistoryCoeffs hc;
+  int st = solve_args(c, d_src_list[0], d_mass, p, d_zre, 32, c ? c->plan.n32 : 0, &hc);
+  if (st) return st;
+  std::lock_guard<std::mutex> lk(c->mu);
+  DeviceGuard g(c->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  c->last_stream = s;
+  const Plan& pl = c->plan;
+  const int n = p->n;
+  const int64_t C = (int64_t)n * n * n;
+  float* J = reinterpret_cast<float*>(c->sortw.keysB);
+  // the transform buffer is free once J is formed: it holds each interval's matching
+  float* ztmp = reinterpret_cast<float*>(c->ws + pl.off_spec);
+  unsigned long long* tile_mass = reinterpret_cast<unsigned long long*>(c->ws + pl.off_tilemass);
+  cudaError_t e = tomo_fill(d_zre, C, c->num_sms, s);
+  for (int k = 0; k < nint && e == cudaSuccess; ++k) {
+    e = radiation_field_f32(n, d_src_list[k], J, c->ws + pl.off_spec, c->ws + pl.off_tw32 + pl.tw32_off[ilog2i(n)],
+                            p->box, p->l_mfp, c->status, s, &c->prof, nullptr);
+    if (e == cudaSuccess && k > 0) e = tomo_mask(J, d_zre, C, c->num_sms, s);
+    if (e == cudaSuccess)
+      e = rank_impl<float>(c->sortw, J, C, nullptr, d_mass, nullptr, tile_mass, false, c->status, s, &c->prof,
+                           kSpinLimit);
+    if (e == cudaSuccess)
+      e = assign_impl(c->assw, c->sortw.idxA, c->sortw.massA, true, tile_mass, C, hc, ztmp, nullptr, c->status, s,
+                      &c->prof, kSpinLimit, c->sortw.idxB, c->sortw.massB, &c->sortw.ctrl->npasses);
+    if (e == cudaSuccess) e = tomo_merge(d_zre, ztmp, C, (float)z_bounds[k + 1], k == nint - 1, c->num_sms, s);
+  }
+  return cuda_status(e);
+}
+
 int amber_solve_ex(amber_ctx* c, const float* d_src, const float* d_mass, const amber_params_t* p, float* d_zre,
                    float* d_J_opt, uint32_t* d_order_out, float* d_mass_rank_out, void* stream) {
   HistoryCoeffs hc;

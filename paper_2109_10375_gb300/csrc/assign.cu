@@ -601,6 +601,44 @@ __global__ void __launch_bounds__(256) k_scatter_back(const uint32_t* __restrict
 }
 
 // ---------------------------------------------------------------------------
+// Tomographic matching helpers: z_re starts as NaN (neutral); before interval
+// k's ranking the cells already ionized get intensity +inf so they rank first;
+// after its matching a neutral cell takes the interval's redshift when it
+// lies at or above the interval's lower bound (always in the last interval).
+__global__ void __launch_bounds__(256) k_tomo_fill(float* __restrict__ z, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    z[i] = __int_as_float(0x7fc00000);  // quiet NaN
+}
+
+__global__ void __launch_bounds__(256) k_tomo_mask(float* __restrict__ J, const float* __restrict__ z, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    if (!isnan(z[i])) J[i] = __int_as_float(0x7f800000);  // +inf
+}
+
+__global__ void __launch_bounds__(256) k_tomo_merge(float* __restrict__ z, const float* __restrict__ ztmp, int64_t n,
+                                                    float z_low, bool last) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    if (isnan(z[i]) && (last || ztmp[i] >= z_low)) z[i] = ztmp[i];
+}
+
+static int elem_grid(int64_t n, int num_sms) {
+  return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)num_sms * 16));
+}
+
+cudaError_t tomo_fill(float* z, int64_t n, int num_sms, cudaStream_t s) {
+  k_tomo_fill<<<elem_grid(n, num_sms), 256, 0, s>>>(z, n);
+  return cudaGetLastError();
+}
+cudaError_t tomo_mask(float* J, const float* z, int64_t n, int num_sms, cudaStream_t s) {
+  k_tomo_mask<<<elem_grid(n, num_sms), 256, 0, s>>>(J, z, n);
+  return cudaGetLastError();
+}
+cudaError_t tomo_merge(float* z, const float* ztmp, int64_t n, float z_low, bool last, int num_sms, cudaStream_t s) {
+  k_tomo_merge<<<elem_grid(n, num_sms), 256, 0, s>>>(z, ztmp, n, z_low, last);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
 void bucket_plan(int64_t n, int* nbuckets, int* shift) {
   // buckets of 2^23 consecutive cells: 32 MB of z_re each, so the active
   // bucket stays in L2; at most 128 buckets for 2^30 cells

@@ -78,6 +78,13 @@ struct ScanArgs {
 
 void bucket_plan(int64_t n, int* nbuckets, int* shift);
 
+// Tomographic matching: fill z with NaN (neutral); give cells with a redshift
+// intensity +inf (rank first); take the interval's redshift for neutral cells
+// at or above z_low (all of them when last).
+cudaError_t tomo_fill(float* z, int64_t n, int num_sms, cudaStream_t s);
+cudaError_t tomo_mask(float* J, const float* z, int64_t n, int num_sms, cudaStream_t s);
+cudaError_t tomo_merge(float* z, const float* ztmp, int64_t n, float z_low, bool last, int num_sms, cudaStream_t s);
+
 // mass_in_rank_order: mass[n] belongs to rank n (sort payload) instead of to
 // cell n.  tile_mass: per-tile partial mass sums from the ranking (summed in
 // the thresholds kernel); null means one reduction pass over mass.
