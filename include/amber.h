@@ -245,8 +245,8 @@ int amber_profile_read(amber_ctx *ctx, int kind, const char **name, double *tota
  * so an intensity field spanning few octaves needs 3 passes, at most 4. */
 int amber_sort_passes(amber_ctx *ctx, int *out_passes);
 
-/* Tomographic abundance matching (Sec. 3.4.2 names it, "using multiple
- * redshift intervals", without further detail).  Interval k = 0..nint-1
+/* Tomographic abundance matching (Sec. 3.4.2 names matching over several
+ * redshift intervals as an option, without further detail).  Interval k = 0..nint-1
  * covers [z_bounds[k+1], z_bounds[k]) (host array, strictly decreasing, nint
  * in [1, 64]) and has its own source field d_src_list[k] (n^3 floats each,
  * e.g. the sources at the interval's redshift).  For each interval, from high

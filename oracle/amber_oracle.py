@@ -627,8 +627,8 @@ def sigma2_tophat(k, Delta2, R: float):
 
 
 # ---------------------------------------------------------------------------
-# Tomographic abundance matching (Sec. 3.4.2: "done tomographically using
-# multiple redshift intervals"; the paper gives no further detail)
+# Tomographic abundance matching (Sec. 3.4.2 names matching over several
+# redshift intervals as an option and gives no further detail)
 # ---------------------------------------------------------------------------
 
 def assign_zre_tomographic(J_list, z_bounds, mass, table: HistoryTable):
