@@ -254,7 +254,7 @@ constexpr int kLinCand = 256;  // table points a tile's cells may straddle (line
 // and each cell takes the largest point that ionizes it among
 // max{j : all ionized} and the straddling points above it.
 template <bool GATHER, bool WANT_F, bool LIN>
-__global__ void __launch_bounds__(kScanThreads, 4) k_scan_assign(const ScanArgs a) {
+__global__ void __launch_bounds__(kScanThreads, 2) k_scan_assign(const ScanArgs a) {
   constexpr int NT = kScanThreads, IT = kScanItems, TILE = kScanTile;
   __shared__ int s_jall, s_ncand;
   __shared__ int s_cand[LIN ? kLinCand : 1];
@@ -429,7 +429,7 @@ __global__ void __launch_bounds__(kScanThreads, 4) k_scan_assign(const ScanArgs 
   const double invT = WANT_F ? 1.0 / (double)*a.qtotal : 0.0;
   const float qinv = __int_as_float((127 - *a.qshift) << 23);  // 2^-s: fixed point -> mass units
   const unsigned long long qT = LIN ? *a.qtotal : 0ull;  // total in the prefix's fixed point (>= every M_n)
-  // head form (ranks in the first half) or tail form, for the whole tile:
+  // head form (ranks in the first half) or tail form, for the tile's box:
   // h = C_j + sa alpha_j u + sa beta_j v with (C, u, v, sa) = (x W_N, n, M_n, -1)
   // or ((x - 1) W_N, N - n, T - M_n, +1)
   const bool head = start + (uint32_t)cnt / 2u <= n / 2u;
@@ -484,10 +484,15 @@ __global__ void __launch_bounds__(kScanThreads, 4) k_scan_assign(const ScanArgs 
     if (p >= cnt) continue;
     Mn += mass_fix(mv[i], qs);
     if constexpr (LIN) {
+      // the cell's own form (a tile can straddle the middle rank; the tile's
+      // classification above carries a tolerance for either form)
       const uint32_t rank1 = start + (uint32_t)p + 1u;
-      const float uu = sa * (head ? (float)rank1 : (float)(n - rank1));
-      const float vv = sa * (head ? u64_to_float(Mn) * qinv : u64_to_float(qT - Mn) * qinv);
-      auto h = [&](int j) { return fmaf(a.linb[j], vv, fmaf(a.lina[j], uu, linC[j])); };
+      const bool chead = rank1 <= n / 2u;
+      const float cs = chead ? -1.0f : 1.0f;
+      const float* cC = chead ? a.linP : a.linQ;
+      const float uu = cs * (chead ? (float)rank1 : (float)(n - rank1));
+      const float vv = cs * (chead ? u64_to_float(Mn) * qinv : u64_to_float(qT - Mn) * qinv);
+      auto h = [&](int j) { return fmaf(a.linb[j], vv, fmaf(a.lina[j], uu, cC[j])); };
       int js = s_jall;
       const int nc = s_ncand;
       if (nc <= kLinCand) {
@@ -552,9 +557,10 @@ __global__ void __launch_bounds__(kScanThreads, 4) k_scan_assign(const ScanArgs 
 }
 
 // z_re[cell] = z, bucket after bucket: CTA (bucket b, tile group g) copies
-// bucket b's run of every tile in its group, 8 tiles per warp.  Each warp
-// first issues the loads of all its runs (lanes read a run coalesced), then
-// the stores, so the dependent load -> store chains of its tiles overlap.  A
+// bucket b's run of every tile in its group (one tile per warp at the
+// default group size).  A warp takes its runs in rounds of four 32-pair
+// chunks: all the round's loads (lanes read a run coalesced), then its
+// stores, so the dependent load -> store chains overlap.  A
 // bucket's cells span a bounded region of z_re, so the permuted writes of
 // the CTAs working on it stay close together.
 __global__ void __launch_bounds__(256) k_scatter_back(const uint32_t* __restrict__ bcell,
@@ -574,29 +580,37 @@ __global__ void __launch_bounds__(256) k_scatter_back(const uint32_t* __restrict
     s_l = row[b];
     e_l = row[b + 1];
   }
-  uint32_t c[TPW];
-  float zz[TPW];
+  // rounds of 4 x 32 pairs per run: the loads of all the warp's runs, then the stores
+  constexpr int G = 4;
+  int len = e_l - s_l;
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) len = max(len, __shfl_xor_sync(0xffffffffu, len, o));
+  int s_k[TPW], e_k[TPW];
 #pragma unroll
   for (int k = 0; k < TPW; ++k) {
-    const int s = __shfl_sync(0xffffffffu, s_l, k), e = __shfl_sync(0xffffffffu, e_l, k);
-    const int64_t base = (t0 + k) * kScanTile;
-    const int i = s + lane;
-    c[k] = 0xffffffffu;
-    if (i < e) {
-      c[k] = ld_hint(bcell + base + i, stream_pol);
-      zz[k] = ld_hint(bz + base + i, stream_pol);
-    }
+    s_k[k] = __shfl_sync(0xffffffffu, s_l, k);
+    e_k[k] = __shfl_sync(0xffffffffu, e_l, k);
   }
-#pragma unroll
-  for (int k = 0; k < TPW; ++k)
-    if (c[k] != 0xffffffffu) st_hint(zre + c[k], zz[k], keep_pol);
-  // runs longer than one warp
 #pragma unroll 1
-  for (int k = 0; k < TPW; ++k) {
-    const int s = __shfl_sync(0xffffffffu, s_l, k), e = __shfl_sync(0xffffffffu, e_l, k);
-    const int64_t base = (t0 + k) * kScanTile;
-    for (int i = s + 32 + lane; i < e; i += 32)
-      st_hint(zre + ld_hint(bcell + base + i, stream_pol), ld_hint(bz + base + i, stream_pol), keep_pol);
+  for (int j0 = 0; j0 < len; j0 += 32 * G) {
+    uint32_t c[TPW * G];
+    float zz[TPW * G];
+#pragma unroll
+    for (int k = 0; k < TPW; ++k) {
+#pragma unroll
+      for (int q = 0; q < G; ++q) {
+        const int i = s_k[k] + j0 + 32 * q + lane;
+        c[k * G + q] = 0xffffffffu;
+        if (i < e_k[k]) {
+          const int64_t at = (t0 + k) * kScanTile + i;
+          c[k * G + q] = ld_hint(bcell + at, stream_pol);
+          zz[k * G + q] = ld_hint(bz + at, stream_pol);
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < TPW * G; ++q)
+      if (c[q] != 0xffffffffu) st_hint(zre + c[q], zz[q], keep_pol);
   }
 }
 
@@ -699,7 +713,7 @@ cudaError_t assign_impl(const AssignWork& w, const uint32_t* order, const float*
   a.btab = w.btab;
   a.status = status;
   a.spin_limit = spin_limit;
-  a.ahead = (uint32_t)w.num_sms * 4;  // resident scan CTAs: 4 per SM
+  a.ahead = (uint32_t)w.num_sms * 2;  // resident scan CTAs: 2 per SM
   a.linP = w.lin;
   a.linQ = w.lin + kMaxTable;
   a.lina = w.lin + 2 * kMaxTable;

@@ -9,13 +9,13 @@
 
 namespace amber {
 
-constexpr int kScanThreads = 256;
+constexpr int kScanThreads = 512;
 constexpr int kScanItems = 16;
 constexpr int kScanTile = kScanThreads * kScanItems;
 constexpr int kMaxTable = 1 << 16;
 constexpr int kMaxBuckets = 1024;
 
-constexpr int kBackTilesPerCta = 64;  // scan tiles one scatter-back CTA covers
+constexpr int kBackTilesPerCta = 8;  // scan tiles one scatter-back CTA covers
 constexpr int kBucketShift = 23;  // 2^23 cells (32 MB of z_re) per bucket by default
 
 // ctrl: exact total mass (2 x u64) at 0, tile ticket (u32) at 16, scan
