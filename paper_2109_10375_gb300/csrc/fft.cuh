@@ -222,7 +222,8 @@ k_fft_strided(cpx<T>* __restrict__ H, int64_t elem_stride, int64_t outer_stride,
 // A_k = (Z_k + conj Z_{N-k})/2 and B_k = (Z_k - conj Z_{N-k})/(2i), k <= N/2.
 // ---------------------------------------------------------------------------
 template <typename T, int N>
-__global__ void __launch_bounds__(xpass_threads<N>())
+// FP32: three CTAs per SM (measured faster for the forward x pass only)
+__global__ void __launch_bounds__(xpass_threads<N>(), sizeof(T) == 4 ? 3 : 1)
 k_fft_r2c_x(const T* __restrict__ src, cpx<T>* __restrict__ H, int64_t nrows, int RS,
             const cpx<T>* __restrict__ tw) {
   using C = FftCfg<N>;

@@ -30,6 +30,7 @@
 // by flipping; -0.0 is folded into +0.0 and NaN latches AMBER_ERR_NONFINITE.
 #include <cstdlib>
 #include <cstring>
+#include <type_traits>
 
 #include "fixed128.cuh"
 #include "sort.cuh"
@@ -239,40 +240,47 @@ __global__ void __launch_bounds__(kSortThreads, AMBER_SORT_MINB) k_sort_pass(con
   K key[kItems];
   uint32_t rd[kItems];
   bool bad = false;
-#pragma unroll
-  for (int it = 0; it < kItems; ++it) {
-    const uint32_t g = wbase + 32 * it;
-    const bool ok = g < n;
-    if constexpr (FIRST) key[it] = ok ? K(enc_desc(reinterpret_cast<const SRC*>(a.J)[g], bad) - kmin) : K(0);
-    else key[it] = ok ? reinterpret_cast<const K*>(a.kin)[g] : K(0);
-  }
   uint32_t* wh = whist + warp * R;
   const unsigned lt = lanemask_lt();
+  // Full tiles (all but the last) take a copy of the ranking without the
+  // bounds guards and the ballot of in-range lanes.
+  auto rank_items = [&](auto full_tag) {
+    constexpr bool FULL = decltype(full_tag)::value;
 #pragma unroll
-  for (int it = 0; it < kItems; ++it) {
-    const bool ok = wbase + 32 * it < n;
-    const unsigned d = (unsigned)(key[it] >> shift) & (R - 1);
-    unsigned peers;
-    if constexpr (MATCH) {
-      // lanes holding the same digit (out-of-range lanes group apart)
-      peers = __match_any_sync(0xffffffffu, ok ? d : 0x10000u);
-    } else {
-      // the same set from one ballot per digit bit: keep the lanes whose bit
-      // agrees (bit - 1 is all ones exactly when the bit is clear)
-      peers = __ballot_sync(0xffffffffu, ok);
-#pragma unroll
-      for (int b = 0; b < RB; ++b) {
-        const unsigned bit = (d >> b) & 1u;
-        peers &= __ballot_sync(0xffffffffu, bit) ^ (bit - 1u);
-      }
+    for (int it = 0; it < kItems; ++it) {
+      const uint32_t g = wbase + 32 * it;
+      const bool ok = FULL || g < n;
+      if constexpr (FIRST) key[it] = ok ? K(enc_desc(reinterpret_cast<const SRC*>(a.J)[g], bad) - kmin) : K(0);
+      else key[it] = ok ? reinterpret_cast<const K*>(a.kin)[g] : K(0);
     }
-    uint32_t base = 0;
-    if (ok) base = wh[d];
-    __syncwarp();
-    if (ok && (peers & lt) == 0u) wh[d] = base + __popc(peers);
-    __syncwarp();
-    rd[it] = ok ? ((base + __popc(peers & lt)) | (d << 16)) : 0xffffffffu;
-  }
+#pragma unroll
+    for (int it = 0; it < kItems; ++it) {
+      const bool ok = FULL || wbase + 32 * it < n;
+      const unsigned d = (unsigned)(key[it] >> shift) & (R - 1);
+      unsigned peers;
+      if constexpr (MATCH) {
+        // lanes holding the same digit (out-of-range lanes group apart)
+        peers = __match_any_sync(0xffffffffu, ok ? d : 0x10000u);
+      } else {
+        // the same set from one ballot per digit bit: keep the lanes whose bit
+        // agrees (bit - 1 is all ones exactly when the bit is clear)
+        peers = FULL ? 0xffffffffu : __ballot_sync(0xffffffffu, ok);
+#pragma unroll
+        for (int b = 0; b < RB; ++b) {
+          const unsigned bit = (d >> b) & 1u;
+          peers &= __ballot_sync(0xffffffffu, bit) ^ (bit - 1u);
+        }
+      }
+      uint32_t base = 0;
+      if (ok) base = wh[d];
+      __syncwarp();
+      if (ok && (peers & lt) == 0u) wh[d] = base + __popc(peers);
+      __syncwarp();
+      rd[it] = ok ? ((base + __popc(peers & lt)) | (d << 16)) : 0xffffffffu;
+    }
+  };
+  if (start + (uint32_t)kTile <= n) rank_items(std::true_type{});
+  else rank_items(std::false_type{});
   __syncthreads();
 
   // ---- per digit (thread tid owns digits tid + 256 j): warp prefixes, the
