@@ -108,8 +108,21 @@ k_fft_strided(cpx<T>* __restrict__ H, int64_t elem_stride, int64_t outer_stride,
       const int n = j + r * (N / R0);
       v[q * R0 + r] = ok ? base[(int64_t)n * elem_stride + b] : mk<T>(0, 0);
     }
-    dft<R0, MODE == PASS_INV>(v + q * R0);
   }
+  if constexpr (MODE == PASS_CONV) {
+    // K(|k|)/n^3 of this tile's columns for |kz| = 0..N/2, into shared memory
+    // after the tile, while the loads are in flight
+    const int ky = signed_freq(outer, N);
+    T* Kt = reinterpret_cast<T*>(sm + L::elems);
+#pragma unroll 1
+    for (int i = tid; i < (N / 2 + 1) * SB; i += NT) {
+      const int kza = i / SB, kx = kx0 + (i - kza * SB);
+      Kt[i] = kernel_K<T>((T)(kx * kx + ky * ky + kza * kza), l_mfp, kf, norm);
+    }
+    if constexpr (R1 == 1) __syncthreads();
+  }
+#pragma unroll
+  for (int q = 0; q < QA; ++q) dft<R0, MODE == PASS_INV>(v + q * R0);
   if constexpr (R1 == 1) {
     // single stage (n <= 32): v already holds natural order n = r for j = 0
   } else {
@@ -159,18 +172,16 @@ k_fft_strided(cpx<T>* __restrict__ H, int64_t elem_stride, int64_t outer_stride,
     // ---- z-pass: multiply by K(|k|)/n^3 at kz = n, ky = outer, kx = kx0 + b
     constexpr int QO = (R1 > 1) ? QB : QA;
     constexpr int RO = (R1 > 1) ? R1 : R0;
-    const int ky = signed_freq(outer, N);
+    const T* Kt = reinterpret_cast<const T*>(sm + L::elems);
 #pragma unroll
     for (int q = 0; q < QO; ++q) {
       const int id = tid + q * NT;
       const int b = id % SB, j = id / SB;
-      const int kx = kx0 + b;
 #pragma unroll
       for (int r = 0; r < RO; ++r) {
         const int n = (R1 > 1) ? j + r * R0 : r;
-        const int kz = signed_freq(n, N);
-        const T k2 = (T)(kx * kx + ky * ky + kz * kz);
-        v[q * RO + r] = scale(v[q * RO + r], kernel_K<T>(k2, l_mfp, kf, norm));
+        const int kza = n <= N / 2 ? n : N - n;
+        v[q * RO + r] = scale(v[q * RO + r], Kt[kza * SB + b]);
       }
       // inverse stage A (radix RO) on the same elements: n = j + r N/RO
       dft<RO, true>(v + q * RO);
@@ -199,8 +210,14 @@ k_fft_strided(cpx<T>* __restrict__ H, int64_t elem_stride, int64_t outer_stride,
         }
         dft<R0, true>(v + q * R0);
         if (kx0 + b < ncol) {
+          // the store addresses are recomputed here: kept live from the
+          // loads, they would spill
+          cpx<T>* ob;
+          int64_t es;
+          asm volatile("mov.b64 %0, %1;" : "=l"(ob) : "l"(base));
+          asm volatile("mov.b64 %0, %1;" : "=l"(es) : "l"(elem_stride));
 #pragma unroll
-          for (int r = 0; r < R0; ++r) base[(int64_t)(j + r * R1) * elem_stride + b] = v[q * R0 + r];
+          for (int r = 0; r < R0; ++r) ob[(int64_t)(j + r * R1) * es + b] = v[q * R0 + r];
         }
       }
     } else {
@@ -444,13 +461,15 @@ cudaError_t radiation_field_n(const T* src, T* J, cpx<T>* H, const cpx<T>* tw, d
   const T norm = (T)(1.0 / ((double)N * N * N));
   const size_t xs = XSmem<T, N>::elems * sizeof(cpx<T>);
   const size_t ss = StridedSmem<T, N>::elems * sizeof(cpx<T>);
+  // the z pass adds its table of K over |kz| = 0..N/2 for the tile's columns
+  const size_t sc = ss + (size_t)(N / 2 + 1) * C::SB * sizeof(T);
   static std::atomic<unsigned long long> attr_done{0};  // per instantiation and device
   if (first_use_on_device(attr_done)) {
     cudaFuncSetAttribute(k_fft_r2c_x<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xs);
     cudaFuncSetAttribute(k_fft_c2r_x<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xs);
     cudaFuncSetAttribute(k_fft_strided<T, N, PASS_FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss);
     cudaFuncSetAttribute(k_fft_strided<T, N, PASS_INV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss);
-    cudaFuncSetAttribute(k_fft_strided<T, N, PASS_CONV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss);
+    cudaFuncSetAttribute(k_fft_strided<T, N, PASS_CONV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sc);
   }
   const int xgrid = (int)((nrows / 2 + C::XP - 1) / C::XP);
   const int ntx = (ncol + C::SB - 1) / C::SB;
@@ -466,7 +485,7 @@ cudaError_t radiation_field_n(const T* src, T* J, cpx<T>* H, const cpx<T>* tw, d
   prof_end(prof, PK_FFT_Y_FWD, s);
   // z-pass: lines (y, kx); element stride N*RS; outer (y) stride RS
   prof_begin(prof, PK_FFT_Z_CONV, s);
-  k_fft_strided<T, N, PASS_CONV><<<sgrid, strided_threads<N>(), ss, s>>>(H, (int64_t)N * RS, RS, ncol, ntx, tw,
+  k_fft_strided<T, N, PASS_CONV><<<sgrid, strided_threads<N>(), sc, s>>>(H, (int64_t)N * RS, RS, ncol, ntx, tw,
                                                                         kf, (T)l_mfp, norm);
   prof_end(prof, PK_FFT_Z_CONV, s);
   prof_begin(prof, PK_FFT_Y_INV, s);
