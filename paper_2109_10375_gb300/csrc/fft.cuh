@@ -71,6 +71,13 @@ template <> __device__ __forceinline__ double kernel_K<double>(double k2, double
   return atan(k * l) / k * norm;
 }
 
+// Number of SM ids: with CTAs per SM, the launch index distance of one resident wave
+__device__ __forceinline__ int sm_count() {
+  unsigned n;
+  asm("mov.u32 %0, %%nsmid;" : "=r"(n));
+  return (int)n;
+}
+
 __device__ __forceinline__ int signed_freq(int m, int n) { return m < n / 2 ? m : m - n; }
 
 // ---------------------------------------------------------------------------
@@ -251,6 +258,11 @@ k_fft_r2c_x(const T* __restrict__ src, cpx<T>* __restrict__ H, int64_t nrows, in
   cpx<T>* sm = reinterpret_cast<cpx<T>*>(smem_raw);
   const int tid = threadIdx.x;
   const int64_t row0 = (int64_t)blockIdx.x * 2 * XP;
+  if (tid == 0) {
+    // the rows of the CTA one resident wave ahead (three per SM) into L2
+    const int64_t r2 = ((int64_t)blockIdx.x + 3 * sm_count()) * 2 * XP;
+    if (r2 < nrows) prefetch_l2_bulk(src + r2 * N, (uint32_t)(min((int64_t)2 * XP, nrows - r2) * N * sizeof(T)));
+  }
 
   cpx<T> v[E];
 #pragma unroll
@@ -332,6 +344,11 @@ k_fft_c2r_x(const cpx<T>* __restrict__ H, T* __restrict__ J, int64_t nrows, int 
   cpx<T>* sm = reinterpret_cast<cpx<T>*>(smem_raw);
   const int tid = threadIdx.x;
   const int64_t row0 = (int64_t)blockIdx.x * 2 * XP;
+  if (tid == 0) {
+    // the rows of the CTA one resident wave ahead (two per SM) into L2
+    const int64_t r2 = ((int64_t)blockIdx.x + 2 * sm_count()) * 2 * XP;
+    if (r2 < nrows) prefetch_l2_bulk(H + r2 * RS, (uint32_t)(min((int64_t)2 * XP, nrows - r2) * RS * sizeof(cpx<T>)));
+  }
 
   // columns k < N/2 of both rows of each pair: E/2 per thread, all loads
   // issued before any shared-memory store
