@@ -477,71 +477,97 @@ __global__ void __launch_bounds__(kScanThreads, 2) k_scan_assign(const ScanArgs 
   // (order and masses were consumed above, so their shared arrays are free).
   uint32_t* scell = sord;
   float* sz = smass;
-  int cx = -1;
+  if (!LIN && cx_lo == cx_hi) {
+    // the whole tile between two thresholds (all but a few tiles): one
+    // interval, its threshold and slope held in registers
+    const int j = cx_lo - 1;
+    const bool mid = j >= 0 && j < M - 1;
+    const unsigned long long Xu = mid ? Xj(j) : 0ull;
+    const float Iu = mid ? Ij(j) : 0.0f;
+    const float zc = j < 0 ? a.z_lo : a.z_hi;
 #pragma unroll
-  for (int i = 0; i < IT; ++i) {
-    const int p = tid * IT + i;
-    if (p >= cnt) continue;
-    Mn += mass_fix(mv[i], qs);
-    if constexpr (LIN) {
-      // the cell's own form (a tile can straddle the middle rank; the tile's
-      // classification above carries a tolerance for either form)
-      const uint32_t rank1 = start + (uint32_t)p + 1u;
-      const bool chead = rank1 <= n / 2u;
-      const float cs = chead ? -1.0f : 1.0f;
-      const float* cC = chead ? a.linP : a.linQ;
-      const float uu = cs * (chead ? (float)rank1 : (float)(n - rank1));
-      const float vv = cs * (chead ? u64_to_float(Mn) * qinv : u64_to_float(qT - Mn) * qinv);
-      auto h = [&](int j) { return fmaf(a.linb[j], vv, fmaf(a.lina[j], uu, cC[j])); };
-      int js = s_jall;
-      const int nc = s_ncand;
-      if (nc <= kLinCand) {
-        for (int k = 0; k < nc; ++k) {
-          const int c = s_cand[k];
-          if (c > js && h(c) >= 0.0f) js = c;
-        }
-      } else {
-        for (int c = M - 1; c > js; --c)
-          if (h(c) >= 0.0f) { js = c; break; }
-      }
-      float z;
-      if (js < 0) z = a.z_lo;
-      else if (js == M - 1) z = a.z_hi;
-      else {
-        const float h0 = h(js), h1 = h(js + 1);
-        float t = h0 / (h0 - h1);
+    for (int i = 0; i < IT; ++i) {
+      const int p = tid * IT + i;
+      if (p >= cnt) continue;
+      Mn += mass_fix(mv[i], qs);
+      float z = zc;
+      if (mid) {
+        float t = u64_to_float(Xu - Mn) * Iu;
         t = fminf(fmaxf(t, 0.0f), 0.99999994f);
-        z = a.z_lo + ((float)js + t) * a.dzt;
+        z = a.z_lo + ((float)j + t) * a.dzt;
       }
       if (WANT_F) a.F[start + p] = (double)Mn * invT;
       const uint32_t q = soff[cell[i] >> a.bucket_shift] + slot[i];
       scell[q + (q >> 5)] = cell[i];
       sz[q + (q >> 5)] = z;
-      continue;
     }
-    if (cx < 0) {
-      int lo = cx_lo, hi = cx_hi;
-      while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (Xj(mid) >= Mn) lo = mid + 1; else hi = mid;
+  } else {
+    int cx = -1;
+#pragma unroll
+    for (int i = 0; i < IT; ++i) {
+      const int p = tid * IT + i;
+      if (p >= cnt) continue;
+      Mn += mass_fix(mv[i], qs);
+      if constexpr (LIN) {
+        // the cell's own form (a tile can straddle the middle rank; the tile's
+        // classification above carries a tolerance for either form)
+        const uint32_t rank1 = start + (uint32_t)p + 1u;
+        const bool chead = rank1 <= n / 2u;
+        const float cs = chead ? -1.0f : 1.0f;
+        const float* cC = chead ? a.linP : a.linQ;
+        const float uu = cs * (chead ? (float)rank1 : (float)(n - rank1));
+        const float vv = cs * (chead ? u64_to_float(Mn) * qinv : u64_to_float(qT - Mn) * qinv);
+        auto h = [&](int j) { return fmaf(a.linb[j], vv, fmaf(a.lina[j], uu, cC[j])); };
+        int js = s_jall;
+        const int nc = s_ncand;
+        if (nc <= kLinCand) {
+          for (int k = 0; k < nc; ++k) {
+            const int c = s_cand[k];
+            if (c > js && h(c) >= 0.0f) js = c;
+          }
+        } else {
+          for (int c = M - 1; c > js; --c)
+            if (h(c) >= 0.0f) { js = c; break; }
+        }
+        float z;
+        if (js < 0) z = a.z_lo;
+        else if (js == M - 1) z = a.z_hi;
+        else {
+          const float h0 = h(js), h1 = h(js + 1);
+          float t = h0 / (h0 - h1);
+          t = fminf(fmaxf(t, 0.0f), 0.99999994f);
+          z = a.z_lo + ((float)js + t) * a.dzt;
+        }
+        if (WANT_F) a.F[start + p] = (double)Mn * invT;
+        const uint32_t q = soff[cell[i] >> a.bucket_shift] + slot[i];
+        scell[q + (q >> 5)] = cell[i];
+        sz[q + (q >> 5)] = z;
+        continue;
       }
-      cx = lo;
-    } else {
-      while (cx > 0 && Xj(cx - 1) < Mn) --cx;
+      if (cx < 0) {
+        int lo = cx_lo, hi = cx_hi;
+        while (lo < hi) {
+          const int mid = (lo + hi) >> 1;
+          if (Xj(mid) >= Mn) lo = mid + 1; else hi = mid;
+        }
+        cx = lo;
+      } else {
+        while (cx > 0 && Xj(cx - 1) < Mn) --cx;
+      }
+      const int j = cx - 1;
+      float z;
+      if (j < 0) z = a.z_lo;
+      else if (j == M - 1) z = a.z_hi;
+      else {
+        float t = u64_to_float(Xj(j) - Mn) * Ij(j);
+        t = fminf(fmaxf(t, 0.0f), 0.99999994f);
+        z = a.z_lo + ((float)j + t) * a.dzt;
+      }
+      if (WANT_F) a.F[start + p] = (double)Mn * invT;
+      const uint32_t q = soff[cell[i] >> a.bucket_shift] + slot[i];
+      scell[q + (q >> 5)] = cell[i];
+      sz[q + (q >> 5)] = z;
     }
-    const int j = cx - 1;
-    float z;
-    if (j < 0) z = a.z_lo;
-    else if (j == M - 1) z = a.z_hi;
-    else {
-      float t = u64_to_float(Xj(j) - Mn) * Ij(j);
-      t = fminf(fmaxf(t, 0.0f), 0.99999994f);
-      z = a.z_lo + ((float)j + t) * a.dzt;
-    }
-    if (WANT_F) a.F[start + p] = (double)Mn * invT;
-    const uint32_t q = soff[cell[i] >> a.bucket_shift] + slot[i];
-    scell[q + (q >> 5)] = cell[i];
-    sz[q + (q >> 5)] = z;
   }
   __syncthreads();
   // the pairs are read back only after the whole scan: keep them out of L2
