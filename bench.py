@@ -248,7 +248,7 @@ def algorithmic_bytes(n: int, sort_passes: int) -> dict:
     return {
         "fft_r2c_x": 4 * C + H, "fft_y_fwd": 2 * H, "fft_z_conv": 2 * H, "fft_y_inv": 2 * H,
         "fft_c2r_x": H + 4 * C,
-        "sort_histogram": 8 * C,            # key range + digit histogram, 4 B/cell each
+        "sort_histogram": 4 * C,            # digit histograms (the key range comes with the inverse x pass)
         "sort_pass": sort,
         "mass_reduce": 4 * C, "thresholds": 0, "scan_assign": 16 * C, "scatter_back": 12 * C,
     }
@@ -474,32 +474,56 @@ def run_amber(args):
     ev_done = [torch.cuda.Event() for _ in range(2)]
     ev_out = [torch.cuda.Event() for _ in range(2)]
     e_steps = max(2, min(args.steps, 8))
-    barrier()
-    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    f0.record(stream)
-    s_in.wait_event(f0)
-    for i in range(e_steps):
-        b = i & 1
-        if i >= 2:
-            s_in.wait_event(ev_done[b])  # the solve of step i-2 has read S_d[b], m_d[b]
-        with torch.cuda.stream(s_in):
-            S_d[b].copy_(S_h, non_blocking=True)
-            m_d[b].copy_(m_h, non_blocking=True)
-            ev_in[b].record(s_in)
-        stream.wait_event(ev_in[b])
-        if i >= 2:
-            stream.wait_event(ev_out[b])  # z_d[b] of step i-2 is on the host
-        ctx.solve(S_d[b], m_d[b], box, L_MFP, h, out=z_d[b], stream=stream)
-        ev_done[b].record(stream)
-        s_out.wait_event(ev_done[b])
-        with torch.cuda.stream(s_out):
-            z_h[b].copy_(z_d[b], non_blocking=True)
-            ev_out[b].record(s_out)
-    stream.wait_event(ev_out[(e_steps - 1) & 1])
-    stream.wait_event(ev_out[(e_steps - 2) & 1])
-    f1.record(stream)
-    barrier()
-    e2e_ms = f0.elapsed_time(f1) / e_steps
+
+    def pipeline(steps, marks=None):
+        """steps double-buffered H2D -> solve -> D2H steps; returns ms per step"""
+        barrier()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        s_in.wait_event(f0)
+        for i in range(steps):
+            b = i & 1
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)] if marks is not None else None
+            if i >= 2:
+                s_in.wait_event(ev_done[b])  # the solve of step i-2 has read S_d[b], m_d[b]
+            with torch.cuda.stream(s_in):
+                if ev:
+                    ev[0].record(s_in)
+                S_d[b].copy_(S_h, non_blocking=True)
+                m_d[b].copy_(m_h, non_blocking=True)
+                if ev:
+                    ev[1].record(s_in)
+                ev_in[b].record(s_in)
+            stream.wait_event(ev_in[b])
+            if i >= 2:
+                stream.wait_event(ev_out[b])  # z_d[b] of step i-2 is on the host
+            if ev:
+                ev[2].record(stream)
+            ctx.solve(S_d[b], m_d[b], box, L_MFP, h, out=z_d[b], stream=stream)
+            if ev:
+                ev[3].record(stream)
+            ev_done[b].record(stream)
+            s_out.wait_event(ev_done[b])
+            with torch.cuda.stream(s_out):
+                if ev:
+                    ev[4].record(s_out)
+                z_h[b].copy_(z_d[b], non_blocking=True)
+                if ev:
+                    ev[5].record(s_out)
+                ev_out[b].record(s_out)
+            if marks is not None:
+                marks.append(ev)
+        stream.wait_event(ev_out[(steps - 1) & 1])
+        stream.wait_event(ev_out[(steps - 2) & 1])
+        f1.record(stream)
+        barrier()
+        return f0.elapsed_time(f1) / steps
+
+    pipeline(2)  # warm-up: first touch of the second buffer set
+    marks = []
+    e2e_ms = pipeline(e_steps, marks)
+    stage_ms = {k: sum(ev[i0].elapsed_time(ev[i1]) for ev in marks) / e_steps
+                for k, i0, i1 in (("h2d", 0, 1), ("solve", 2, 3), ("d2h", 4, 5))}
     e2e_ms = reduce_max(e2e_ms, dist, "cuda")
     # the copies alone, for context
     c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -557,7 +581,8 @@ def run_amber(args):
                 "e2e": {"value": whole_job_rate(C, ws, e2e_ms), "unit": "cells/s", "h2d_bytes_per_step": 8 * C,
                         "d2h_bytes_per_step": 4 * C, "ms_per_step": e2e_ms, "steps": e_steps,
                         "overlap": "double-buffered: H2D and D2H streams overlap the neighbouring steps' solves",
-                        "h2d_GBps_alone": h2d_gbps, "d2h_GBps_alone": d2h_gbps},
+                        "h2d_GBps_alone": h2d_gbps, "d2h_GBps_alone": d2h_gbps,
+                        "stage_ms_mean": stage_ms},
                 "gpu_launches": int(round(launches_per_step * args.steps)),
                 "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peaks["hbm_gbs"],
                              "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": _traffic(dom, n),
