@@ -254,11 +254,25 @@ def algorithmic_bytes(n: int, sort_passes: int) -> dict:
     }
 
 
-def _src_hash() -> str:
-    h = hashlib.sha256()
+# The translation unit that holds each kernel kind (all of them include the
+# shared headers, which every hash covers).
+_KERNEL_SOURCES = {"fft": "fft_f32.cu", "sort": "sort.cu", "scan_assign": "assign.cu", "scatter_back": "assign.cu",
+                   "thresholds": "assign.cu", "mass_reduce": "assign.cu"}
+
+
+def _src_hash(kernel: str = None, read=None) -> str:
+    """Hash of the sources a kernel kind is built from: every header plus its
+    translation unit (all sources when no kernel is named).  read(name) returns
+    a file's bytes (default: the working tree)."""
     d = os.path.join(ROOT, "paper_2109_10375_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
-        h.update(open(os.path.join(d, f), "rb").read())
+    read = read or (lambda f: open(os.path.join(d, f), "rb").read())
+    names = sorted(os.listdir(d))
+    if kernel is not None:
+        unit = _KERNEL_SOURCES.get(kernel.split("_")[0], _KERNEL_SOURCES.get(kernel))
+        names = [f for f in names if f.endswith(".cuh") or f == unit]
+    h = hashlib.sha256()
+    for f in names:
+        h.update(read(f))
     return h.hexdigest()[:16]
 
 
@@ -269,10 +283,8 @@ def _traffic(kernel: str, n: int):
         d = json.load(open(p))
     except Exception:
         return None
-    if d.get("src_hash") != _src_hash():
-        return None
     k = d.get("kernels", {}).get(kernel)
-    if not k:
+    if not k or k.get("src_hash") != _src_hash(kernel):
         return None
     return k["bytes_per_launch"] * (n ** 3) / k["cells"]
 

@@ -477,7 +477,42 @@ __global__ void __launch_bounds__(kScanThreads, 2) k_scan_assign(const ScanArgs 
   // (order and masses were consumed above, so their shared arrays are free).
   uint32_t* scell = sord;
   float* sz = smass;
-  if (!LIN && cx_lo == cx_hi) {
+  if (LIN && s_ncand == 0) {
+    // no table point above max{j : all ionized} can ionize any cell of the
+    // tile: every cell takes j* = jall, whose two margin rows are held in
+    // registers
+    const int js = s_jall;
+    const bool mid = js >= 0 && js < M - 1;
+    float la0 = 0.f, lb0 = 0.f, P0 = 0.f, Q0 = 0.f, la1 = 0.f, lb1 = 0.f, P1 = 0.f, Q1 = 0.f;
+    if (mid) {
+      la0 = a.lina[js], lb0 = a.linb[js], P0 = a.linP[js], Q0 = a.linQ[js];
+      la1 = a.lina[js + 1], lb1 = a.linb[js + 1], P1 = a.linP[js + 1], Q1 = a.linQ[js + 1];
+    }
+    const float zc = js < 0 ? a.z_lo : a.z_hi;
+#pragma unroll
+    for (int i = 0; i < IT; ++i) {
+      const int p = tid * IT + i;
+      if (p >= cnt) continue;
+      Mn += mass_fix(mv[i], qs);
+      float z = zc;
+      if (mid) {
+        const uint32_t rank1 = start + (uint32_t)p + 1u;
+        const bool chead = rank1 <= n / 2u;
+        const float cs = chead ? -1.0f : 1.0f;
+        const float uu = cs * (chead ? (float)rank1 : (float)(n - rank1));
+        const float vv = cs * (chead ? u64_to_float(Mn) * qinv : u64_to_float(qT - Mn) * qinv);
+        const float h0 = fmaf(lb0, vv, fmaf(la0, uu, chead ? P0 : Q0));
+        const float h1 = fmaf(lb1, vv, fmaf(la1, uu, chead ? P1 : Q1));
+        float t = h0 / (h0 - h1);
+        t = fminf(fmaxf(t, 0.0f), 0.99999994f);
+        z = a.z_lo + ((float)js + t) * a.dzt;
+      }
+      if (WANT_F) a.F[start + p] = (double)Mn * invT;
+      const uint32_t q = soff[cell[i] >> a.bucket_shift] + slot[i];
+      scell[q + (q >> 5)] = cell[i];
+      sz[q + (q >> 5)] = z;
+    }
+  } else if (!LIN && cx_lo == cx_hi) {
     // the whole tile between two thresholds (all but a few tiles): one
     // interval, its threshold and slope held in registers
     const int j = cx_lo - 1;

@@ -51,3 +51,22 @@ def test_reference_arm_prints_one_json_line():
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["unit"] == "cells/s" and d["value"] > 0
     assert d["cpu_baseline"]["kind"] == "oracle" and d["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def test_traffic_hash_follows_only_the_kernels_own_sources():
+    # roofline.traffic is dropped once the counted kernel's sources change: a
+    # change to the scan's translation unit leaves the sort's hash alone, a
+    # change to a shared header moves every hash
+    sys.path.insert(0, ROOT)
+    import bench
+    d = os.path.join(ROOT, "paper_2109_10375_gb300", "csrc")
+    plain = lambda f: open(os.path.join(d, f), "rb").read()
+    edit = lambda name: (lambda f: plain(f) + (b"//" if f == name else b""))
+    assert bench._src_hash("sort_pass", edit("assign.cu")) == bench._src_hash("sort_pass", plain)
+    assert bench._src_hash("scan_assign", edit("assign.cu")) != bench._src_hash("scan_assign", plain)
+    assert bench._src_hash("fft_z_conv", edit("sort.cu")) == bench._src_hash("fft_z_conv", plain)
+    for k in ("sort_pass", "scan_assign", "fft_r2c_x", "scatter_back"):
+        assert bench._src_hash(k, edit("common.cuh")) != bench._src_hash(k, plain)
+    t = json.load(open(os.path.join(ROOT, "profiles", "dram_traffic.json")))
+    for k, v in t["kernels"].items():
+        assert v["src_hash"] and v["bytes_per_launch"] > 0 and v["cells"] > 0, k
