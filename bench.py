@@ -21,6 +21,7 @@ from __future__ import annotations
 
 import argparse
 import hashlib
+import re
 import json
 import math
 import os
@@ -254,22 +255,30 @@ def algorithmic_bytes(n: int, sort_passes: int) -> dict:
     }
 
 
-# The translation unit that holds each kernel kind (all of them include the
-# shared headers, which every hash covers).
+# The translation unit that holds each kernel kind; its hash covers that unit
+# and every csrc/ header it includes, directly or not.
 _KERNEL_SOURCES = {"fft": "fft_f32.cu", "sort": "sort.cu", "scan_assign": "assign.cu", "scatter_back": "assign.cu",
                    "thresholds": "assign.cu", "mass_reduce": "assign.cu"}
 
 
 def _src_hash(kernel: str = None, read=None) -> str:
-    """Hash of the sources a kernel kind is built from: every header plus its
-    translation unit (all sources when no kernel is named).  read(name) returns
-    a file's bytes (default: the working tree)."""
+    """Hash of the sources a kernel kind is built from: its translation unit
+    and the csrc/ headers it includes (all sources when no kernel is named).
+    read(name) returns a file's bytes (default: the working tree)."""
     d = os.path.join(ROOT, "paper_2109_10375_gb300", "csrc")
     read = read or (lambda f: open(os.path.join(d, f), "rb").read())
     names = sorted(os.listdir(d))
     if kernel is not None:
         unit = _KERNEL_SOURCES.get(kernel.split("_")[0], _KERNEL_SOURCES.get(kernel))
-        names = [f for f in names if f.endswith(".cuh") or f == unit]
+        todo, seen = [unit], set()
+        while todo:
+            f = todo.pop()
+            if f in seen or f not in names:
+                continue
+            seen.add(f)
+            todo += re.findall(rb'#include\s+"([^"]+)"', read(f))
+            todo = [t.decode() if isinstance(t, bytes) else t for t in todo]
+        names = sorted(seen)
     h = hashlib.sha256()
     for f in names:
         h.update(read(f))
@@ -314,6 +323,13 @@ def run_amber(args):
     box = 1000.0 * n / 1024
     C = n ** 3
     S, m = synth.realisation(n, box, rank, device="cuda")
+    # pinned host buffers of the end-to-end measurement, taken while host
+    # memory is fresh (filled from S and m here, read back near the end)
+    S_h = torch.empty(S.shape, dtype=torch.float32, pin_memory=True)
+    m_h = torch.empty(S.shape, dtype=torch.float32, pin_memory=True)
+    z_h = [torch.empty(S.shape, dtype=torch.float32, pin_memory=True) for _ in range(2)]
+    S_h.copy_(S)
+    m_h.copy_(m)
     torch.cuda.synchronize()
     torch.cuda.empty_cache()
     h = B.history(*HIST)
@@ -473,11 +489,8 @@ def run_amber(args):
     # step copies its inputs in, solves and copies z_re out; two buffer sets
     # let one step's copies overlap the neighbouring steps' solves (H2D and
     # D2H on their own streams, ordered by events).
-    S_h = S.cpu().pin_memory()
-    m_h = m.cpu().pin_memory()
     del S, m
     torch.cuda.empty_cache()
-    z_h = [torch.empty(z.shape, dtype=torch.float32).pin_memory() for _ in range(2)]
     S_d = [torch.empty(z.shape, device="cuda") for _ in range(2)]
     m_d = [torch.empty(z.shape, device="cuda") for _ in range(2)]
     z_d = [z, torch.empty_like(z)]
@@ -485,7 +498,7 @@ def run_amber(args):
     ev_in = [torch.cuda.Event() for _ in range(2)]
     ev_done = [torch.cuda.Event() for _ in range(2)]
     ev_out = [torch.cuda.Event() for _ in range(2)]
-    e_steps = max(2, min(args.steps, 8))
+    e_steps = max(2, args.steps)  # the same K as the device-timed steps
 
     def pipeline(steps, marks=None):
         """steps double-buffered H2D -> solve -> D2H steps; returns ms per step"""
@@ -532,10 +545,15 @@ def run_amber(args):
         return f0.elapsed_time(f1) / steps
 
     pipeline(2)  # warm-up: first touch of the second buffer set
-    marks = []
-    e2e_ms = pipeline(e_steps, marks)
-    stage_ms = {k: sum(ev[i0].elapsed_time(ev[i1]) for ev in marks) / e_steps
-                for k, i0, i1 in (("h2d", 0, 1), ("solve", 2, 3), ("d2h", 4, 5))}
+    # three timed trials; the median one is reported (the host side of the
+    # copies is shared with the rest of the machine)
+    trials = []
+    for _ in range(3):
+        marks = []
+        t_ms = pipeline(e_steps, marks)
+        trials.append((t_ms, {k: sum(ev[i0].elapsed_time(ev[i1]) for ev in marks) / e_steps
+                              for k, i0, i1 in (("h2d", 0, 1), ("solve", 2, 3), ("d2h", 4, 5))}))
+    e2e_ms, stage_ms = sorted(trials, key=lambda t: t[0])[1]
     e2e_ms = reduce_max(e2e_ms, dist, "cuda")
     # the copies alone, for context
     c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -594,7 +612,8 @@ def run_amber(args):
                         "d2h_bytes_per_step": 4 * C, "ms_per_step": e2e_ms, "steps": e_steps,
                         "overlap": "double-buffered: H2D and D2H streams overlap the neighbouring steps' solves",
                         "h2d_GBps_alone": h2d_gbps, "d2h_GBps_alone": d2h_gbps,
-                        "stage_ms_mean": stage_ms},
+                        "stage_ms_mean": stage_ms, "trials_ms": [t[0] for t in trials],
+                        "reported": "median of 3 timed trials"},
                 "gpu_launches": int(round(launches_per_step * args.steps)),
                 "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peaks["hbm_gbs"],
                              "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": _traffic(dom, n),

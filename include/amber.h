@@ -251,8 +251,9 @@ int amber_sort_passes(amber_ctx *ctx, int *out_passes);
  * in [1, 64]) and has its own source field d_src_list[k] (n^3 floats each,
  * e.g. the sources at the interval's redshift).  For each interval, from high
  * to low redshift: J_k = the radiation field of d_src_list[k]; cells that
- * already have a redshift rank first (intensity +inf: they hold the earliest
- * share of the ionized mass), the rest by descending J_k; abundance matching
+ * already have a redshift rank first (they take the next float above the
+ * largest J_k, and among themselves cell order: they hold the earliest share
+ * of the ionized mass), the rest by descending J_k; abundance matching
  * over that ranking (the plain mass weighting of p->hist) gives each
  * still-neutral cell a redshift, which it keeps if it is at or above
  * z_bounds[k+1] (always, in the last interval).  With the same source in

@@ -662,11 +662,14 @@ int amber_solve_tomographic(amber_ctx* c, const float* const* d_src_list, int ni
   unsigned long long* tile_mass = reinterpret_cast<unsigned long long*>(c->ws + pl.off_tilemass);
   cudaError_t e = tomo_fill(d_zre, C, c->num_sms, s);
   for (int k = 0; k < nint && e == cudaSuccess; ++k) {
-    e = radiation_field_f32(n, d_src_list[k], J, c->ws + pl.off_spec, c->ws + pl.off_tw32 + pl.tw32_off[ilog2i(n)],
-                            p->box, p->l_mfp, c->status, s, &c->prof, nullptr);
-    if (e == cudaSuccess && k > 0) e = tomo_mask(J, d_zre, C, c->num_sms, s);
+    // the inverse x pass folds this interval's key range into the sort control
+    e = sort_ctrl_reset(c->sortw.ctrl, s);
     if (e == cudaSuccess)
-      e = rank_impl<float>(c->sortw, J, C, nullptr, d_mass, nullptr, tile_mass, false, c->status, s, &c->prof,
+      e = radiation_field_f32(n, d_src_list[k], J, c->ws + pl.off_spec, c->ws + pl.off_tw32 + pl.tw32_off[ilog2i(n)],
+                              p->box, p->l_mfp, c->status, s, &c->prof, c->sortw.ctrl);
+    if (e == cudaSuccess && k > 0) e = tomo_mask(J, d_zre, C, c->sortw.ctrl, c->num_sms, s);
+    if (e == cudaSuccess)
+      e = rank_impl<float>(c->sortw, J, C, nullptr, d_mass, nullptr, tile_mass, true, c->status, s, &c->prof,
                            kSpinLimit);
     if (e == cudaSuccess)
       e = assign_impl(c->assw, c->sortw.idxA, c->sortw.massA, true, tile_mass, C, hc, ztmp, nullptr, c->status, s,

@@ -685,9 +685,22 @@ __global__ void __launch_bounds__(256) k_tomo_fill(float* __restrict__ z, int64_
     z[i] = __int_as_float(0x7fc00000);  // quiet NaN
 }
 
-__global__ void __launch_bounds__(256) k_tomo_mask(float* __restrict__ J, const float* __restrict__ z, int64_t n) {
+// Cells ionized in an earlier interval take the next float above the largest
+// intensity of this interval (its key is one below the minimum key): they
+// rank first, in cell order, exactly as +inf would, while the key range -- and
+// so the number of digit passes -- grows by one key instead of to the top of
+// the float range.
+__global__ void __launch_bounds__(256) k_tomo_mask(float* __restrict__ J, const float* __restrict__ z, int64_t n,
+                                                   const SortCtrl* __restrict__ ctrl) {
+  const uint32_t k = (uint32_t)ctrl->kmin - 1u;  // kmin > 0 for finite intensities
+  const uint32_t u = ~k;                          // undo the descending flip
+  const float first = __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    if (!isnan(z[i])) J[i] = __int_as_float(0x7f800000);  // +inf
+    if (!isnan(z[i])) J[i] = first;
+}
+
+__global__ void k_tomo_widen(SortCtrl* ctrl) {
+  if (ctrl->kmin > 0) ctrl->kmin -= 1;
 }
 
 __global__ void __launch_bounds__(256) k_tomo_merge(float* __restrict__ z, const float* __restrict__ ztmp, int64_t n,
@@ -704,8 +717,9 @@ cudaError_t tomo_fill(float* z, int64_t n, int num_sms, cudaStream_t s) {
   k_tomo_fill<<<elem_grid(n, num_sms), 256, 0, s>>>(z, n);
   return cudaGetLastError();
 }
-cudaError_t tomo_mask(float* J, const float* z, int64_t n, int num_sms, cudaStream_t s) {
-  k_tomo_mask<<<elem_grid(n, num_sms), 256, 0, s>>>(J, z, n);
+cudaError_t tomo_mask(float* J, const float* z, int64_t n, SortCtrl* ctrl, int num_sms, cudaStream_t s) {
+  k_tomo_mask<<<elem_grid(n, num_sms), 256, 0, s>>>(J, z, n, ctrl);
+  k_tomo_widen<<<1, 1, 0, s>>>(ctrl);
   return cudaGetLastError();
 }
 cudaError_t tomo_merge(float* z, const float* ztmp, int64_t n, float z_low, bool last, int num_sms, cudaStream_t s) {

@@ -82,7 +82,7 @@ void bucket_plan(int64_t n, int* nbuckets, int* shift);
 // intensity +inf (rank first); take the interval's redshift for neutral cells
 // at or above z_low (all of them when last).
 cudaError_t tomo_fill(float* z, int64_t n, int num_sms, cudaStream_t s);
-cudaError_t tomo_mask(float* J, const float* z, int64_t n, int num_sms, cudaStream_t s);
+cudaError_t tomo_mask(float* J, const float* z, int64_t n, SortCtrl* ctrl, int num_sms, cudaStream_t s);
 cudaError_t tomo_merge(float* z, const float* ztmp, int64_t n, float z_low, bool last, int num_sms, cudaStream_t s);
 
 // mass_in_rank_order: mass[n] belongs to rank n (sort payload) instead of to

@@ -36,9 +36,13 @@ def test_one_source_in_every_interval_is_the_plain_solve(ctx, B):
     S, m = synth.realisation(n, box, 0, device="cuda")
     h = B.history(8.0, 4.0, 3.0)
     plain = ctx.solve(S, m, box, 3.0, h)
+    plain_passes = ctx.sort_passes()
     z = ctx.solve_tomographic([S, S, S], [20.0, 9.0, 7.5, 5.0], m, box, 3.0, h)
     assert ctx.sync_status() == 0
     assert torch.equal(z, plain)
+    # the ionized cells' intensity (one float above the interval's largest)
+    # widens the key range by one key: the last ranking needs no extra digit pass
+    assert ctx.sort_passes() == plain_passes
 
 
 def test_tomographic_vs_oracle(ctx, B):
