@@ -405,6 +405,25 @@ def test_assign_weighted_vs_oracle_given_order(ctx, B, weighting, n):
     assert np.quantile(d, 0.999) < 5e-5, np.quantile(d, 0.999)
 
 
+@pytest.mark.parametrize("weighting", [1, 2])
+@pytest.mark.parametrize("n_table", [2, 3, 17])
+def test_assign_weighted_short_table(ctx, B, weighting, n_table):
+    # few table points over 200000 ranks: most scan tiles lie between two
+    # points, where every cell of the tile takes the same point
+    n = 200_000
+    g = np.random.default_rng(300 + n_table)
+    mass = g.uniform(0.01, 3.0, n).astype(np.float32)
+    order = g.permutation(n).astype(np.int32)
+    h = B.history(8.0, 4.0, 3.0, n_table=n_table, weighting=weighting)
+    z = ctx.assign_zre(torch.from_numpy(order).cuda(), torch.from_numpy(mass).cuda(), h)
+    check_status(ctx, B)
+    t = O.history_table(8.0, 4.0, 3.0, n_table=n_table)
+    zo = O.assign_zre_weighted(order, mass.astype(np.float64), t, weighting, 8.0, 0.3)
+    d = np.abs(z.cpu().numpy().astype(np.float64) - zo)
+    assert np.mean(d > 1e-3) <= 1e-4, (np.mean(d > 1e-3), d.max())
+    assert np.quantile(d, 0.999) < 5e-5, np.quantile(d, 0.999)
+
+
 def test_assign_volume_equals_unit_masses(ctx, B):
     n = 200_000
     g = np.random.default_rng(4)
