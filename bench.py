@@ -366,6 +366,7 @@ def run_amber(args):
     ms = e0.elapsed_time(e1) / args.steps
     prof = ctx.profile_read()
     ctx.profile(False)
+    passes = ctx.sort_passes()  # digit passes of the timed solves' ranking
     st = ctx.sync_status()
     if st != 0:
         raise RuntimeError(f"device status after timed region: {B.status_string(st)}")
@@ -571,10 +572,17 @@ def run_amber(args):
     st = ctx.sync_status()
     if st != 0:
         raise RuntimeError(f"device status after end-to-end steps: {B.status_string(st)}")
+    # the autotuner's measurement of this workload (after the timed steps,
+    # which ran the default choices)
+    tune = None
+    if rank == 0 and ws == 1 and not args.no_extras:
+        tune = ctx.autotune(S_d[0], m_d[0], box, L_MFP)
+        st = ctx.sync_status()
+        if st != 0:
+            raise RuntimeError(f"device status after autotuning: {B.status_string(st)}")
     del S_d, m_d, z_d, z_h, S_h, m_h
 
     launches_per_step = sum(v[1] for v in prof.values()) / args.steps
-    passes = ctx.sort_passes()
     ab = algorithmic_bytes(n, passes)
     kernels = {}
     for k, (ms_k, cnt) in prof.items():
@@ -594,6 +602,8 @@ def run_amber(args):
         cpu = oracle_baseline(ns, box * ns / n, args.cpu_seconds)
 
     extras = {}
+    if tune is not None:
+        extras["autotune"] = tune
     if rank == 0 and ws == 1 and not args.no_extras:
         ctx.close()
         torch.cuda.empty_cache()
@@ -653,6 +663,16 @@ def run_batched(B, synth, torch, reps: int = 3):
     cells = sum(it[0].numel() for it in items)
     ctxs = [B.Context(256 ** 3) for _ in range(8)]
     stream = torch.cuda.current_stream()
+    # the autotuner picks each size's FFT variant, digit width and digit-peer
+    # method on that size's first realisation; plain loop and batch then
+    # share the choices (the batch finds the sizes tuned)
+    tuning = {}
+    for n_t in (128, 256):
+        it = next(x for x in items if x[0].shape[0] == n_t)
+        t = ctxs[0].autotune(it[0], it[1], it[2], it[3])
+        for c in ctxs[1:]:
+            c.set_tuning(n_t, t["fft_variant"], t["sort_digit_bits"], t["sort_match"])
+        tuning[str(n_t)] = t
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     # plain: the single-instance path, one call after another
     for it in items:
@@ -680,7 +700,8 @@ def run_batched(B, synth, torch, reps: int = 3):
         c.close()
     return {"workload": "48 realisations: 32 x 128^3 (box 100) + 16 x 256^3 (box 200), l_mfp U[1,20], "
                         "z_mid U[6.5,9], dz U[2,6], Az U[1.5,5]",
-            "cells": cells, "plain_loop_ms": plain_ms, "plain_loop_cells_per_s": cells / (plain_ms / 1e3),
+            "cells": cells, "tuning": tuning, "plain_loop_ms": plain_ms,
+            "plain_loop_cells_per_s": cells / (plain_ms / 1e3),
             "graph_ms": graph_ms, "graph_cells_per_s": cells / (graph_ms / 1e3), "speedup": plain_ms / graph_ms,
             "contexts": len(ctxs), "status": st}
 

@@ -198,11 +198,61 @@ int amber_solve_ex(amber_ctx *ctx, const float *d_src, const float *d_mass, cons
 int amber_assign_zre_ranked(amber_ctx *ctx, const uint32_t *d_order, const float *d_mass_rank, int64_t ncells,
                             const amber_history_t *h, float *d_zre, double *d_F_opt, void *stream);
 
+/* ---- Autotuning of the FP32 solve path per grid size ------------------- */
+
+/* The choices the FP32 solve path (amber_solve, amber_solve_ex,
+ * amber_solve_tomographic, amber_batch_*) and the FP32 amber_radiation_field
+ * make for one grid size n of one context:
+ *   fft_variant      0: the default tiles (every n); 1: an alternative radix
+ *                    split or tile width (n >= 128: 1024 with 4-line tiles,
+ *                    512 as 16 x 32, 256 as 32 x 8, 128 as 8 x 16);
+ *   sort_digit_bits  9 or 8: digit width of the radix sort (a few-octave
+ *                    intensity field needs 27 bits: 3 passes of 9 bits, 4 of 8;
+ *                    a 24-bit range takes 3 of either, the 8-bit ones cheaper);
+ *   sort_match       0: digit peers by one warp ballot per digit bit;
+ *                    1: by warp match (AMBER_SORT_RANK=ballot|match in the
+ *                    environment overrides it).
+ * Every choice gives the same ranking (the stable descending order is
+ * unique); the FFT variants differ only in FP32 rounding.  Defaults: 0, 8
+ * for n >= 512 and 9 below, 0 (the tuner's picks on a synthetic field of the
+ * paper's kind).
+ * tuned: 1 once amber_autotune measured this size; fft_ms[v] and sort_ms[k]
+ * hold the median times it measured (k: (9, ballot), (9, match), (8,
+ * ballot), (8, match); 0 where not applicable). */
+typedef struct {
+  int n;
+  int fft_variant;
+  int sort_digit_bits;
+  int sort_match;
+  int tuned;
+  double fft_ms[2];
+  double sort_ms[4];
+} amber_tuning_t;
+
+/* Measures every choice on the caller's own field (d_src, d_mass: n^3 floats
+ * each, the solve's inputs; box and l_mfp as for amber_solve), keeps the
+ * fastest for n on this context and writes the result to *out (may be NULL).
+ * Each candidate runs once untimed and three times timed (CUDA events; the
+ * median counts); the ranking is timed with the mass payload as in the
+ * solve.  Synchronises the stream.  Leaves no result in the caller's
+ * buffers; overwrites the context's workspace.  Errors as for amber_solve. */
+int amber_autotune(amber_ctx *ctx, const float *d_src, const float *d_mass, int n, double box, double l_mfp,
+                   amber_tuning_t *out, void *stream);
+/* Sets the choices for t->n explicitly (t->tuned and the times are kept as
+ * given).  AMBER_ERR_INVALID_ARG for a size the context cannot hold or a
+ * choice out of range. */
+int amber_set_tuning(amber_ctx *ctx, const amber_tuning_t *t);
+/* The current choices for size n. */
+int amber_get_tuning(amber_ctx *ctx, int n, amber_tuning_t *out);
+
 /* Batched solves: one captured CUDA graph replays many amber_solve calls.
  * Item i runs on ctxs[i % nctx], each context on its own stream forked from
  * and joined into one origin, so small realisations overlap on the GPU and
  * the whole batch costs one host launch.  Items are validated before the
- * capture (same rules as amber_solve, precision 32).  The graph records the
+ * capture (same rules as amber_solve, precision 32).  Before capturing, each
+ * grid size not yet tuned on the first context is autotuned on the first item
+ * of that size (amber_autotune), and the choices are copied to every context
+ * of the batch; AMBER_AUTOTUNE=0 in the environment skips this.  The graph records the
  * given device pointers and parameters: buffers and contexts must stay
  * alive while the batch exists, and a context must not run other work while
  * the batch runs. */

@@ -32,7 +32,7 @@ EXPORTED = [
     "amber_solve_ex", "amber_assign_zre_ranked", "amber_batch_create", "amber_batch_launch", "amber_batch_destroy",
     "amber_delta_z", "amber_epsilon_z_pdf", "amber_power_bins", "amber_power_spectrum",
     "amber_lpt_displacement", "amber_mesh_density", "amber_esf_fcoll", "amber_sigma2_tophat",
-    "amber_solve_tomographic",
+    "amber_solve_tomographic", "amber_autotune", "amber_set_tuning", "amber_get_tuning",
     "amber_rank_noalloc",
 ]
 
@@ -52,6 +52,16 @@ class amber_history_t(C.Structure):
 class amber_params_t(C.Structure):
     _fields_ = [("n", C.c_int), ("box", C.c_double), ("l_mfp", C.c_double),
                 ("hist", amber_history_t), ("precision", C.c_int)]
+
+
+class amber_tuning_t(C.Structure):
+    _fields_ = [("n", C.c_int), ("fft_variant", C.c_int), ("sort_digit_bits", C.c_int), ("sort_match", C.c_int),
+                ("tuned", C.c_int), ("fft_ms", C.c_double * 2), ("sort_ms", C.c_double * 4)]
+
+    def as_dict(self) -> dict:
+        return {"n": self.n, "fft_variant": self.fft_variant, "sort_digit_bits": self.sort_digit_bits,
+                "sort_match": self.sort_match, "tuned": self.tuned, "fft_ms": list(self.fft_ms),
+                "sort_ms": list(self.sort_ms)}
 
 
 class amber_batch_item(C.Structure):
@@ -107,6 +117,9 @@ def _load():
         "amber_sigma2_tophat": (i32, [C.POINTER(dbl), C.POINTER(dbl), i32, dbl, C.POINTER(dbl)]),
         "amber_solve_tomographic": (i32, [vp, C.POINTER(vp), i32, C.POINTER(dbl), vp, C.POINTER(amber_params_t), vp,
                                           vp]),
+        "amber_autotune": (i32, [vp, vp, vp, i32, dbl, dbl, C.POINTER(amber_tuning_t), vp]),
+        "amber_set_tuning": (i32, [vp, C.POINTER(amber_tuning_t)]),
+        "amber_get_tuning": (i32, [vp, i32, C.POINTER(amber_tuning_t)]),
         "amber_rank_noalloc": (i32, [vp, i64, vp, vp, vp]),
         "amber_test_wait_timeout": (i32, [vp, C.c_uint, vp]),
     }
@@ -348,6 +361,23 @@ class Context:
 
     def test_wait_timeout(self, spin_limit: int, stream=None):
         _check(lib.amber_test_wait_timeout(self._h, spin_limit, _stream(stream)), "amber_test_wait_timeout")
+
+    # --- autotuning of the FP32 solve path per grid size ----------------------
+    def autotune(self, S, mass, box: float, l_mfp: float, stream=None) -> dict:
+        """Time every FFT variant and ranking choice on these inputs; keep the fastest for S's size."""
+        t = amber_tuning_t()
+        _check(lib.amber_autotune(self._h, _ptr(S), _ptr(mass), S.shape[0], box, l_mfp, C.byref(t), _stream(stream)),
+               "amber_autotune")
+        return t.as_dict()
+
+    def set_tuning(self, n: int, fft_variant: int = 0, sort_digit_bits: int = 9, sort_match: int = 0):
+        t = amber_tuning_t(n, fft_variant, sort_digit_bits, sort_match, 0)
+        _check(lib.amber_set_tuning(self._h, C.byref(t)), "amber_set_tuning")
+
+    def get_tuning(self, n: int) -> dict:
+        t = amber_tuning_t()
+        _check(lib.amber_get_tuning(self._h, n, C.byref(t)), "amber_get_tuning")
+        return t.as_dict()
 
     def solve_tomographic(self, sources, z_bounds, mass, box: float, l_mfp: float, h: amber_history_t, out=None,
                           stream=None):

@@ -3,6 +3,7 @@
 // kernel event timing, and the extern "C" entry points declared in amber.h.
 #include <cmath>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -18,8 +19,10 @@
 namespace amber {
 // krange: if not null, the intensities' key range is folded into it (the
 // sort's control block, reset beforehand) so the ranking needs no range pass.
+// variant: the FFT tile/radix variant (0 default; 1 for n >= 128).
 cudaError_t radiation_field_f32(int n, const float* src, float* J, void* H, const void* tw, double box, double l_mfp,
-                               unsigned int* status, cudaStream_t s, FftProfile* prof, SortCtrl* krange);
+                               unsigned int* status, cudaStream_t s, FftProfile* prof, SortCtrl* krange,
+                               int variant);
 cudaError_t radiation_field_f64(int n, const double* src, double* J, void* H, const void* tw, double box,
                                double l_mfp, unsigned int* status, cudaStream_t s, FftProfile* prof,
                                SortCtrl* krange);
@@ -231,6 +234,7 @@ struct amber_ctx {
   int num_sms = 0;
   FftProfile prof;
   cudaStream_t last_stream = nullptr;
+  amber_tuning_t tune[11] = {};  // per log2 n: FFT variant, digit width and peers of the FP32 solve path
   std::mutex mu;
 };
 
@@ -307,6 +311,12 @@ int amber_create(amber_ctx** out, int device, int64_t max_cells) {
   }
   DeviceGuard g(device);
   amber_ctx* c = new (std::nothrow) amber_ctx();
+  // defaults: the autotuner's picks on the synthetic recipe -- 8-bit digits
+  // from 512^3 up (four passes of 8 bits beat three of 9 there: 30.7 vs
+  // 32.1 ms per ranking at 1024^3), 9-bit below, default FFT tiles, ballots
+  if (c)
+    for (int l = 0; l < 11; ++l)
+      c->tune[l] = amber_tuning_t{1 << l, 0, l >= 9 ? 8 : 9, 0, 0, {0.0, 0.0}, {0.0, 0.0, 0.0, 0.0}};
   if (!c) return AMBER_ERR_OOM;
   c->device = device;
   c->max_cells = max_cells;
@@ -403,7 +413,7 @@ int amber_radiation_field(amber_ctx* c, const float* d_src, int n, double box, d
   const Plan& p = c->plan;
   const int l = ilog2i(n);
   return cuda_status(radiation_field_f32(n, d_src, d_J, c->ws + p.off_spec, c->ws + p.off_tw32 + p.tw32_off[l], box,
-                                         l_mfp, c->status, s, &c->prof, nullptr));
+                                         l_mfp, c->status, s, &c->prof, nullptr, c->tune[l].fft_variant));
 }
 
 int amber_radiation_field_f64(amber_ctx* c, const double* d_src, int n, double box, double l_mfp, double* d_J,
@@ -609,15 +619,16 @@ static cudaError_t solve_f32_enqueue(amber_ctx* c, const float* d_src, const flo
   const int n = p->n;
   const int64_t C = (int64_t)n * n * n;
   float* J = d_J_opt ? d_J_opt : reinterpret_cast<float*>(c->sortw.keysB);
+  const amber_tuning_t& tu = c->tune[ilog2i(n)];
   cudaError_t e = sort_ctrl_reset(c->sortw.ctrl, s);
   if (e == cudaSuccess)
     e = radiation_field_f32(n, d_src, J, c->ws + pl.off_spec, c->ws + pl.off_tw32 + pl.tw32_off[ilog2i(n)], p->box,
-                           p->l_mfp, c->status, s, &c->prof, c->sortw.ctrl);
+                           p->l_mfp, c->status, s, &c->prof, c->sortw.ctrl, tu.fft_variant);
   // the first sort pass sums each tile's masses; the thresholds kernel adds them
   unsigned long long* tile_mass = reinterpret_cast<unsigned long long*>(c->ws + pl.off_tilemass);
   if (e == cudaSuccess)
     e = rank_impl<float>(c->sortw, J, C, order_out, d_mass, order_out ? mass_rank_out : nullptr, tile_mass, true,
-                         c->status, s, &c->prof, kSpinLimit);
+                         c->status, s, &c->prof, kSpinLimit, tu.sort_digit_bits, tu.sort_match);
   if (e != cudaSuccess) return e;
   if (order_out)
     return assign_impl(c->assw, order_out, mass_rank_out, true, tile_mass, C, hc, d_zre, nullptr, c->status, s,
@@ -625,6 +636,84 @@ static cudaError_t solve_f32_enqueue(amber_ctx* c, const float* d_src, const flo
   // the order and rank-order masses sit on the A or B side by pass parity
   return assign_impl(c->assw, c->sortw.idxA, c->sortw.massA, true, tile_mass, C, hc, d_zre, nullptr, c->status, s,
                      &c->prof, kSpinLimit, c->sortw.idxB, c->sortw.massB, &c->sortw.ctrl->npasses);
+}
+
+// Autotuning of one grid size (the context's lock held): every FFT variant,
+// then every (digit width, digit-peer method) of the ranking on the chosen
+// variant's intensities, each once untimed and three times timed.
+static bool autotune_enabled() {
+  const char* v = getenv("AMBER_AUTOTUNE");
+  return !(v && strcmp(v, "0") == 0);
+}
+
+static int autotune_locked(amber_ctx* c, const float* d_src, const float* d_mass, int n, double box, double l_mfp,
+                           amber_tuning_t* out, cudaStream_t s) {
+  const Plan& pl = c->plan;
+  const int lg = ilog2i(n);
+  const int64_t C = (int64_t)n * n * n;
+  const void* tw = c->ws + pl.off_tw32 + pl.tw32_off[lg];
+  float* J = reinterpret_cast<float*>(c->sortw.keysB);
+  // the spectrum buffer (>= 4 B/cell) is free once a transform is done: it
+  // keeps the intensities the ranking candidates start from
+  float* Jkeep = reinterpret_cast<float*>(c->ws + pl.off_spec);
+  unsigned long long* tile_mass = reinterpret_cast<unsigned long long*>(c->ws + pl.off_tilemass);
+  const bool prof_on = c->prof.on;
+  c->prof.on = false;
+  amber_tuning_t t = c->tune[lg];
+  t.n = n;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  // median of three timed runs after one untimed run
+  auto timed = [&](auto&& run, double* ms_out) {
+    double ms[3] = {0.0, 0.0, 0.0};
+    for (int r = -1; r < 3 && e == cudaSuccess; ++r) {
+      e = cudaEventRecord(e0, s);
+      if (e == cudaSuccess) e = run();
+      if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float f = 0.f;
+      if (e == cudaSuccess && r >= 0) e = cudaEventElapsedTime(&f, e0, e1);
+      if (r >= 0) ms[r] = f;
+    }
+    std::sort(ms, ms + 3);
+    *ms_out = ms[1];
+  };
+  const int nv = n >= 128 ? 2 : 1;
+  t.fft_ms[0] = t.fft_ms[1] = 0.0;
+  for (int v = 0; v < nv && e == cudaSuccess; ++v)
+    timed([&] { return radiation_field_f32(n, d_src, J, c->ws + pl.off_spec, tw, box, l_mfp, c->status, s, nullptr,
+                                           nullptr, v); }, &t.fft_ms[v]);
+  t.fft_variant = (nv == 2 && t.fft_ms[1] < t.fft_ms[0]) ? 1 : 0;
+  if (e == cudaSuccess)
+    e = radiation_field_f32(n, d_src, J, c->ws + pl.off_spec, tw, box, l_mfp, c->status, s, nullptr, nullptr,
+                            t.fft_variant);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(Jkeep, J, (size_t)C * sizeof(float), cudaMemcpyDeviceToDevice, s);
+  static const int cand[4][2] = {{9, 0}, {9, 1}, {8, 0}, {8, 1}};
+  int best = 0;
+  for (int k = 0; k < 4 && e == cudaSuccess; ++k) {
+    timed([&] {
+      cudaError_t r = cudaMemcpyAsync(J, Jkeep, (size_t)C * sizeof(float), cudaMemcpyDeviceToDevice, s);
+      if (r == cudaSuccess)
+        r = rank_impl<float>(c->sortw, J, C, nullptr, d_mass, nullptr, tile_mass, false, c->status, s, nullptr,
+                             kSpinLimit, cand[k][0], cand[k][1]);
+      return r;
+    }, &t.sort_ms[k]);
+    if (t.sort_ms[k] < t.sort_ms[best]) best = k;
+  }
+  t.sort_digit_bits = cand[best][0];
+  t.sort_match = cand[best][1];
+  t.tuned = 1;
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  c->prof.on = prof_on;
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return AMBER_ERR_CUDA;
+  }
+  c->tune[lg] = t;
+  if (out) *out = t;
+  return AMBER_OK;
 }
 
 int amber_solve(amber_ctx* c, const float* d_src, const float* d_mass, const amber_params_t* p, float* d_zre,
@@ -637,6 +726,34 @@ int amber_solve(amber_ctx* c, const float* d_src, const float* d_mass, const amb
   cudaStream_t s = (cudaStream_t)stream;
   c->last_stream = s;
   return cuda_status(solve_f32_enqueue(c, d_src, d_mass, p, hc, d_zre, d_J_opt, nullptr, nullptr, s));
+}
+
+int amber_autotune(amber_ctx* c, const float* d_src, const float* d_mass, int n, double box, double l_mfp,
+                   amber_tuning_t* out, void* stream) {
+  const int st = rf_args_ok(c, d_src, n, box, l_mfp, d_src, c ? c->plan.n32 : 0);
+  if (st) return st;
+  if (!d_mass) return AMBER_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(c->mu);
+  DeviceGuard g(c->device);
+  c->last_stream = (cudaStream_t)stream;
+  return autotune_locked(c, d_src, d_mass, n, box, l_mfp, out, (cudaStream_t)stream);
+}
+
+int amber_set_tuning(amber_ctx* c, const amber_tuning_t* t) {
+  if (!c || !t || !is_pow2_in(t->n, 4, 1024) || t->n > c->plan.n32) return AMBER_ERR_INVALID_ARG;
+  if (t->fft_variant < 0 || t->fft_variant > (t->n >= 128 ? 1 : 0)) return AMBER_ERR_INVALID_ARG;
+  if ((t->sort_digit_bits != 8 && t->sort_digit_bits != 9) || (t->sort_match != 0 && t->sort_match != 1))
+    return AMBER_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(c->mu);
+  c->tune[ilog2i(t->n)] = *t;
+  return AMBER_OK;
+}
+
+int amber_get_tuning(amber_ctx* c, int n, amber_tuning_t* out) {
+  if (!c || !out || !is_pow2_in(n, 4, 1024)) return AMBER_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(c->mu);
+  *out = c->tune[ilog2i(n)];
+  return AMBER_OK;
 }
 
 int amber_solve_tomographic(amber_ctx* c, const float* const* d_src_list, int nint, const double* z_bounds,
@@ -666,11 +783,12 @@ int amber_solve_tomographic(amber_ctx* c, const float* const* d_src_list, int ni
     e = sort_ctrl_reset(c->sortw.ctrl, s);
     if (e == cudaSuccess)
       e = radiation_field_f32(n, d_src_list[k], J, c->ws + pl.off_spec, c->ws + pl.off_tw32 + pl.tw32_off[ilog2i(n)],
-                              p->box, p->l_mfp, c->status, s, &c->prof, c->sortw.ctrl);
+                              p->box, p->l_mfp, c->status, s, &c->prof, c->sortw.ctrl,
+                              c->tune[ilog2i(n)].fft_variant);
     if (e == cudaSuccess && k > 0) e = tomo_mask(J, d_zre, C, c->sortw.ctrl, c->num_sms, s);
     if (e == cudaSuccess)
       e = rank_impl<float>(c->sortw, J, C, nullptr, d_mass, nullptr, tile_mass, true, c->status, s, &c->prof,
-                           kSpinLimit);
+                           kSpinLimit, c->tune[ilog2i(n)].sort_digit_bits, c->tune[ilog2i(n)].sort_match);
     if (e == cudaSuccess)
       e = assign_impl(c->assw, c->sortw.idxA, c->sortw.massA, true, tile_mass, C, hc, ztmp, nullptr, c->status, s,
                       &c->prof, kSpinLimit, c->sortw.idxB, c->sortw.massB, &c->sortw.ctrl->npasses);
@@ -734,6 +852,17 @@ int amber_batch_create(amber_batch** out, amber_ctx* const* ctxs, int nctx, cons
   std::vector<std::unique_lock<std::mutex>> locks;
   for (int k = 0; k < nctx; ++k) locks.emplace_back(ctxs[k]->mu);
   DeviceGuard g(dev);
+  // each size not yet tuned: autotune on its first item, then share the
+  // choices with every context of the batch
+  for (int i = 0; i < nitems && autotune_enabled(); ++i) {
+    const int n = items[i].params.n, lg = ilog2i(n);
+    if (ctxs[0]->tune[lg].tuned) continue;
+    amber_ctx* c = ctxs[i % nctx];
+    const int st = autotune_locked(c, items[i].d_src, items[i].d_mass, n, items[i].params.box,
+                                   items[i].params.l_mfp, nullptr, nullptr);
+    if (st) return st;
+    for (int k = 0; k < nctx; ++k) ctxs[k]->tune[lg] = c->tune[lg];
+  }
   amber_batch* b = new (std::nothrow) amber_batch();
   if (!b) return AMBER_ERR_OOM;
   b->device = dev;

@@ -22,26 +22,34 @@
 
 namespace amber {
 
-template <int N> struct FftCfg;
-//                                        R0  R1   E  strided-lines  x-pairs
-template <> struct FftCfg<1024> { static constexpr int R0 = 32, R1 = 32, E = 32, SB = 8,  XP = 8;  };
-template <> struct FftCfg<512>  { static constexpr int R0 = 32, R1 = 16, E = 32, SB = 16, XP = 16; };
-template <> struct FftCfg<256>  { static constexpr int R0 = 16, R1 = 16, E = 16, SB = 16, XP = 16; };
-template <> struct FftCfg<128>  { static constexpr int R0 = 16, R1 = 8,  E = 16, SB = 32, XP = 32; };
-template <> struct FftCfg<64>   { static constexpr int R0 = 8,  R1 = 8,  E = 8,  SB = 32, XP = 32; };
-template <> struct FftCfg<32>   { static constexpr int R0 = 32, R1 = 1,  E = 32, SB = 32, XP = 32; };
-template <> struct FftCfg<16>   { static constexpr int R0 = 16, R1 = 1,  E = 16, SB = 32, XP = 32; };
-template <> struct FftCfg<8>    { static constexpr int R0 = 8,  R1 = 1,  E = 8,  SB = 32, XP = 32; };
-template <> struct FftCfg<4>    { static constexpr int R0 = 4,  R1 = 1,  E = 4,  SB = 32, XP = 32; };
+// Per size N, variant V: the radix split N = R0 R1, elements per thread E
+// (a multiple of both radices), lines per strided tile SB and row pairs per
+// x-pass tile XP.  Variant 0 is the default; variant 1 (N >= 128) is the
+// alternative split or tile the autotuner times against it.
+template <int N, int V = 0> struct FftCfg;
+//                                           R0  R1   E  strided-lines  x-pairs
+template <> struct FftCfg<1024, 0> { static constexpr int R0 = 32, R1 = 32, E = 32, SB = 8,  XP = 8;  };
+template <> struct FftCfg<512, 0>  { static constexpr int R0 = 32, R1 = 16, E = 32, SB = 16, XP = 16; };
+template <> struct FftCfg<256, 0>  { static constexpr int R0 = 16, R1 = 16, E = 16, SB = 16, XP = 16; };
+template <> struct FftCfg<128, 0>  { static constexpr int R0 = 16, R1 = 8,  E = 16, SB = 32, XP = 32; };
+template <> struct FftCfg<64, 0>   { static constexpr int R0 = 8,  R1 = 8,  E = 8,  SB = 32, XP = 32; };
+template <> struct FftCfg<32, 0>   { static constexpr int R0 = 32, R1 = 1,  E = 32, SB = 32, XP = 32; };
+template <> struct FftCfg<16, 0>   { static constexpr int R0 = 16, R1 = 1,  E = 16, SB = 32, XP = 32; };
+template <> struct FftCfg<8, 0>    { static constexpr int R0 = 8,  R1 = 1,  E = 8,  SB = 32, XP = 32; };
+template <> struct FftCfg<4, 0>    { static constexpr int R0 = 4,  R1 = 1,  E = 4,  SB = 32, XP = 32; };
+template <> struct FftCfg<1024, 1> { static constexpr int R0 = 32, R1 = 32, E = 32, SB = 4,  XP = 4;  };
+template <> struct FftCfg<512, 1>  { static constexpr int R0 = 16, R1 = 32, E = 32, SB = 8,  XP = 8;  };
+template <> struct FftCfg<256, 1>  { static constexpr int R0 = 32, R1 = 8,  E = 32, SB = 8,  XP = 8;  };
+template <> struct FftCfg<128, 1>  { static constexpr int R0 = 8,  R1 = 16, E = 16, SB = 16, XP = 16; };
 
-template <int N> constexpr int strided_threads() { return FftCfg<N>::SB * N / FftCfg<N>::E; }
-template <int N> constexpr int xpass_threads() { return FftCfg<N>::XP * N / FftCfg<N>::E; }
+template <int N, int V = 0> constexpr int strided_threads() { return FftCfg<N, V>::SB * N / FftCfg<N, V>::E; }
+template <int N, int V = 0> constexpr int xpass_threads() { return FftCfg<N, V>::XP * N / FftCfg<N, V>::E; }
 
 // Shared-memory layout of a strided tile: element (n, b) of line b.  With
 // 8 float2 lines a row is 64 bytes; the pad per 32 rows puts the row groups
 // a stage-A butterfly writes (n = 32 j + r) on alternating bank halves.
-template <typename T, int N> struct StridedSmem {
-  static constexpr int SB = FftCfg<N>::SB;
+template <typename T, int N, int V = 0> struct StridedSmem {
+  static constexpr int SB = FftCfg<N, V>::SB;
   static constexpr int PAD = (SB * (int)sizeof(cpx<T>) == 64) ? 8 : 0;
   static constexpr int elems = N * SB + (N / 32) * PAD;
   static __device__ __forceinline__ int pos(int n, int b) { return n * SB + b + (n >> 5) * PAD; }
@@ -49,10 +57,10 @@ template <typename T, int N> struct StridedSmem {
 
 // Shared-memory layout of x-pass lines: line p, element n.  One pad element
 // per R0 keeps stage-A writes (n = R0 j + r, lanes along j) conflict-free.
-template <typename T, int N> struct XSmem {
-  static constexpr int R0 = FftCfg<N>::R0;
+template <typename T, int N, int V = 0> struct XSmem {
+  static constexpr int R0 = FftCfg<N, V>::R0;
   static constexpr int LS = N + N / R0;
-  static constexpr int elems = FftCfg<N>::XP * LS;
+  static constexpr int elems = FftCfg<N, V>::XP * LS;
   static __device__ __forceinline__ int pos(int p, int n) { return p * LS + n + n / R0; }
 };
 
@@ -87,13 +95,13 @@ __device__ __forceinline__ int signed_freq(int m, int n) { return m < n / 2 ? m 
 // ---------------------------------------------------------------------------
 enum { PASS_FWD = 0, PASS_INV = 1, PASS_CONV = 2 };
 
-template <typename T, int N, int MODE>
-__global__ void __launch_bounds__(strided_threads<N>(), 2)
+template <typename T, int N, int MODE, int V = 0>
+__global__ void __launch_bounds__(strided_threads<N, V>(), 2)
 k_fft_strided(cpx<T>* __restrict__ H, int64_t elem_stride, int64_t outer_stride, int ncol,
               int ntx, const cpx<T>* __restrict__ tw, T kf, T l_mfp, T norm) {
-  using C = FftCfg<N>;
-  using L = StridedSmem<T, N>;
-  constexpr int R0 = C::R0, R1 = C::R1, E = C::E, SB = C::SB, NT = strided_threads<N>();
+  using C = FftCfg<N, V>;
+  using L = StridedSmem<T, N, V>;
+  constexpr int R0 = C::R0, R1 = C::R1, E = C::E, SB = C::SB, NT = strided_threads<N, V>();
   constexpr int QA = E / R0, QB = (R1 > 1) ? E / R1 : 0;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<T>* sm = reinterpret_cast<cpx<T>*>(smem_raw);
@@ -245,14 +253,14 @@ k_fft_strided(cpx<T>* __restrict__ H, int64_t elem_stride, int64_t outer_stride,
 // x-pass R2C: rows 2p and 2p+1 form z = a + i b; after the complex FFT
 // A_k = (Z_k + conj Z_{N-k})/2 and B_k = (Z_k - conj Z_{N-k})/(2i), k <= N/2.
 // ---------------------------------------------------------------------------
-template <typename T, int N>
+template <typename T, int N, int V = 0>
 // FP32: three CTAs per SM (measured faster for the forward x pass only)
-__global__ void __launch_bounds__(xpass_threads<N>(), sizeof(T) == 4 ? 3 : 1)
+__global__ void __launch_bounds__(xpass_threads<N, V>(), sizeof(T) == 4 ? 3 : 1)
 k_fft_r2c_x(const T* __restrict__ src, cpx<T>* __restrict__ H, int64_t nrows, int RS,
             const cpx<T>* __restrict__ tw) {
-  using C = FftCfg<N>;
-  using L = XSmem<T, N>;
-  constexpr int R0 = C::R0, R1 = C::R1, E = C::E, XP = C::XP, NT = xpass_threads<N>();
+  using C = FftCfg<N, V>;
+  using L = XSmem<T, N, V>;
+  constexpr int R0 = C::R0, R1 = C::R1, E = C::E, XP = C::XP, NT = xpass_threads<N, V>();
   constexpr int QA = E / R0, QB = (R1 > 1) ? E / R1 : 0;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<T>* sm = reinterpret_cast<cpx<T>*>(smem_raw);
@@ -332,14 +340,14 @@ k_fft_r2c_x(const T* __restrict__ src, cpx<T>* __restrict__ H, int64_t nrows, in
 // DC and Nyquist use the real parts only.  Re z -> row 2p, Im z -> row 2p+1.
 // The 1/n^3 normalisation was applied with the kernel in the z-pass.
 // ---------------------------------------------------------------------------
-template <typename T, int N>
-__global__ void __launch_bounds__(xpass_threads<N>())
+template <typename T, int N, int V = 0>
+__global__ void __launch_bounds__(xpass_threads<N, V>())
 k_fft_c2r_x(const cpx<T>* __restrict__ H, T* __restrict__ J, int64_t nrows, int RS,
             const cpx<T>* __restrict__ tw, unsigned int* __restrict__ status, SortCtrl* __restrict__ krange) {
-  using C = FftCfg<N>;
-  using L = XSmem<T, N>;
+  using C = FftCfg<N, V>;
+  using L = XSmem<T, N, V>;
   using K = typename KeyOf<T>::K;
-  constexpr int R0 = C::R0, R1 = C::R1, E = C::E, XP = C::XP, NT = xpass_threads<N>();
+  constexpr int R0 = C::R0, R1 = C::R1, E = C::E, XP = C::XP, NT = xpass_threads<N, V>();
   constexpr int QA = E / R0, QB = (R1 > 1) ? E / R1 : 0;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<T>* sm = reinterpret_cast<cpx<T>*>(smem_raw);
@@ -468,50 +476,50 @@ enum ProfKind {
   PK_SORT_HIST, PK_SORT_PASS, PK_MASS_REDUCE, PK_THRESHOLDS, PK_SCAN_ASSIGN, PK_SCATTER_BACK, PK_COUNT
 };
 
-template <typename T, int N>
+template <typename T, int N, int V = 0>
 cudaError_t radiation_field_n(const T* src, T* J, cpx<T>* H, const cpx<T>* tw, double box, double l_mfp,
                               unsigned int* status, cudaStream_t s, FftProfile* prof, SortCtrl* krange) {
-  using C = FftCfg<N>;
+  using C = FftCfg<N, V>;
   const int RS = N / 2 + 2;
   const int ncol = N / 2 + 1;
   const int64_t nrows = (int64_t)N * N;
   const T kf = (T)(2.0 * 3.14159265358979323846 / box);
   const T norm = (T)(1.0 / ((double)N * N * N));
-  const size_t xs = XSmem<T, N>::elems * sizeof(cpx<T>);
-  const size_t ss = StridedSmem<T, N>::elems * sizeof(cpx<T>);
+  const size_t xs = XSmem<T, N, V>::elems * sizeof(cpx<T>);
+  const size_t ss = StridedSmem<T, N, V>::elems * sizeof(cpx<T>);
   // the z pass adds its table of K over |kz| = 0..N/2 for the tile's columns
   const size_t sc = ss + (size_t)(N / 2 + 1) * C::SB * sizeof(T);
   static std::atomic<unsigned long long> attr_done{0};  // per instantiation and device
   if (first_use_on_device(attr_done)) {
-    cudaFuncSetAttribute(k_fft_r2c_x<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xs);
-    cudaFuncSetAttribute(k_fft_c2r_x<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xs);
-    cudaFuncSetAttribute(k_fft_strided<T, N, PASS_FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss);
-    cudaFuncSetAttribute(k_fft_strided<T, N, PASS_INV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss);
-    cudaFuncSetAttribute(k_fft_strided<T, N, PASS_CONV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sc);
+    cudaFuncSetAttribute(k_fft_r2c_x<T, N, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xs);
+    cudaFuncSetAttribute(k_fft_c2r_x<T, N, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xs);
+    cudaFuncSetAttribute(k_fft_strided<T, N, PASS_FWD, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss);
+    cudaFuncSetAttribute(k_fft_strided<T, N, PASS_INV, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss);
+    cudaFuncSetAttribute(k_fft_strided<T, N, PASS_CONV, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sc);
   }
   const int xgrid = (int)((nrows / 2 + C::XP - 1) / C::XP);
   const int ntx = (ncol + C::SB - 1) / C::SB;
   const int sgrid = N * ntx;
 
   prof_begin(prof, PK_R2C_X, s);
-  k_fft_r2c_x<T, N><<<xgrid, xpass_threads<N>(), xs, s>>>(src, H, nrows, RS, tw);
+  k_fft_r2c_x<T, N, V><<<xgrid, xpass_threads<N, V>(), xs, s>>>(src, H, nrows, RS, tw);
   prof_end(prof, PK_R2C_X, s);
   // y-pass: lines (z, kx); element stride RS; outer (z) stride N*RS
   prof_begin(prof, PK_FFT_Y_FWD, s);
-  k_fft_strided<T, N, PASS_FWD><<<sgrid, strided_threads<N>(), ss, s>>>(H, RS, (int64_t)N * RS, ncol, ntx, tw,
+  k_fft_strided<T, N, PASS_FWD, V><<<sgrid, strided_threads<N, V>(), ss, s>>>(H, RS, (int64_t)N * RS, ncol, ntx, tw,
                                                                        kf, (T)l_mfp, norm);
   prof_end(prof, PK_FFT_Y_FWD, s);
   // z-pass: lines (y, kx); element stride N*RS; outer (y) stride RS
   prof_begin(prof, PK_FFT_Z_CONV, s);
-  k_fft_strided<T, N, PASS_CONV><<<sgrid, strided_threads<N>(), sc, s>>>(H, (int64_t)N * RS, RS, ncol, ntx, tw,
+  k_fft_strided<T, N, PASS_CONV, V><<<sgrid, strided_threads<N, V>(), sc, s>>>(H, (int64_t)N * RS, RS, ncol, ntx, tw,
                                                                         kf, (T)l_mfp, norm);
   prof_end(prof, PK_FFT_Z_CONV, s);
   prof_begin(prof, PK_FFT_Y_INV, s);
-  k_fft_strided<T, N, PASS_INV><<<sgrid, strided_threads<N>(), ss, s>>>(H, RS, (int64_t)N * RS, ncol, ntx, tw,
+  k_fft_strided<T, N, PASS_INV, V><<<sgrid, strided_threads<N, V>(), ss, s>>>(H, RS, (int64_t)N * RS, ncol, ntx, tw,
                                                                        kf, (T)l_mfp, norm);
   prof_end(prof, PK_FFT_Y_INV, s);
   prof_begin(prof, PK_C2R_X, s);
-  k_fft_c2r_x<T, N><<<xgrid, xpass_threads<N>(), xs, s>>>(H, J, nrows, RS, tw, status, krange);
+  k_fft_c2r_x<T, N, V><<<xgrid, xpass_threads<N, V>(), xs, s>>>(H, J, nrows, RS, tw, status, krange);
   prof_end(prof, PK_C2R_X, s);
   return cudaGetLastError();
 }

@@ -5,9 +5,19 @@ namespace amber {
 
 cudaError_t radiation_field_f32(int n, const float* src, float* J, void* H, const void* tw, double box, double l_mfp,
                                unsigned int* status, cudaStream_t s, FftProfile* prof,
-                               SortCtrl* krange) {
+                               SortCtrl* krange, int variant) {
   auto* h = reinterpret_cast<cpx<float>*>(H);
   auto* w = reinterpret_cast<const cpx<float>*>(tw);
+  if (variant == 1) {
+    switch (n) {
+      case 128: return radiation_field_n<float, 128, 1>(src, J, h, w, box, l_mfp, status, s, prof, krange);
+      case 256: return radiation_field_n<float, 256, 1>(src, J, h, w, box, l_mfp, status, s, prof, krange);
+      case 512: return radiation_field_n<float, 512, 1>(src, J, h, w, box, l_mfp, status, s, prof, krange);
+      case 1024: return radiation_field_n<float, 1024, 1>(src, J, h, w, box, l_mfp, status, s, prof, krange);
+      default: return cudaErrorInvalidValue;
+    }
+  }
+  if (variant != 0) return cudaErrorInvalidValue;
   switch (n) {
     case 4: return radiation_field_n<float, 4>(src, J, h, w, box, l_mfp, status, s, prof, krange);
     case 8: return radiation_field_n<float, 8>(src, J, h, w, box, l_mfp, status, s, prof, krange);

@@ -37,8 +37,10 @@
 
 namespace amber {
 
-template <typename SRC> constexpr int max_passes() {
-  return (8 * (int)sizeof(typename KeyOf<SRC>::K) + KeyOf<SRC>::RB - 1) / KeyOf<SRC>::RB;
+// RB: digit width in bits (KeyOf<SRC>::RB by default; FP32 keys also have an
+// 8-bit instantiation the autotuner can choose).
+template <typename SRC, int RB = KeyOf<SRC>::RB> constexpr int max_passes() {
+  return (8 * (int)sizeof(typename KeyOf<SRC>::K) + RB - 1) / RB;
 }
 
 __device__ __forceinline__ unsigned lanemask_lt() {
@@ -76,12 +78,12 @@ __global__ void __launch_bounds__(256) k_key_range(const SRC* __restrict__ J, in
   if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) raise_status(status, AMBER_ERR_NONFINITE);
 }
 
-template <typename SRC>
+template <typename SRC, int RB>
 __global__ void __launch_bounds__(256) k_sort_histogram(const SRC* __restrict__ J, int64_t n,
                                                         SortCtrl* __restrict__ ctrl,
                                                         uint32_t* __restrict__ lb0, int64_t lb0_words) {
   using K = typename KeyOf<SRC>::K;
-  constexpr int RB = KeyOf<SRC>::RB, R = 1 << RB, P = max_passes<SRC>();
+  constexpr int R = 1 << RB, P = max_passes<SRC, RB>();
   constexpr int V = 16 / sizeof(SRC);  // elements per 16-byte load
   __shared__ uint32_t h[P][R];
   for (int i = threadIdx.x; i < P * R; i += blockDim.x) (&h[0][0])[i] = 0;
@@ -136,10 +138,10 @@ __global__ void __launch_bounds__(256) k_sort_histogram(const SRC* __restrict__ 
 }
 
 // One CTA: exclusive scan of each digit histogram, and the pass count.
-template <typename SRC>
+template <typename SRC, int RB>
 __global__ void __launch_bounds__(256) k_sort_offsets(SortCtrl* __restrict__ ctrl) {
   using K = typename KeyOf<SRC>::K;
-  constexpr int RB = KeyOf<SRC>::RB, R = 1 << RB, P = max_passes<SRC>();
+  constexpr int R = 1 << RB, P = max_passes<SRC, RB>();
   __shared__ uint32_t wsum[8];
   __shared__ uint32_t carry;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -184,10 +186,11 @@ __global__ void __launch_bounds__(256) k_sort_offsets(SortCtrl* __restrict__ ctr
 // order, summed per tile into tile_mass and checked.  The last needed pass writes
 // only the payloads (to the final arrays).
 // ---------------------------------------------------------------------------
-template <typename SRC, bool FIRST, bool MASS, bool MATCH>
+template <typename SRC, int RB, bool FIRST, bool MASS, bool MATCH>
 __global__ void __launch_bounds__(kSortThreads, AMBER_SORT_MINB) k_sort_pass(const PassArgs a) {
   using K = typename KeyOf<SRC>::K;
-  constexpr int RB = KeyOf<SRC>::RB, R = 1 << RB, DPT = R / kSortThreads;  // digits per thread
+  constexpr int R = 1 << RB, DPT = R / kSortThreads;  // digits per thread
+  static_assert(DPT >= 1 && R <= kMaxRadix, "digit width");
   constexpr int NW = kSortThreads / 32;
   const int npasses = a.ctrl->npasses;
   if (a.pass >= npasses) return;  // the key range needs fewer digits
@@ -438,8 +441,8 @@ __global__ void __launch_bounds__(kSortThreads, AMBER_SORT_MINB) k_sort_pass(con
 // ---------------------------------------------------------------------------
 // Host side.
 // ---------------------------------------------------------------------------
-template <typename SRC> static size_t pass_smem(bool mass) {
-  constexpr int R = 1 << KeyOf<SRC>::RB;
+template <typename SRC, int RB> static size_t pass_smem(bool mass) {
+  constexpr int R = 1 << RB;
   return (size_t)kTile * sizeof(typename KeyOf<SRC>::K) + (size_t)kTile * 4 * (mass ? 2 : 1) +
          (size_t)(kSortThreads / 32) * R * 4 + 2 * R * 4;
 }
@@ -447,31 +450,32 @@ template <typename SRC> static size_t pass_smem(bool mass) {
 int64_t sort_tiles(int64_t n) { return (n + kTile - 1) / kTile; }
 size_t sort_lookback_words(int64_t n) { return (size_t)sort_tiles(n) * kMaxRadix; }
 
-template <typename SRC, bool FIRST, bool MASS, bool MATCH>
+template <typename SRC, int RB, bool FIRST, bool MASS, bool MATCH>
 static void launch_pass_v(const PassArgs& a, int64_t tiles, cudaStream_t s) {
-  const size_t smem = pass_smem<SRC>(MASS);
+  const size_t smem = pass_smem<SRC, RB>(MASS);
   static std::atomic<unsigned long long> attr{0};  // per instantiation and device
   if (first_use_on_device(attr))
-    cudaFuncSetAttribute(k_sort_pass<SRC, FIRST, MASS, MATCH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(k_sort_pass<SRC, RB, FIRST, MASS, MATCH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem);
-  k_sort_pass<SRC, FIRST, MASS, MATCH><<<(unsigned)tiles, kSortThreads, smem, s>>>(a);
+  k_sort_pass<SRC, RB, FIRST, MASS, MATCH><<<(unsigned)tiles, kSortThreads, smem, s>>>(a);
 }
 
 // Digit peers by ballots (one per digit bit) or by warp match; measured on
 // GB300 the ballots are faster (35.2 vs 37.7 ms for the three passes at
-// 1024^3).  AMBER_SORT_RANK=ballot|match picks, ballot by default.
-static bool rank_by_match() {
-  static const bool m = [] {
+// 1024^3).  The caller (the context's tuning) picks; AMBER_SORT_RANK=
+// ballot|match overrides it.
+static int rank_env() {
+  static const int m = [] {
     const char* v = getenv("AMBER_SORT_RANK");
-    return v && strcmp(v, "match") == 0;
+    return !v ? -1 : strcmp(v, "match") == 0 ? 1 : strcmp(v, "ballot") == 0 ? 0 : -1;
   }();
   return m;
 }
 
-template <typename SRC, bool FIRST, bool MASS>
-static void launch_pass(const PassArgs& a, int64_t tiles, cudaStream_t s) {
-  if (rank_by_match()) launch_pass_v<SRC, FIRST, MASS, true>(a, tiles, s);
-  else launch_pass_v<SRC, FIRST, MASS, false>(a, tiles, s);
+template <typename SRC, int RB, bool FIRST, bool MASS>
+static void launch_pass(const PassArgs& a, int64_t tiles, cudaStream_t s, bool match) {
+  if (match) launch_pass_v<SRC, RB, FIRST, MASS, true>(a, tiles, s);
+  else launch_pass_v<SRC, RB, FIRST, MASS, false>(a, tiles, s);
 }
 
 cudaError_t sort_ctrl_reset(SortCtrl* ctrl, cudaStream_t s) {
@@ -480,12 +484,13 @@ cudaError_t sort_ctrl_reset(SortCtrl* ctrl, cudaStream_t s) {
   return cudaMemsetAsync(&ctrl->kmin, 0xff, sizeof(ctrl->kmin), s);
 }
 
-template <typename SRC>
-cudaError_t rank_impl(const SortWork& w, const SRC* J, int64_t n, uint32_t* order, const float* mass_in,
-                      float* mass_out, unsigned long long* tile_mass, bool range_ready, unsigned int* status,
-                      cudaStream_t s, FftProfile* prof, unsigned int spin_limit) {
+template <typename SRC, int RB>
+static cudaError_t rank_impl_rb(const SortWork& w, const SRC* J, int64_t n, uint32_t* order, const float* mass_in,
+                                float* mass_out, unsigned long long* tile_mass, bool range_ready,
+                                unsigned int* status, cudaStream_t s, FftProfile* prof, unsigned int spin_limit,
+                                bool match) {
   using K = typename KeyOf<SRC>::K;
-  constexpr int R = 1 << KeyOf<SRC>::RB, P = max_passes<SRC>();
+  constexpr int R = 1 << RB, P = max_passes<SRC, RB>();
   const bool with_mass = mass_in != nullptr;
   const int64_t tiles = sort_tiles(n);
   const int64_t lbw = tiles * R;  // words per look-back region used
@@ -503,8 +508,8 @@ cudaError_t rank_impl(const SortWork& w, const SRC* J, int64_t n, uint32_t* orde
     int grid = (int)std::min<int64_t>((n / (16 / (int)sizeof(SRC)) + 255) / 256, (int64_t)w.num_sms * 8);
     if (grid < 1) grid = 1;
     if (!range_ready) k_key_range<SRC><<<grid, 256, 0, s>>>(J, n, ctrl, status);
-    k_sort_histogram<SRC><<<grid, 256, 0, s>>>(J, n, ctrl, lbA, lbw);
-    k_sort_offsets<SRC><<<1, 256, 0, s>>>(ctrl);
+    k_sort_histogram<SRC, RB><<<grid, 256, 0, s>>>(J, n, ctrl, lbA, lbw);
+    k_sort_offsets<SRC, RB><<<1, 256, 0, s>>>(ctrl);
   }
   prof_end(prof, PK_SORT_HIST, s);
 
@@ -535,11 +540,11 @@ cudaError_t rank_impl(const SortWork& w, const SRC* J, int64_t n, uint32_t* orde
     a.ahead = (uint32_t)w.num_sms;  // a third of the resident wave: measured best
     prof_begin(prof, PK_SORT_PASS, s);
     if (p == 0) {
-      if (with_mass) launch_pass<SRC, true, true>(a, tiles, s);
-      else launch_pass<SRC, true, false>(a, tiles, s);
+      if (with_mass) launch_pass<SRC, RB, true, true>(a, tiles, s, match);
+      else launch_pass<SRC, RB, true, false>(a, tiles, s, match);
     } else {
-      if (with_mass) launch_pass<SRC, false, true>(a, tiles, s);
-      else launch_pass<SRC, false, false>(a, tiles, s);
+      if (with_mass) launch_pass<SRC, RB, false, true>(a, tiles, s, match);
+      else launch_pass<SRC, RB, false, false>(a, tiles, s, match);
     }
     prof_end(prof, PK_SORT_PASS, s);
     kin = a.kout;
@@ -549,12 +554,34 @@ cudaError_t rank_impl(const SortWork& w, const SRC* J, int64_t n, uint32_t* orde
   return cudaGetLastError();
 }
 
+template <typename SRC>
+cudaError_t rank_impl(const SortWork& w, const SRC* J, int64_t n, uint32_t* order, const float* mass_in,
+                      float* mass_out, unsigned long long* tile_mass, bool range_ready, unsigned int* status,
+                      cudaStream_t s, FftProfile* prof, unsigned int spin_limit, int digit_bits, int match) {
+  const int env = rank_env();
+  const bool m = env >= 0 ? env == 1 : match == 1;
+  if (digit_bits == 0) digit_bits = KeyOf<SRC>::RB;
+  if constexpr (sizeof(SRC) == 4) {
+    if (digit_bits == 8)
+      return rank_impl_rb<SRC, 8>(w, J, n, order, mass_in, mass_out, tile_mass, range_ready, status, s, prof,
+                                  spin_limit, m);
+    if (digit_bits == 9)
+      return rank_impl_rb<SRC, 9>(w, J, n, order, mass_in, mass_out, tile_mass, range_ready, status, s, prof,
+                                  spin_limit, m);
+  } else {
+    if (digit_bits == 8)
+      return rank_impl_rb<SRC, 8>(w, J, n, order, mass_in, mass_out, tile_mass, range_ready, status, s, prof,
+                                  spin_limit, m);
+  }
+  return cudaErrorInvalidValue;
+}
+
 template cudaError_t rank_impl<float>(const SortWork&, const float*, int64_t, uint32_t*, const float*, float*,
                                       unsigned long long*, bool, unsigned int*, cudaStream_t, FftProfile*,
-                                      unsigned int);
+                                      unsigned int, int, int);
 template cudaError_t rank_impl<double>(const SortWork&, const double*, int64_t, uint32_t*, const float*, float*,
                                        unsigned long long*, bool, unsigned int*, cudaStream_t, FftProfile*,
-                                       unsigned int);
+                                       unsigned int, int, int);
 
 // Failure-detection hook: the look-back wait on a word nothing publishes.
 __global__ void k_wait_never(const uint32_t* __restrict__ word, unsigned int* __restrict__ status,

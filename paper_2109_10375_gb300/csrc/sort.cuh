@@ -72,11 +72,14 @@ cudaError_t sort_ctrl_reset(SortCtrl* ctrl, cudaStream_t s);
 // mass_out) NULL the results stay in idxA/massA when the needed pass count
 // is odd and in idxB/massB when it is even (read it from ctrl->npasses).  range_ready:
 // ctrl was reset and its key range already folded in (by the intensity
-// kernel), so the range pass is skipped.
+// kernel), so the range pass is skipped.  digit_bits: 9 or 8 for FP32 keys, 8
+// for FP64 (0: the default, 9 / 8); match: 1 digit peers by warp match, 0 by
+// ballots (default).  The environment variable AMBER_SORT_RANK=ballot|match
+// overrides match.
 template <typename SRC>
 cudaError_t rank_impl(const SortWork& w, const SRC* J, int64_t n, uint32_t* order, const float* mass_in,
                       float* mass_out, unsigned long long* tile_mass, bool range_ready, unsigned int* status,
-                      cudaStream_t s, FftProfile* prof, unsigned int spin_limit);
+                      cudaStream_t s, FftProfile* prof, unsigned int spin_limit, int digit_bits = 0, int match = 0);
 
 cudaError_t wait_timeout_test(uint32_t* zero_word, unsigned int* status, unsigned int spin_limit, cudaStream_t s);
 
