@@ -291,8 +291,9 @@ int amber_profile_kinds(void);
 int amber_profile_read(amber_ctx *ctx, int kind, const char **name, double *total_ms, int64_t *launches);
 
 /* Digit passes the last ranking needed (diagnostic; synchronises the
- * context's last stream).  The sort runs on key - min(key) with 9-bit digits,
- * so an intensity field spanning few octaves needs 3 passes, at most 4. */
+ * context's last stream).  The sort runs on key - min(key) with 9- or 8-bit
+ * digits (amber_tuning_t), so an intensity field spanning few octaves (27
+ * bits) needs 3 or 4 passes; at most 4 for FP32 keys. */
 int amber_sort_passes(amber_ctx *ctx, int *out_passes);
 
 /* Tomographic abundance matching (Sec. 3.4.2 names matching over several

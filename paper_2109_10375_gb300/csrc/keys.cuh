@@ -32,7 +32,8 @@ __device__ __forceinline__ uint64_t enc_desc(double v, bool& bad) {
 }
 
 template <typename SRC> struct KeyOf;
-// FP32 intensities: 9-bit digits over the 32-bit key (at most 4 passes).
+// FP32 intensities: 9-bit digits over the 32-bit key by default (at most 4
+// passes); the sort also has 8-bit instances (see max_passes in sort.cu).
 template <> struct KeyOf<float> { using K = uint32_t; static constexpr int RB = 9; };
 // FP64 intensities (n <= 256): 8-bit digits over the 64-bit key.
 template <> struct KeyOf<double> { using K = uint64_t; static constexpr int RB = 8; };

@@ -6,7 +6,8 @@
 //
 //   k_key_range      : min and max key (the sort runs on key - min, so a
 //                      field whose intensities span a few octaves needs
-//                      27 bits, i.e. three 9-bit digits instead of four)
+//                      27 bits: three 9-bit digits or four 8-bit ones
+//                      instead of four or more)
 //   k_sort_histogram : one read of the intensities; counts of every digit
 //                      position at once (shared-memory counters, one add per
 //                      warp when all 32 lanes share a digit)

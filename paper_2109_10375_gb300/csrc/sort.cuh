@@ -23,7 +23,7 @@ constexpr int kSortThreads = AMBER_SORT_THREADS;  // 256 or 512 (divides the rad
 constexpr int kItems = AMBER_SORT_ITEMS;
 constexpr int kTile = kSortThreads * kItems;  // 4096 keys per tile
 constexpr int kLookWindow = 8;                // predecessors read per look-back round trip
-constexpr int kMaxRadix = 512;                // 9-bit digits
+constexpr int kMaxRadix = 512;                // digits of up to 9 bits
 
 struct SortWork {
   void* keysA;
