@@ -582,7 +582,9 @@ def run_amber(args):
             raise RuntimeError(f"device status after autotuning: {B.status_string(st)}")
     del S_d, m_d, z_d, z_h, S_h, m_h
 
-    launches_per_step = sum(v[1] for v in prof.values()) / args.steps
+    # each timed bracket is one kernel launch, except the histogram's, which
+    # also holds the one-CTA digit-offset scan (k_sort_offsets)
+    launches_per_step = (sum(v[1] for v in prof.values()) + prof["sort_histogram"][1]) / args.steps
     ab = algorithmic_bytes(n, passes)
     kernels = {}
     for k, (ms_k, cnt) in prof.items():
