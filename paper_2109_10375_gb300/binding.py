@@ -370,8 +370,12 @@ class Context:
                "amber_autotune")
         return t.as_dict()
 
-    def set_tuning(self, n: int, fft_variant: int = 0, sort_digit_bits: int = 9, sort_match: int = 0):
-        t = amber_tuning_t(n, fft_variant, sort_digit_bits, sort_match, 0)
+    def set_tuning(self, n: int, fft_variant=None, sort_digit_bits=None, sort_match=None):
+        """Set the choices for size n; a choice left as None keeps its current value."""
+        cur = self.get_tuning(n)
+        t = amber_tuning_t(n, cur["fft_variant"] if fft_variant is None else fft_variant,
+                           cur["sort_digit_bits"] if sort_digit_bits is None else sort_digit_bits,
+                           cur["sort_match"] if sort_match is None else sort_match, 0)
         _check(lib.amber_set_tuning(self._h, C.byref(t)), "amber_set_tuning")
 
     def get_tuning(self, n: int) -> dict:
