@@ -14,6 +14,11 @@
  *    `box` (h^-1 Mpc); n is a power of two in [4, 1024].
  *  - Pointers named d_* are DEVICE pointers owned by the caller (any CUDA
  *    allocation on the context's device).  The library never frees them.
+ *    Each must start on a multiple of its element size (4 bytes for float
+ *    and uint32 arrays, 8 for double); a misaligned pointer returns
+ *    AMBER_ERR_INVALID_ARG with nothing enqueued.  No wider alignment is
+ *    needed: an array may start anywhere on its element size (a view
+ *    such as J + 1 is fine).
  *  - `stream` is a cudaStream_t passed as void*; NULL means the legacy default
  *    stream.  All device work is asynchronous on that stream; no call
  *    allocates device memory after amber_create.
@@ -394,10 +399,25 @@ int amber_power_bins(int n, int *nbins);
  * d_Pab_opt (Re P_ab; zero without b), d_modes the number of modes.  With
  * these, Delta^2 = k^3 P / (2 pi^2), b_ab = sqrt(P_aa / P_bb) and
  * r_ab = P_ab / sqrt(P_aa P_bb) (Eqs. bias, rcc).  FP32 transforms, FP64 shell
- * sums.  d_b_opt may be NULL (auto spectrum of a only).  Uses the context's
+ * sums.  d_b_opt may be NULL (auto spectrum of a only).  amber_power_derived
+ * forms Delta^2, b and r on the device.  Uses the context's
  * transform and sort buffers; n^3 <= max_cells (else AMBER_ERR_CAPACITY). */
 int amber_power_spectrum(amber_ctx *ctx, const float *d_a, const float *d_b_opt, int n, double box, double *d_k,
                          double *d_Paa, double *d_Pbb_opt, double *d_Pab_opt, double *d_modes, void *stream);
+
+/* Statistics derived from amber_power_spectrum's shell averages, FP64 on the
+ * device, per shell b < nbins (Sec. 2.3.1):
+ *   d_D2aa[b] = k^3 P_aa / (2 pi^2)           (Eq. Dk; d_D2bb_opt likewise for b)
+ *   d_bias_opt[b] = sqrt(P_aa / P_bb)          (Eq. bias)
+ *   d_r_opt[b] = P_ab / sqrt(P_aa P_bb)        (Eq. rcc)
+ * Inputs d_k, d_Paa, d_Pbb_opt, d_Pab_opt and outputs are device arrays of
+ * nbins doubles (caller-owned; amber_power_bins gives nbins).  The outputs
+ * for b need d_Pbb_opt, and d_r_opt needs d_Pab_opt too (else
+ * AMBER_ERR_INVALID_ARG).  A shell without modes (P = 0) gets Delta^2 = 0
+ * and NaN ratios. */
+int amber_power_derived(amber_ctx *ctx, const double *d_k, const double *d_Paa, const double *d_Pbb_opt,
+                        const double *d_Pab_opt, int nbins, double *d_D2aa, double *d_D2bb_opt, double *d_bias_opt,
+                        double *d_r_opt, void *stream);
 
 /* Test hook for failure detection: runs the production lookback wait on a
  * status array nothing ever publishes, with `spin_limit` iterations, and
@@ -416,6 +436,9 @@ int amber_test_wait_timeout(amber_ctx *ctx, unsigned int spin_limit, void *strea
  *    nothing.
  *  - The first call on each device (that device current) looks up the
  *    array's device address; make that first call before any stream capture.
+ *    The address is kept for the life of the process, so this entry point is
+ *    not valid after a cudaDeviceReset (or any teardown of the device's
+ *    primary context) in the same process.
  *  - Every call shares the one array and clears what must start at zero; calls
  *    whose GPU work overlaps (other streams, other threads) race and must not
  *    be issued.  Runs on the current device, asynchronously on `stream`.

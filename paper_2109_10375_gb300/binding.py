@@ -33,7 +33,7 @@ EXPORTED = [
     "amber_delta_z", "amber_epsilon_z_pdf", "amber_power_bins", "amber_power_spectrum",
     "amber_lpt_displacement", "amber_mesh_density", "amber_esf_fcoll", "amber_sigma2_tophat",
     "amber_solve_tomographic", "amber_autotune", "amber_set_tuning", "amber_get_tuning",
-    "amber_rank_noalloc",
+    "amber_rank_noalloc", "amber_power_derived",
 ]
 
 
@@ -121,6 +121,7 @@ def _load():
         "amber_set_tuning": (i32, [vp, C.POINTER(amber_tuning_t)]),
         "amber_get_tuning": (i32, [vp, i32, C.POINTER(amber_tuning_t)]),
         "amber_rank_noalloc": (i32, [vp, i64, vp, vp, vp]),
+        "amber_power_derived": (i32, [vp, vp, vp, vp, vp, i32, vp, vp, vp, vp, vp]),
         "amber_test_wait_timeout": (i32, [vp, C.c_uint, vp]),
     }
     for name, (res, args) in sig.items():
@@ -170,16 +171,6 @@ def power_bins(n: int) -> int:
     return out.value
 
 
-def derived_spectra(s: dict) -> dict:
-    """Delta^2 (Eq. Dk), bias b_ab (Eq. bias) and cross-correlation r_ab (Eq. rcc)
-    from power_spectrum's output (host numpy; shells without modes give nan)."""
-    import numpy as np
-    k, Paa, Pbb, Pab = (s[key].cpu().numpy() for key in ("k", "Paa", "Pbb", "Pab"))
-    with np.errstate(invalid="ignore", divide="ignore"):
-        return {"k": k, "Delta2_aa": k ** 3 * Paa / (2 * np.pi ** 2), "Delta2_bb": k ** 3 * Pbb / (2 * np.pi ** 2),
-                "bias": np.sqrt(Paa / Pbb), "r": Pab / np.sqrt(Paa * Pbb)}
-
-
 def history_coeffs(h: amber_history_t):
     out = (C.c_double * 3)()
     _check(lib.amber_history_coeffs(C.byref(h), out), "amber_history_coeffs")
@@ -202,7 +193,12 @@ def workspace_bytes(max_cells: int) -> int:
 
 
 def _ptr(t):
-    return None if t is None else C.c_void_p(t.data_ptr())
+    """Raw data pointer of a tensor the library reads or writes as a flat array."""
+    if t is None:
+        return None
+    if not t.is_contiguous():
+        raise ValueError("libamber takes contiguous arrays; pass .contiguous()")
+    return C.c_void_p(t.data_ptr())
 
 
 def _stream(stream):
@@ -225,7 +221,7 @@ class Batch:
         self._keep = (list(ctxs), list(items))
         arr = (amber_batch_item * len(items))()
         for i, (S, m, box, l, h, z) in enumerate(items):
-            arr[i].d_src, arr[i].d_mass, arr[i].d_zre = S.data_ptr(), m.data_ptr(), z.data_ptr()
+            arr[i].d_src, arr[i].d_mass, arr[i].d_zre = _ptr(S).value, _ptr(m).value, _ptr(z).value
             arr[i].params = params(S.shape[0], box, l, h)
         hs = (C.c_void_p * len(ctxs))(*[c._h.value for c in ctxs])
         self._h = C.c_void_p()
@@ -449,6 +445,19 @@ class Context:
         _check(lib.amber_epsilon_z_pdf(self._h, _ptr(z), _ptr(z_ref), z.numel(), lo, hi, nbins, _ptr(counts),
                                        _ptr(mom), _stream(stream)), "amber_epsilon_z_pdf")
         return counts, mom
+
+    def derived_spectra(self, s: dict, stream=None) -> dict:
+        """Delta^2 (Eq. Dk), bias (Eq. bias) and cross-correlation r (Eq. rcc) per
+        shell from power_spectrum's output, formed on the device (device tensors)."""
+        import torch
+        nb = s["k"].numel()
+        out = {key: torch.empty(nb, dtype=torch.float64, device=s["k"].device)
+               for key in ("Delta2_aa", "Delta2_bb", "bias", "r")}
+        _check(lib.amber_power_derived(self._h, _ptr(s["k"]), _ptr(s["Paa"]), _ptr(s["Pbb"]), _ptr(s["Pab"]), nb,
+                                       _ptr(out["Delta2_aa"]), _ptr(out["Delta2_bb"]), _ptr(out["bias"]),
+                                       _ptr(out["r"]), _stream(stream)), "amber_power_derived")
+        out["k"] = s["k"]
+        return out
 
     def power_spectrum(self, a, b=None, box: float = 1.0, stream=None):
         """Shell spectra (Eqs. Pk, Dk, bias, rcc) of n^3 float fields: dict of

@@ -253,6 +253,15 @@ struct DeviceGuard {
 
 bool is_pow2_in(int n, int lo, int hi) { return n >= lo && n <= hi && (n & (n - 1)) == 0; }
 
+// A device array must start on a multiple of its element size (NULL passes:
+// optional arguments are checked for presence separately).  Kernels need no
+// more than that: wider vector loads check their own alignment.
+template <typename T> bool elem_aligned(const T* p) { return (reinterpret_cast<uintptr_t>(p) % sizeof(T)) == 0; }
+bool all_aligned() { return true; }
+template <typename T, typename... R> bool all_aligned(const T* p, const R*... rest) {
+  return elem_aligned(p) && all_aligned(rest...);
+}
+
 int cuda_status(cudaError_t e) {
   if (e == cudaSuccess) return AMBER_OK;
   return AMBER_ERR_CUDA;
@@ -394,13 +403,16 @@ int amber_destroy(amber_ctx* c) {
   return AMBER_OK;
 }
 
-static int rf_args_ok(amber_ctx* c, const void* src, int n, double box, double l, const void* J, int nmax) {
-  if (!c || !src || !J) return AMBER_ERR_INVALID_ARG;
+extern "C++" {
+template <typename T>
+static int rf_args_ok(amber_ctx* c, const T* src, int n, double box, double l, const T* J, int nmax) {
+  if (!c || !src || !J || !all_aligned(src, J)) return AMBER_ERR_INVALID_ARG;
   if (!is_pow2_in(n, 4, 1024) || !(box > 0.0) || !std::isfinite(box) || !(l > 0.0) || !std::isfinite(l))
     return AMBER_ERR_INVALID_ARG;
   if (n > nmax) return AMBER_ERR_CAPACITY;
   return AMBER_OK;
 }
+}  // extern "C++"
 
 int amber_radiation_field(amber_ctx* c, const float* d_src, int n, double box, double l_mfp, float* d_J,
                           void* stream) {
@@ -437,7 +449,7 @@ int amber_power_bins(int n, int* nbins) {
 }
 
 int amber_delta_z(amber_ctx* c, const float* d_z, int64_t ncells, float* d_out, double* d_zbar_opt, void* stream) {
-  if (!c || !d_z || !d_out || ncells < 1) return AMBER_ERR_INVALID_ARG;
+  if (!c || !d_z || !d_out || ncells < 1 || !all_aligned(d_z, d_out, d_zbar_opt)) return AMBER_ERR_INVALID_ARG;
   std::lock_guard<std::mutex> lk(c->mu);
   DeviceGuard g(c->device);
   cudaStream_t s = (cudaStream_t)stream;
@@ -448,7 +460,8 @@ int amber_delta_z(amber_ctx* c, const float* d_z, int64_t ncells, float* d_out, 
 
 int amber_epsilon_z_pdf(amber_ctx* c, const float* d_z, const float* d_zref, int64_t ncells, double lo, double hi,
                         int nbins, unsigned long long* d_counts, double* d_moments_opt, void* stream) {
-  if (!c || !d_z || !d_zref || !d_counts || ncells < 1) return AMBER_ERR_INVALID_ARG;
+  if (!c || !d_z || !d_zref || !d_counts || ncells < 1 || !all_aligned(d_z, d_zref, d_counts, d_moments_opt))
+    return AMBER_ERR_INVALID_ARG;
   if (!std::isfinite(lo) || !std::isfinite(hi) || !(hi > lo) || nbins < 1 || nbins > 16000)
     return AMBER_ERR_INVALID_ARG;
   std::lock_guard<std::mutex> lk(c->mu);
@@ -461,6 +474,7 @@ int amber_epsilon_z_pdf(amber_ctx* c, const float* d_z, const float* d_zref, int
 int amber_power_spectrum(amber_ctx* c, const float* d_a, const float* d_b_opt, int n, double box, double* d_k,
                          double* d_Paa, double* d_Pbb_opt, double* d_Pab_opt, double* d_modes, void* stream) {
   if (!c || !d_a || !d_k || !d_Paa || !d_modes) return AMBER_ERR_INVALID_ARG;
+  if (!all_aligned(d_a, d_b_opt, d_k, d_Paa, d_Pbb_opt, d_Pab_opt, d_modes)) return AMBER_ERR_INVALID_ARG;
   if (!is_pow2_in(n, 4, 1024) || !(box > 0.0) || !std::isfinite(box)) return AMBER_ERR_INVALID_ARG;
   if (n > c->plan.n32) return AMBER_ERR_CAPACITY;
   std::lock_guard<std::mutex> lk(c->mu);
@@ -479,6 +493,22 @@ int amber_power_spectrum(amber_ctx* c, const float* d_a, const float* d_b_opt, i
     e = power_impl(Ha, Hb, n, box, reinterpret_cast<double*>(c->ws + p.off_pow), d_k, d_Paa, d_Pbb_opt, d_Pab_opt,
                    d_modes, c->num_sms, s);
   return cuda_status(e);
+}
+
+int amber_power_derived(amber_ctx* c, const double* d_k, const double* d_Paa, const double* d_Pbb_opt,
+                        const double* d_Pab_opt, int nbins, double* d_D2aa, double* d_D2bb_opt, double* d_bias_opt,
+                        double* d_r_opt, void* stream) {
+  if (!c || !d_k || !d_Paa || !d_D2aa || nbins < 1 || nbins > kMaxPowerBins) return AMBER_ERR_INVALID_ARG;
+  if ((d_D2bb_opt || d_bias_opt || d_r_opt) && !d_Pbb_opt) return AMBER_ERR_INVALID_ARG;
+  if (d_r_opt && !d_Pab_opt) return AMBER_ERR_INVALID_ARG;
+  if (!all_aligned(d_k, d_Paa, d_Pbb_opt, d_Pab_opt, d_D2aa, d_D2bb_opt, d_bias_opt, d_r_opt))
+    return AMBER_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(c->mu);
+  DeviceGuard g(c->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  c->last_stream = s;
+  return cuda_status(power_derived_impl(d_k, d_Paa, d_Pbb_opt, d_Pab_opt, nbins, d_D2aa, d_D2bb_opt, d_bias_opt,
+                                        d_r_opt, s));
 }
 
 static LptWork lpt_work(amber_ctx* c, int n) {
@@ -564,7 +594,7 @@ int amber_sigma2_tophat(const double* k, const double* Delta2, int nk, double R,
 }
 
 int amber_rank(amber_ctx* c, const float* d_J, int64_t ncells, uint32_t* d_order, void* stream) {
-  if (!c || !d_J || !d_order || ncells < 1) return AMBER_ERR_INVALID_ARG;
+  if (!c || !d_J || !d_order || ncells < 1 || !all_aligned(d_J, d_order)) return AMBER_ERR_INVALID_ARG;
   if (ncells > c->max_cells) return AMBER_ERR_CAPACITY;
   std::lock_guard<std::mutex> lk(c->mu);
   DeviceGuard g(c->device);
@@ -575,7 +605,7 @@ int amber_rank(amber_ctx* c, const float* d_J, int64_t ncells, uint32_t* d_order
 }
 
 int amber_rank_f64(amber_ctx* c, const double* d_J, int64_t ncells, uint32_t* d_order, void* stream) {
-  if (!c || !d_J || !d_order || ncells < 1) return AMBER_ERR_INVALID_ARG;
+  if (!c || !d_J || !d_order || ncells < 1 || !all_aligned(d_J, d_order)) return AMBER_ERR_INVALID_ARG;
   if (ncells > c->plan.cells64) return AMBER_ERR_CAPACITY;
   std::lock_guard<std::mutex> lk(c->mu);
   DeviceGuard g(c->device);
@@ -587,7 +617,8 @@ int amber_rank_f64(amber_ctx* c, const double* d_J, int64_t ncells, uint32_t* d_
 
 int amber_assign_zre(amber_ctx* c, const uint32_t* d_order, const float* d_mass, int64_t ncells,
                      const amber_history_t* h, float* d_zre, double* d_F_opt, void* stream) {
-  if (!c || !d_order || !d_mass || !d_zre || ncells < 1) return AMBER_ERR_INVALID_ARG;
+  if (!c || !d_order || !d_mass || !d_zre || ncells < 1 || !all_aligned(d_order, d_mass, d_zre, d_F_opt))
+    return AMBER_ERR_INVALID_ARG;
   if (ncells > c->max_cells) return AMBER_ERR_CAPACITY;
   HistoryCoeffs hc;
   const int st = history_coeffs(h, &hc);
@@ -600,14 +631,17 @@ int amber_assign_zre(amber_ctx* c, const uint32_t* d_order, const float* d_mass,
                                  &c->prof, kSpinLimit));
 }
 
-static int solve_args(amber_ctx* c, const void* src, const float* mass, const amber_params_t* p, const float* zre,
+extern "C++" {
+template <typename T>
+static int solve_args(amber_ctx* c, const T* src, const float* mass, const amber_params_t* p, const float* zre,
                       int want_prec, int nmax, HistoryCoeffs* hc) {
-  if (!c || !src || !mass || !p || !zre) return AMBER_ERR_INVALID_ARG;
+  if (!c || !src || !mass || !p || !zre || !all_aligned(src, mass, zre)) return AMBER_ERR_INVALID_ARG;
   if (p->precision != want_prec) return AMBER_ERR_INVALID_ARG;
-  int st = rf_args_ok(c, src, p->n, p->box, p->l_mfp, zre, nmax);
+  int st = rf_args_ok(c, src, p->n, p->box, p->l_mfp, src, nmax);
   if (st) return st;
   return history_coeffs(&p->hist, hc);
 }
+}  // extern "C++"
 
 // Enqueue one FP32 solve on s (no locking, no validation).  With order_out
 // (and mass_rank_out) the sort leaves the rank order and the rank-order
@@ -721,6 +755,7 @@ int amber_solve(amber_ctx* c, const float* d_src, const float* d_mass, const amb
   HistoryCoeffs hc;
   int st = solve_args(c, d_src, d_mass, p, d_zre, 32, c ? c->plan.n32 : 0, &hc);
   if (st) return st;
+  if (!all_aligned(d_J_opt)) return AMBER_ERR_INVALID_ARG;
   std::lock_guard<std::mutex> lk(c->mu);
   DeviceGuard g(c->device);
   cudaStream_t s = (cudaStream_t)stream;
@@ -802,7 +837,8 @@ int amber_solve_ex(amber_ctx* c, const float* d_src, const float* d_mass, const 
   HistoryCoeffs hc;
   int st = solve_args(c, d_src, d_mass, p, d_zre, 32, c ? c->plan.n32 : 0, &hc);
   if (st) return st;
-  if (!d_order_out || !d_mass_rank_out) return AMBER_ERR_INVALID_ARG;
+  if (!d_order_out || !d_mass_rank_out || !all_aligned(d_J_opt, d_order_out, d_mass_rank_out))
+    return AMBER_ERR_INVALID_ARG;
   std::lock_guard<std::mutex> lk(c->mu);
   DeviceGuard g(c->device);
   cudaStream_t s = (cudaStream_t)stream;
@@ -812,7 +848,8 @@ int amber_solve_ex(amber_ctx* c, const float* d_src, const float* d_mass, const 
 
 int amber_assign_zre_ranked(amber_ctx* c, const uint32_t* d_order, const float* d_mass_rank, int64_t ncells,
                             const amber_history_t* h, float* d_zre, double* d_F_opt, void* stream) {
-  if (!c || !d_order || !d_mass_rank || !d_zre || ncells < 1) return AMBER_ERR_INVALID_ARG;
+  if (!c || !d_order || !d_mass_rank || !d_zre || ncells < 1 || !all_aligned(d_order, d_mass_rank, d_zre, d_F_opt))
+    return AMBER_ERR_INVALID_ARG;
   if (ncells > c->max_cells) return AMBER_ERR_CAPACITY;
   HistoryCoeffs hc;
   const int st = history_coeffs(h, &hc);
@@ -934,6 +971,7 @@ int amber_solve_f64(amber_ctx* c, const double* d_src, const float* d_mass, cons
   HistoryCoeffs hc;
   int st = solve_args(c, d_src, d_mass, p, d_zre, 64, c ? c->plan.n64 : 0, &hc);
   if (st) return st;
+  if (!all_aligned(d_J_opt)) return AMBER_ERR_INVALID_ARG;
   std::lock_guard<std::mutex> lk(c->mu);
   DeviceGuard g(c->device);
   cudaStream_t s = (cudaStream_t)stream;
@@ -1025,6 +1063,7 @@ int amber_source_field(amber_ctx* c, const float* d_delta, int64_t ncells, doubl
                        float* d_S, float* d_mass_opt, void* stream) {
   if (!c || !d_delta || !d_S || ncells < 1 || !std::isfinite(delta_c) || !(sigma_f > 0.0) || !std::isfinite(sigma_f))
     return AMBER_ERR_INVALID_ARG;
+  if (!all_aligned(d_delta, d_S, d_mass_opt)) return AMBER_ERR_INVALID_ARG;
   if (ncells > c->max_cells) return AMBER_ERR_CAPACITY;
   std::lock_guard<std::mutex> lk(c->mu);
   DeviceGuard g(c->device);

@@ -36,7 +36,8 @@ __global__ void __launch_bounds__(256) k_mass_reduce(const float* __restrict__ m
   bool bad = false;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t nvec = n / 4;
+  // 16-byte loads only from a 16-byte aligned array, else element by element
+  const int64_t nvec = (reinterpret_cast<uintptr_t>(mass) & 15) == 0 ? n / 4 : 0;
   for (int64_t v = gtid; v < nvec; v += stride) {
     const float4 m = reinterpret_cast<const float4*>(mass)[v];
     acc += mass_q64(m.x, bad) + mass_q64(m.y, bad) + mass_q64(m.z, bad) + mass_q64(m.w, bad);

@@ -52,7 +52,10 @@ using namespace amber;
 
 extern "C" int amber_rank_noalloc(const float* d_J, int64_t ncells, uint32_t* d_order, unsigned int* d_status_opt,
                                   void* stream) {
-  if (!d_J || !d_order || ncells < 1) return AMBER_ERR_INVALID_ARG;
+  // arrays start on their element size (checked before any CUDA call)
+  if (!d_J || !d_order || ncells < 1 || (reinterpret_cast<uintptr_t>(d_J) & 3) != 0 ||
+      (reinterpret_cast<uintptr_t>(d_order) & 3) != 0 || (reinterpret_cast<uintptr_t>(d_status_opt) & 3) != 0)
+    return AMBER_ERR_INVALID_ARG;
   if (ncells > kNoAllocMaxCells) return AMBER_ERR_CAPACITY;  // the fixed scratch holds 2^20 cells
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {

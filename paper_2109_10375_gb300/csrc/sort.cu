@@ -100,7 +100,10 @@ __global__ void __launch_bounds__(256) k_sort_histogram(const SRC* __restrict__ 
   bool bad = false;
   const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
   const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t nvec = n / V;
+  // 16-byte loads only from a 16-byte aligned array (a caller's view may start
+  // anywhere on its element size); otherwise every element takes the tail loop
+  const bool vec = (reinterpret_cast<uintptr_t>(J) & 15) == 0;
+  const int64_t nvec = vec ? n / V : 0;
   const int64_t vec_iters = (nvec + nthreads - 1) / nthreads;
   for (int64_t it = 0; it < vec_iters; ++it) {  // the same trip count on every lane
     const int64_t v = it * nthreads + gtid;

@@ -170,6 +170,32 @@ __global__ void k_power_final(const double* __restrict__ acc, int nb, double kf,
   }
 }
 
+// Derived shell statistics (Eqs. Dk, bias, rcc), FP64 per shell:
+// Delta^2 = k^3 P / (2 pi^2), b = sqrt(P_aa / P_bb), r = P_ab / sqrt(P_aa P_bb).
+// A shell without modes has P = 0 and gets Delta^2 = 0 and NaN ratios (0/0).
+__global__ void k_power_derived(const double* __restrict__ k, const double* __restrict__ Paa,
+                                const double* __restrict__ Pbb, const double* __restrict__ Pab, int nb,
+                                double* __restrict__ D2aa, double* __restrict__ D2bb, double* __restrict__ bias,
+                                double* __restrict__ r) {
+  const double inv2pi2 = 1.0 / (2.0 * 3.14159265358979323846 * 3.14159265358979323846);
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += gridDim.x * blockDim.x) {
+    const double kb = k[b], k3 = kb * kb * kb, a = Paa[b];
+    D2aa[b] = k3 * a * inv2pi2;
+    if (Pbb) {
+      const double q = Pbb[b];
+      if (D2bb) D2bb[b] = k3 * q * inv2pi2;
+      if (bias) bias[b] = sqrt(a / q);
+      if (r && Pab) r[b] = Pab[b] / sqrt(a * q);
+    }
+  }
+}
+
+cudaError_t power_derived_impl(const double* k, const double* Paa, const double* Pbb, const double* Pab, int nb,
+                               double* D2aa, double* D2bb, double* bias, double* r, cudaStream_t s) {
+  k_power_derived<<<(nb + 255) / 256, 256, 0, s>>>(k, Paa, Pbb, Pab, nb, D2aa, D2bb, bias, r);
+  return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------------------
 static int grid_for(int64_t n, int num_sms) {
   int64_t g = (n + 1023) / 1024;

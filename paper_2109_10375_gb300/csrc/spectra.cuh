@@ -32,4 +32,10 @@ cudaError_t epsilon_pdf_impl(const float* z, const float* zref, int64_t n, doubl
 cudaError_t power_impl(const void* Ha, const void* Hb, int n, double box, double* acc, double* k, double* Paa,
                        double* Pbb, double* Pab, double* modes, int num_sms, cudaStream_t s);
 
+// Delta^2 of a (and b) (Eq. Dk), bias (Eq. bias) and cross-correlation (Eq. rcc)
+// per shell from power_impl's outputs; Pbb/Pab and every output but D2aa may be
+// null (the ratios need Pbb).
+cudaError_t power_derived_impl(const double* k, const double* Paa, const double* Pbb, const double* Pab, int nb,
+                               double* D2aa, double* D2bb, double* bias, double* r, cudaStream_t s);
+
 }  // namespace amber

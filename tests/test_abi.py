@@ -96,3 +96,21 @@ def test_sigma2_tophat_host_matches_oracle():
     D2 = 0.3 * (k / 1.0) ** 1.5 * np.exp(-k / 50.0)
     for R in (0.2, 0.5, 2.0):
         assert abs(B.sigma2_tophat(k, D2, R) / O.sigma2_tophat(k, D2, R) - 1.0) < 1e-9
+
+
+def test_noalloc_rejects_pointers_off_their_element_size(B):
+    # the argument checks run before any CUDA call, so nothing is enqueued and
+    # no device is needed: a float array must start on a multiple of 4 bytes
+    vp = C.c_void_p
+    assert B.lib.amber_rank_noalloc(vp(0x1002), 64, vp(0x2000), None, None) == B.AMBER_ERR_INVALID_ARG
+    assert B.lib.amber_rank_noalloc(vp(0x1000), 64, vp(0x2001), None, None) == B.AMBER_ERR_INVALID_ARG
+    assert B.lib.amber_rank_noalloc(vp(0x1000), 64, vp(0x2000), vp(0x3002), None) == B.AMBER_ERR_INVALID_ARG
+    assert B.lib.amber_rank_noalloc(vp(0x1000), 0, vp(0x2000), None, None) == B.AMBER_ERR_INVALID_ARG
+
+
+def test_binding_rejects_non_contiguous_tensors(B):
+    import torch
+    t = torch.zeros(8, 8)[:, ::2]
+    with pytest.raises(ValueError):
+        B._ptr(t)
+    assert B._ptr(torch.zeros(4)) is not None and B._ptr(None) is None

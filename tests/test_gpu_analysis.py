@@ -99,11 +99,43 @@ def test_power_spectrum_of_z_fields_and_derived(ctx, B):
     np.testing.assert_allclose(da.cpu().numpy(), oa, rtol=0, atol=2e-6)
     ref = O.power_spectrum(oa, ob, box)
     _check_spectra(_cpu(got), ref, rtol=1e-4)
-    der = B.derived_spectra(got)
+    der = {k: v.cpu().numpy() for k, v in ctx.derived_spectra(got).items()}
+    assert ctx.sync_status() == 0
     live = ref[4] > 0
     live[0] = False  # k = 0: the mean of a normalised field, rounding noise on both sides
+    # Eqs. Dk, bias and rcc formed in the library against the oracle's (pinned) forms
+    np.testing.assert_allclose(der["Delta2_aa"][live], O.dimensionless_power(ref[0], ref[1])[live], rtol=1e-4)
+    np.testing.assert_allclose(der["Delta2_bb"][live], O.dimensionless_power(ref[0], ref[2])[live], rtol=1e-4)
     np.testing.assert_allclose(der["bias"][live], O.bias(ref[1], ref[2])[live], rtol=1e-4)
     np.testing.assert_allclose(der["r"][live], O.cross_correlation(ref[3], ref[1], ref[2])[live], rtol=1e-4)
+    # a shell without modes: Delta^2 = 0, NaN ratios
+    empty = ~(ref[4] > 0)
+    if empty.any():
+        assert np.all(der["Delta2_aa"][empty] == 0.0) and np.all(np.isnan(der["bias"][empty]))
+
+
+def test_power_derived_on_given_shells(ctx, B):
+    # the derived statistics of fixed shell averages (no transform): exact
+    # FP64 arithmetic against the oracle's forms, and argument checks
+    nb = 37
+    g = np.random.default_rng(9)
+    k = np.linspace(0.0, 3.0, nb)
+    Paa, Pbb = g.uniform(0.5, 2.0, nb), g.uniform(0.5, 2.0, nb)
+    Pab = g.uniform(-0.4, 0.4, nb)
+    t = lambda a: torch.from_numpy(a).cuda()
+    s = {"k": t(k), "Paa": t(Paa), "Pbb": t(Pbb), "Pab": t(Pab)}
+    der = {key: v.cpu().numpy() for key, v in ctx.derived_spectra(s).items()}
+    np.testing.assert_allclose(der["Delta2_aa"], O.dimensionless_power(k, Paa), rtol=1e-14)
+    np.testing.assert_allclose(der["Delta2_bb"], O.dimensionless_power(k, Pbb), rtol=1e-14)
+    np.testing.assert_allclose(der["bias"], O.bias(Paa, Pbb), rtol=1e-14)
+    np.testing.assert_allclose(der["r"], O.cross_correlation(Pab, Paa, Pbb), rtol=1e-14)
+    vp = __import__("ctypes").c_void_p
+    out = torch.empty(nb, dtype=torch.float64, device="cuda")
+    # a bias without P_bb, and a misaligned array, are refused before any launch
+    assert B.lib.amber_power_derived(ctx._h, vp(s["k"].data_ptr()), vp(s["Paa"].data_ptr()), None, None, nb,
+                                     vp(out.data_ptr()), None, vp(out.data_ptr()), None, None) == B.AMBER_ERR_INVALID_ARG
+    assert B.lib.amber_power_derived(ctx._h, vp(s["k"].data_ptr() + 4), vp(s["Paa"].data_ptr()), None, None, nb,
+                                     vp(out.data_ptr()), None, None, None, None) == B.AMBER_ERR_INVALID_ARG
 
 
 def test_power_spectrum_parseval_512(B):

@@ -124,11 +124,12 @@ def test_serving_results_same_alone_and_in_the_mix(B):
     assert overlapped > 0  # requests really ran concurrently
     for a, b in zip(alone, mix):
         assert torch.equal(a.z, b.z), a.rid
-    # one request against the oracle
-    q = mix[-1]
+    # one 64^3 request against the oracle, at the stated tolerance: > 1e-3 in at
+    # most 1e-4 of the cells
+    q = next(x for x in reversed(mix) if x.n == 64)
     box = serve.BOX_PER_CELL.get(q.n, 100.0 / 128) * q.n
     from paper_2109_10375_gb300 import synth as sy
     d = sy.gaussian_density(q.n, box, 1000 + q.realisation).float().double().numpy()
     So, mo = O.source_field(d, q.delta_c, 0.7)
     _, _, zo = O.solve(So, mo, box, q.l_mfp, *q.history)
-    assert np.mean(np.abs(q.z.cpu().numpy().reshape(-1) - zo) > 1e-3) <= 1e-3
+    assert np.mean(np.abs(q.z.cpu().numpy().reshape(-1) - zo) > 1e-3) <= 1e-4

@@ -35,6 +35,8 @@ PINS = [
     lambda: [pins.test_power_spectrum_plane_wave(m) for m in [(1, 0, 0), (0, 3, 2), (2, -1, 4), (4, 4, 4)]],
     lambda: pins.test_power_shell_counts_brute_force(),
     lambda: pins.test_bias_and_cross_correlation_identities(),
+    lambda: [pins.test_dimensionless_power_integrates_to_the_variance_closed_form(v) for v in (0.0, -2.5, 1.0)],
+    lambda: pins.test_dimensionless_power_of_a_band_limited_field_sums_to_its_variance(),
     lambda: pins.test_white_noise_power_is_flat(),
     lambda: pins.test_delta_z_and_epsilon_z_closed_forms(),
     lambda: pins.test_lpt_plane_wave_is_zeldovich(),
@@ -144,6 +146,8 @@ MUTATIONS = {
     "growth_not_pivoted_at_midpoint": ("weight_coeffs", _coeffs_unpivoted),
     "power_missing_volume": ("power_spectrum", _power_no_volume),
     "power_cross_is_geometric_mean": ("power_spectrum", _power_cross_swapped),
+    "delta2_k_squared": ("dimensionless_power", lambda k, P: np.asarray(k) ** 2 * np.asarray(P) / (2.0 * math.pi ** 2)),
+    "delta2_wrong_constant": ("dimensionless_power", lambda k, P: np.asarray(k) ** 3 * np.asarray(P) / (2.0 * math.pi)),
     "delta_z_not_normalised": ("delta_z", lambda z: (lambda zz: (zz - zz.mean(), float(zz.mean())))(
         np.asarray(z, dtype=np.float64))),
     "tsc_weights_mirrored": ("assignment_weights_1d", _tsc_mirrored),

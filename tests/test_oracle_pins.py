@@ -505,6 +505,45 @@ def test_power_spectrum_plane_wave(m0):
     np.testing.assert_allclose(o.dimensionless_power(k[b], P[b]), k[b] ** 3 * P[b] / (2 * np.pi ** 2), rtol=1e-14)
 
 
+def _integral_dlnk(fn, lo, hi, npts=40001):
+    """Trapezoid rule of fn(k) over ln k on [lo, hi]."""
+    u = np.linspace(math.log(lo), math.log(hi), npts)
+    f = fn(np.exp(u))
+    return float(np.sum(0.5 * (f[1:] + f[:-1]) * np.diff(u)))
+
+
+@pytest.mark.parametrize("n_index", [0.0, -2.5, 1.0])
+def test_dimensionless_power_integrates_to_the_variance_closed_form(n_index):
+    # sigma^2 = int P(k) d^3k / (2 pi)^3 = int Delta^2(k) dln k.  For
+    # P = A k^n exp(-(k R)^2) the left side is, by the Gamma integral,
+    # A Gamma((3 + n)/2) / (4 pi^2 R^(3 + n)): a dropped 2 pi^2, a k^2 for k^3
+    # or any other slip in Eq. Dk breaks the equality
+    A, R = 2.7, 1.3
+    closed = A * math.gamma((3.0 + n_index) / 2.0) / (4.0 * math.pi ** 2 * R ** (3.0 + n_index))
+    num = _integral_dlnk(lambda k: o.dimensionless_power(k, A * k ** n_index * np.exp(-(k * R) ** 2)),
+                         1e-18 / R, 12.0 / R)
+    assert abs(num / closed - 1.0) < 1e-6
+
+
+def test_dimensionless_power_of_a_band_limited_field_sums_to_its_variance():
+    # a Gaussian random field whose power sits in shells 10..25 of a 64^3 grid
+    # (where the mode count of shell b is close to 4 pi b^2): the shell sum of
+    # Delta^2 over ln k (width kf / k per shell) recovers the field's variance
+    n, box = 64, 80.0
+    g = np.random.default_rng(5)
+    w = np.fft.rfftn(g.normal(size=(n, n, n)))
+    m = np.fft.fftfreq(n, 1.0 / n)
+    mr = np.fft.rfftfreq(n, 1.0 / n)
+    mag = np.sqrt(m[:, None, None] ** 2 + m[None, :, None] ** 2 + mr[None, None, :] ** 2)
+    field = np.fft.irfftn(w * np.exp(-((mag - 17.0) / 4.0) ** 2), s=(n, n, n), axes=(0, 1, 2))
+    k, P, _, _, modes = o.power_spectrum(field, field, box)
+    kf = 2.0 * math.pi / box
+    live = (modes > 0) & (k > 0)
+    D2 = o.dimensionless_power(k[live], P[live])
+    shell_sum = float(np.sum(D2 * kf / k[live]))
+    assert abs(shell_sum / field.var() - 1.0) < 0.02
+
+
 def test_power_shell_counts_brute_force():
     # lattice points with round(|m|) = b, counted by explicit loops
     n = 6

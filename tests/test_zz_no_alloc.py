@@ -55,3 +55,41 @@ def test_rank_noalloc_rejects_more_cells_than_its_scratch(B):
     out = torch.zeros(8, dtype=torch.int32, device="cuda")
     rc = B.lib.amber_rank_noalloc(C.c_void_p(J.data_ptr()), MAX_CELLS + 1, C.c_void_p(out.data_ptr()), None, None)
     assert rc == B.AMBER_ERR_CAPACITY
+
+
+@pytest.mark.parametrize("n", [1, 4095, 4097])
+def test_rank_noalloc_small_and_ragged_sizes_without_status_word(B, n):
+    # fewer keys than one sort tile, and a ragged tail; no caller status word,
+    # so device errors go to the array's own word (none are expected)
+    stream = torch.cuda.current_stream()
+    J = _keys(n, 10 + n)
+    with B.Context(MAX_CELLS) as ctx:
+        ref = ctx.rank(J)
+        for _ in range(2):
+            out = torch.full((n,), -1, dtype=torch.int32, device="cuda")
+            rc = B.lib.amber_rank_noalloc(C.c_void_p(J.data_ptr()), n, C.c_void_p(out.data_ptr()), None,
+                                          C.c_void_p(stream.cuda_stream))
+            assert rc == B.AMBER_OK, B.status_string(rc)
+            torch.cuda.synchronize()
+            assert torch.equal(out, ref)
+
+
+def test_rank_noalloc_view_off_a_16_byte_boundary(B):
+    # J[1:] starts 4 bytes past an aligned allocation: the histogram reads it
+    # element by element instead of 16 bytes at a time
+    stream = torch.cuda.current_stream()
+    base = _keys(300_001, 77)
+    J = base[1:]
+    assert J.data_ptr() % 16 != 0
+    n = J.numel()
+    with B.Context(MAX_CELLS) as ctx:
+        ref = ctx.rank(J.clone())
+        view = ctx.rank(J)
+        out = torch.full((n,), -1, dtype=torch.int32, device="cuda")
+        rc = B.lib.amber_rank_noalloc(C.c_void_p(J.data_ptr()), n, C.c_void_p(out.data_ptr()), None,
+                                      C.c_void_p(stream.cuda_stream))
+        assert rc == B.AMBER_OK
+        torch.cuda.synchronize()
+        assert ctx.sync_status() == 0
+    assert torch.equal(view, ref)
+    assert torch.equal(out, ref)
