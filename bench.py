@@ -149,6 +149,44 @@ def oracle_baseline(n_sample: int, box: float, seconds: float) -> dict:
             "single_core_sample": f"{reps1} x {n_sample}^3 in one process, {el1:.1f} s"}
 
 
+def oracle_accuracy(S_h, m_h, J, z, n: int, box: float) -> dict:
+    """Error of the workload's GPU results (J and z_re of one solve) against
+    the FP64 oracle's whole path on the same input fields, every cell: the
+    oracle runs as it stands (oracle.solve_large: the steps of oracle.solve on
+    all host cores).  Tolerances: intensity relative L2 <= 1e-5 and max
+    relative <= 1e-4 (denominator max(|J|, 5e-2 rms J), the FP32 reading);
+    z_re off by more than 1e-3 in at most 1e-4 of the cells."""
+    import numpy as np
+    from oracle import amber_oracle as O
+    t0 = time.perf_counter()
+    workers = max(1, min(16, os.cpu_count() or 1))
+    S64 = S_h.numpy().astype(np.float64)
+    m64 = m_h.numpy().astype(np.float64)
+    J_o, order_o, z_o = O.solve_large(S64, m64, box, L_MFP, *HIST, workers=workers)
+    del S64, m64, order_o
+    J_o = J_o.reshape(-1)
+    d = J.reshape(-1).astype(np.float64)
+    d -= J_o
+    rms = float(np.sqrt(np.mean(J_o * J_o)))
+    rel_l2 = float(np.linalg.norm(d) / np.linalg.norm(J_o))
+    max_abs = float(np.max(np.abs(d)))
+    np.abs(d, out=d)
+    d /= np.maximum(np.abs(J_o), 5e-2 * rms)
+    max_rel = float(d.max())
+    del d, J_o
+    dz = np.abs(z.reshape(-1).astype(np.float64) - z_o)
+    out = {"against": f"FP64 oracle (oracle.solve_large, {workers} host processes) on the same {n}^3 inputs, "
+                      "every cell",
+           "J_rel_l2": rel_l2, "J_max_rel": max_rel, "J_max_abs_over_rms": max_abs / rms,
+           "J_max_rel_denominator": "max(|J_oracle|, 5e-2 rms(J_oracle))",
+           "zre_frac_dz_gt_1e-3": float(np.mean(dz > 1e-3)), "zre_max_abs_dz": float(dz.max()),
+           "zre_median_abs_dz": float(np.median(dz)),
+           "tolerances": {"J_rel_l2": 1e-5, "J_max_rel": 1e-4, "zre_frac_dz_gt_1e-3": 1e-4},
+           "host_seconds": time.perf_counter() - t0}
+    out["within_tolerance"] = bool(rel_l2 <= 1e-5 and max_rel <= 1e-4 and out["zre_frac_dz_gt_1e-3"] <= 1e-4)
+    return out
+
+
 def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
@@ -242,8 +280,25 @@ class ClockSampler:
 # Roofline bookkeeping: algorithmic bytes per launch of each kernel
 # ---------------------------------------------------------------------------
 
-def algorithmic_bytes(n: int, sort_passes: int) -> dict:
-    """Algorithmic HBM bytes per step of each kernel kind (the design's byte model)."""
+def model_bytes(n: int, sort_passes: int) -> dict:
+    """Algorithmic HBM bytes per step of each kernel kind, on the scope table's
+    byte model ("model A"): every FFT pass reads and writes 4 B/cell (the half
+    spectrum counted as 4 B/cell), the histogram reads 4, the digit passes move
+    12 (first: key in, key + index out), 16 (middle) and 12 (last: no key out)
+    B/cell, and the matching reads the order and the rank-order masses (4 + 4)
+    and writes z (4).  112 B/cell for four 8-bit passes, 96 for three."""
+    C = n ** 3
+    sort = (12 + 16 * (sort_passes - 2) + 12) * C if sort_passes >= 2 else 8 * C
+    return {"fft_r2c_x": 8 * C, "fft_y_fwd": 8 * C, "fft_z_conv": 8 * C, "fft_y_inv": 8 * C, "fft_c2r_x": 8 * C,
+            "sort_histogram": 4 * C, "sort_pass": sort, "scan_assign": 8 * C, "scatter_back": 4 * C,
+            "mass_reduce": 0, "thresholds": 0}
+
+
+def design_bytes(n: int, sort_passes: int) -> dict:
+    """Algorithmic bytes per step of each kernel as this design moves them:
+    the half spectrum at its true size, the mass riding through the sort as a
+    second payload (+8 B/cell per pass), and the scan's (cell, z) pairs
+    written and read back by the scatter to cell order."""
     C = n ** 3
     H = 8 * n * n * (n // 2 + 1)  # half spectrum, complex64
     if sort_passes == 1:
@@ -494,6 +549,17 @@ def run_amber(args):
     # step copies its inputs in, solves and copies z_re out; two buffer sets
     # let one step's copies overlap the neighbouring steps' solves (H2D and
     # D2H on their own streams, ordered by events).
+    # the workload's intensity and z_re, kept on the host for the comparison
+    # with the oracle (the cpu_baseline leg, after every GPU measurement)
+    J_keep = z_keep = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline and not args.no_accuracy:
+        Jbuf = torch.empty_like(S)
+        ctx.solve(S, m, box, L_MFP, h, out=z, J_out=Jbuf)
+        st = ctx.sync_status()
+        if st != 0:
+            raise RuntimeError(f"device status (accuracy solve): {B.status_string(st)}")
+        J_keep, z_keep = Jbuf.cpu().numpy(), z.cpu().numpy()
+        del Jbuf
     del S, m
     torch.cuda.empty_cache()
     S_d = [torch.empty(z.shape, device="cuda") for _ in range(2)]
@@ -584,28 +650,34 @@ def run_amber(args):
         st = ctx.sync_status()
         if st != 0:
             raise RuntimeError(f"device status after autotuning: {B.status_string(st)}")
-    del S_d, m_d, z_d, z_h, S_h, m_h
+    del S_d, m_d, z_d, z_h
 
     # each timed bracket is one kernel launch, except the histogram's, which
     # also holds the one-CTA digit-offset scan (k_sort_offsets)
     launches_per_step = (sum(v[1] for v in prof.values()) + prof["sort_histogram"][1]) / args.steps
-    ab = algorithmic_bytes(n, passes)
+    mb, db = model_bytes(n, passes), design_bytes(n, passes)
     kernels = {}
     for k, (ms_k, cnt) in prof.items():
         if cnt == 0:
             continue
         ms_step = ms_k / args.steps
         kernels[k] = {"ms_per_step": ms_step, "launches_per_step": cnt / args.steps,
-                      "algorithmic_bytes_per_step": ab.get(k, 0),
-                      "GBps": (ab.get(k, 0) / (ms_step / 1e3) / 1e9) if ms_step > 0 else None}
+                      "model_bytes_per_step": mb.get(k, 0), "design_bytes_per_step": db.get(k, 0),
+                      "GBps_model": (mb.get(k, 0) / (ms_step / 1e3) / 1e9) if ms_step > 0 else None,
+                      "GBps_design": (db.get(k, 0) / (ms_step / 1e3) / 1e9) if ms_step > 0 else None}
     dom = max(kernels, key=lambda k: kernels[k]["ms_per_step"])
     peaks, src = _peaks()
-    achieved = kernels[dom]["GBps"]
-    path_bytes = sum(ab.get(k, 0) for k in kernels)
-    cpu = None
+    peak = peaks["hbm_gbs"]
+    achieved = kernels[dom]["GBps_model"]
+    path_model = sum(mb.get(k, 0) for k in kernels)
+    path_design = sum(db.get(k, 0) for k in kernels)
+    cpu, accuracy = None, None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         ns = args.cpu_sample_n
         cpu = oracle_baseline(ns, box * ns / n, args.cpu_seconds)
+        if not args.no_accuracy:
+            accuracy = oracle_accuracy(S_h, m_h, J_keep, z_keep, n, box)
+    del J_keep, z_keep, S_h, m_h
 
     extras = {}
     if tune is not None:
@@ -631,16 +703,23 @@ def run_amber(args):
                         "stage_ms_mean": stage_ms, "trials_ms": [t[0] for t in trials],
                         "reported": "median of 3 timed trials"},
                 "gpu_launches": int(round(launches_per_step * args.steps)),
-                "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peaks["hbm_gbs"],
-                             "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": _traffic(dom, n),
-                             "peak_source": src,
-                             "path_bytes_per_cell": path_bytes / C,
-                             "path_frac": (path_bytes / (ms_max / 1e3) / 1e9) / peaks["hbm_gbs"],
-                             "path_frac_112B_model": (112 * C / (ms_max / 1e3) / 1e9) / peaks["hbm_gbs"],
+                "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
+                             "unit": "GB/s", "frac": achieved / peak, "traffic": _traffic(dom, n),
+                             "peak_source": src, "peak_kind": "measured copy bandwidth (burst)",
+                             "bytes_model": "scope-table model A (sort 12+16+..+12 B/cell per pass set)",
+                             "model_bytes_per_launch": mb[dom] / max(1, kernels[dom]["launches_per_step"]),
+                             "launch_ms": kernels[dom]["ms_per_step"] / max(1, kernels[dom]["launches_per_step"]),
+                             "path_bytes_per_cell": path_model / C,
+                             "path_frac": (path_model / (ms_max / 1e3) / 1e9) / peak,
+                             "design_bytes_per_cell": {"kernel": db[dom] / C, "path": path_design / C},
+                             "design_frac": {"kernel": kernels[dom]["GBps_design"] / peak,
+                                             "path": (path_design / (ms_max / 1e3) / 1e9) / peak},
                              "sort_passes": passes},
                 "kernels": kernels,
                 "clocks": clocks,
                 "cpu_baseline": cpu}
+        if accuracy is not None:
+            line["accuracy"] = accuracy
         if weightings:
             line["weightings"] = weightings
         if tomographic:
@@ -782,6 +861,8 @@ def main():
     ap.add_argument("--cpu-sample-n", type=int, default=128)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-accuracy", action="store_true",
+                    help="skip the oracle comparison of the workload's J and z_re (minutes of host time)")
     ap.add_argument("--no-extras", action="store_true", help="skip the batched and serving measurements")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "amber":

@@ -221,18 +221,26 @@ def kmag_half(n: int, box: float):
     return np.sqrt(k[:, None, None] ** 2 + k[None, :, None] ** 2 + kx[None, None, :] ** 2)
 
 
-def radiation_field(S, box: float, l_mfp: float):
+def radiation_field(S, box: float, l_mfp: float, workers: int | None = None):
     """J = IDFT(DFT(S) * K(|k|)) in float64, cell order [z][y][x].
 
     The discrete convolution on the periodic grid: forward sum
     S_hat(k) = sum_x S(x) e^{-i k.x}, inverse with the 1/C normalisation.
+    workers: if given, the two FFTs run on that many threads (scipy.fft, the
+    same real-input transforms); the product is formed in place.
     """
     S = np.asarray(S, dtype=np.float64)
     n = S.shape[0]
     assert S.shape == (n, n, n)
-    S_hat = np.fft.rfftn(S)
-    J_hat = S_hat * kernel_transform(kmag_half(n, box), l_mfp)
-    return np.fft.irfftn(J_hat, s=S.shape, axes=(0, 1, 2))
+    if workers:
+        import scipy.fft as sfft
+        S_hat = sfft.rfftn(S, workers=workers)
+    else:
+        S_hat = np.fft.rfftn(S)
+    S_hat *= kernel_transform(kmag_half(n, box), l_mfp)
+    if workers:
+        return sfft.irfftn(S_hat, s=S.shape, axes=(0, 1, 2), workers=workers)
+    return np.fft.irfftn(S_hat, s=S.shape, axes=(0, 1, 2))
 
 
 # ---------------------------------------------------------------------------
@@ -245,6 +253,59 @@ def rank(J):
     if not np.all(np.isfinite(J)):
         raise ValueError("non-finite intensity")
     return np.argsort(-J, kind="stable")
+
+
+def _sort_block(args):
+    """Worker of rank_blocks: stable descending order of one block of cells,
+    read from and written to shared memory (global cell indices)."""
+    from multiprocessing import shared_memory
+    jname, oname, C, lo, hi = args
+    js = shared_memory.SharedMemory(name=jname)
+    os_ = shared_memory.SharedMemory(name=oname)
+    try:
+        J = np.ndarray((C,), dtype=np.float64, buffer=js.buf)
+        out = np.ndarray((C,), dtype=np.int32, buffer=os_.buf)
+        out[lo:hi] = np.argsort(-J[lo:hi], kind="stable") + lo
+    finally:
+        js.close()
+        os_.close()
+    return hi - lo
+
+
+def rank_blocks(J, workers: int):
+    """rank(J) for fields too large for one process to sort in reasonable time.
+
+    The same stable descending order, as a merge sort over contiguous blocks:
+    `workers` spawned processes each sort one block of consecutive cells
+    stably (ties keep ascending cell index), then one stable sort of the
+    concatenated, already sorted blocks merges them -- equal intensities from
+    different blocks keep block order, which is ascending cell index.  Both
+    sorts are numpy's stable argsort.  Returns int32 cell indices."""
+    import multiprocessing as mp
+    from multiprocessing import shared_memory
+    J = np.asarray(J, dtype=np.float64).reshape(-1)
+    if not np.all(np.isfinite(J)):
+        raise ValueError("non-finite intensity")
+    C = J.shape[0]
+    bounds = np.linspace(0, C, max(1, int(workers)) + 1).astype(np.int64)
+    js = shared_memory.SharedMemory(create=True, size=max(8 * C, 8))
+    os_ = shared_memory.SharedMemory(create=True, size=max(4 * C, 4))
+    try:
+        np.ndarray((C,), dtype=np.float64, buffer=js.buf)[:] = J
+        jobs = [(js.name, os_.name, C, int(a), int(b)) for a, b in zip(bounds[:-1], bounds[1:]) if b > a]
+        with mp.get_context("spawn").Pool(len(jobs)) as pool:
+            pool.map(_sort_block, jobs, chunksize=1)
+        g = np.array(np.ndarray((C,), dtype=np.int32, buffer=os_.buf))
+    finally:
+        js.close()
+        js.unlink()
+        os_.close()
+        os_.unlink()
+    vals = J[g]
+    np.negative(vals, out=vals)
+    perm = np.argsort(vals, kind="stable")  # merges the sorted blocks
+    del vals
+    return g[perm]
 
 
 def cumulative_mass_fraction(order, mass):
@@ -657,6 +718,65 @@ def assign_zre_tomographic(J_list, z_bounds, mass, table: HistoryTable):
         take = ~done & ((z_tmp >= z_bounds[k + 1]) | (k == K - 1))
         z_re[take] = z_tmp[take]
     return z_re
+
+
+def solve_large(S, mass, box: float, l_mfp: float, z_mid: float, dz: float, Az: float, workers: int,
+                z_lo: float = 5.0, z_hi: float = 20.0, n_table: int = 2000, block: int = 1 << 26):
+    """solve() for grids too large for one core (1024^3 in minutes): the same
+    steps in the same order, with the two FFTs on `workers` threads, the
+    ranking by rank_blocks (the same stable order), and the table inverse --
+    which acts on each F_n alone -- applied to `block` ranks at a time.
+    Returns J (float64 [n][n][n]), order (int32) and z_re (float64, cell order)."""
+    J = radiation_field(S, box, l_mfp, workers=workers)
+    order = rank_blocks(J, workers)
+    table = history_table(z_mid, dz, Az, z_lo, z_hi, n_table)
+    F = cumulative_mass_fraction(order, mass)
+    z_n = assign_from_fraction_blocks(F, table, workers, block)
+    del F
+    z_re = np.empty(z_n.shape[0], dtype=np.float64)
+    z_re[order] = z_n
+    return J, order, z_re
+
+
+def _assign_block(args):
+    """Worker of assign_from_fraction_blocks: the table inverse of ranks
+    [lo, hi), read from and written to shared memory."""
+    from multiprocessing import shared_memory
+    fname, zname, C, lo, hi, table = args
+    fs = shared_memory.SharedMemory(name=fname)
+    zs = shared_memory.SharedMemory(name=zname)
+    try:
+        F = np.ndarray((C,), dtype=np.float64, buffer=fs.buf)
+        z = np.ndarray((C,), dtype=np.float64, buffer=zs.buf)
+        z[lo:hi] = assign_from_fraction(F[lo:hi], table)
+    finally:
+        fs.close()
+        zs.close()
+    return hi - lo
+
+
+def assign_from_fraction_blocks(F, table: HistoryTable, workers: int, block: int = 1 << 26):
+    """assign_from_fraction(F, table), which acts on each F_n alone, applied
+    to `block` ranks at a time by `workers` spawned processes."""
+    import multiprocessing as mp
+    from multiprocessing import shared_memory
+    F = np.asarray(F, dtype=np.float64).reshape(-1)
+    C = F.shape[0]
+    if workers <= 1 or C <= block:
+        return assign_from_fraction(F, table)
+    fs = shared_memory.SharedMemory(create=True, size=8 * C)
+    zs = shared_memory.SharedMemory(create=True, size=8 * C)
+    try:
+        np.ndarray((C,), dtype=np.float64, buffer=fs.buf)[:] = F
+        jobs = [(fs.name, zs.name, C, a, min(a + block, C), table) for a in range(0, C, block)]
+        with mp.get_context("spawn").Pool(min(int(workers), len(jobs))) as pool:
+            pool.map(_assign_block, jobs, chunksize=1)
+        return np.array(np.ndarray((C,), dtype=np.float64, buffer=zs.buf))
+    finally:
+        fs.close()
+        fs.unlink()
+        zs.close()
+        zs.unlink()
 
 
 def solve(S, mass, box: float, l_mfp: float, z_mid: float, dz: float, Az: float,

@@ -70,3 +70,13 @@ def test_traffic_hash_follows_only_the_kernels_own_sources():
     t = json.load(open(os.path.join(ROOT, "profiles", "dram_traffic.json")))
     for k, v in t["kernels"].items():
         assert v["src_hash"] and v["bytes_per_launch"] > 0 and v["cells"] > 0, k
+
+
+def test_model_bytes_follow_the_scope_table():
+    # model A: five FFT passes x 8, histogram 4, digit passes 12 + 16 + .. + 12,
+    # matching 12 B/cell -- 112 B/cell with four 8-bit passes, 96 with three
+    import bench
+    for passes, total in ((4, 112), (3, 96)):
+        mb = bench.model_bytes(64, passes)
+        assert sum(mb.values()) == total * 64 ** 3
+        assert mb["sort_pass"] == (total - 56) * 64 ** 3

@@ -753,3 +753,30 @@ def test_tomographic_two_interval_brute_force():
             acc += mass[c]
             ref[c] = float(o.assign_from_fraction(np.array([acc / T]), t)[0])
     np.testing.assert_allclose(z, ref, rtol=0, atol=1e-12)
+
+
+def test_rank_blocks_is_the_stable_descending_order():
+    # the block-parallel merge sort gives rank()'s order exactly, ties included
+    # (few distinct values, ties spread across blocks), for block counts that
+    # do and do not divide the cell count
+    g = np.random.default_rng(12)
+    for C, workers in ((1, 3), (1000, 1), (10007, 3), (65536, 4)):
+        J = np.round(g.normal(size=C), 1)
+        J[::7] = 0.25
+        ref = o.rank(J)
+        got = o.rank_blocks(J, workers)
+        np.testing.assert_array_equal(got, ref)
+
+
+def test_solve_large_is_solve():
+    # the multi-core form of the whole oracle path gives solve()'s results:
+    # the same order and z, J up to the FFT's rounding
+    from paper_2109_10375_gb300 import synth
+    for n, box in ((16, 25.0), (32, 50.0)):
+        S, m = synth.realisation(n, box, 3)
+        S, m = S.double().numpy(), m.double().numpy()
+        J0, o0, z0 = o.solve(S, m, box, 3.0, 8.0, 4.0, 3.0)
+        J1, o1, z1 = o.solve_large(S, m, box, 3.0, 8.0, 4.0, 3.0, workers=3, block=1000)
+        assert np.max(np.abs(J1 - J0)) <= 1e-13 * np.max(np.abs(J0))
+        np.testing.assert_array_equal(o1, o0)
+        np.testing.assert_array_equal(z1, z0)
