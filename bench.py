@@ -803,7 +803,9 @@ def run_serving(torch, n_requests: int = 800, rate: float = 200.0):
     out = serve.summarize(reqs)
     out.update({"rate_per_s": rate, "mix": {"128^3": 0.6, "256^3": 0.3, "512^3": 0.1}, "realisations": 20,
                 "history_only_fraction": 0.7, "slots": len(srv.slots),
-                "waits_for_hbm": srv.waiting_hbm})
+                "cache": "rank order per (realisation, grid, l_mfp, delta_c); transformed source per "
+                         "(realisation, grid, delta_c)",
+                "waits_for_hbm": srv.waiting_hbm, "evictions": srv.evictions})
     srv.close()
     return out
 

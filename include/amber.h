@@ -203,6 +203,32 @@ int amber_solve_ex(amber_ctx *ctx, const float *d_src, const float *d_mass, cons
 int amber_assign_zre_ranked(amber_ctx *ctx, const uint32_t *d_order, const float *d_mass_rank, int64_t ncells,
                             const amber_history_t *h, float *d_zre, double *d_F_opt, void *stream);
 
+/* ---- Reuse of the transformed source field (parameter studies) --------- */
+
+/* Bytes of the transformed source field of an n^3 grid that
+ * amber_source_spectrum writes: n^2 (n/2 + 2) complex64 values.  Host only. */
+int amber_spectrum_bytes(int n, size_t *out_bytes);
+
+/* The first two of the radiation field's five passes (Sec. 3.4.1): the
+ * real-to-complex transform along x and the forward transform along y of
+ * the source d_src (n^3 floats), written to d_spec (caller-owned device
+ * memory of amber_spectrum_bytes(n) bytes, 16-byte aligned; layout
+ * [z][y][kx] complex64, kx in [0, n/2] on rows of n/2 + 2).  The z transform
+ * is left to amber_solve_spectrum, which fuses it with the kernel multiply,
+ * so a parameter study that varies l_mfp (Sec. 5) keeps d_spec per source
+ * field and skips these passes.  Uses the context's FFT tile variant for n
+ * (amber_tuning_t). */
+int amber_source_spectrum(amber_ctx *ctx, const float *d_src, int n, void *d_spec, void *stream);
+
+/* amber_solve_ex starting from d_spec (amber_source_spectrum's output, only
+ * read): the forward z transform with the kernel multiply for p->l_mfp, the
+ * inverse transforms, ranking and matching.  With the same context tuning
+ * the results equal amber_solve_ex's on the source field bit for bit.
+ * d_order_out and d_mass_rank_out are both given (as for amber_solve_ex)
+ * or both NULL. */
+int amber_solve_spectrum(amber_ctx *ctx, const void *d_spec, const float *d_mass, const amber_params_t *p,
+                         float *d_zre, float *d_J_opt, uint32_t *d_order_out, float *d_mass_rank_out, void *stream);
+
 /* ---- Autotuning of the FP32 solve path per grid size ------------------- */
 
 /* The choices the FP32 solve path (amber_solve, amber_solve_ex,

@@ -33,7 +33,8 @@ EXPORTED = [
     "amber_delta_z", "amber_epsilon_z_pdf", "amber_power_bins", "amber_power_spectrum",
     "amber_lpt_displacement", "amber_mesh_density", "amber_esf_fcoll", "amber_sigma2_tophat",
     "amber_solve_tomographic", "amber_autotune", "amber_set_tuning", "amber_get_tuning",
-    "amber_rank_noalloc", "amber_power_derived",
+    "amber_rank_noalloc", "amber_power_derived", "amber_spectrum_bytes", "amber_source_spectrum",
+    "amber_solve_spectrum",
 ]
 
 
@@ -122,6 +123,9 @@ def _load():
         "amber_get_tuning": (i32, [vp, i32, C.POINTER(amber_tuning_t)]),
         "amber_rank_noalloc": (i32, [vp, i64, vp, vp, vp]),
         "amber_power_derived": (i32, [vp, vp, vp, vp, vp, i32, vp, vp, vp, vp, vp]),
+        "amber_spectrum_bytes": (i32, [i32, C.POINTER(C.c_size_t)]),
+        "amber_source_spectrum": (i32, [vp, vp, i32, vp, vp]),
+        "amber_solve_spectrum": (i32, [vp, vp, vp, C.POINTER(amber_params_t), vp, vp, vp, vp, vp]),
         "amber_test_wait_timeout": (i32, [vp, C.c_uint, vp]),
     }
     for name, (res, args) in sig.items():
@@ -184,6 +188,12 @@ def history_table(h: amber_history_t):
     _check(lib.amber_history_table(C.byref(h), z.ctypes.data_as(C.POINTER(C.c_double)),
                                    x.ctypes.data_as(C.POINTER(C.c_double))), "amber_history_table")
     return z, x
+
+
+def spectrum_bytes(n: int) -> int:
+    out = C.c_size_t()
+    _check(lib.amber_spectrum_bytes(n, C.byref(out)), "amber_spectrum_bytes")
+    return out.value
 
 
 def workspace_bytes(max_cells: int) -> int:
@@ -325,6 +335,25 @@ class Context:
         p = params(S.shape[0], box, l_mfp, h)
         _check(lib.amber_solve_ex(self._h, _ptr(S), _ptr(mass), C.byref(p), _ptr(out), _ptr(J_out), _ptr(order_out),
                                   _ptr(mass_rank_out), _stream(stream)), "amber_solve_ex")
+        return out
+
+    def source_spectrum(self, S, out=None, stream=None):
+        """The x- and y-transformed source field (a flat uint8 device tensor of
+        amber_spectrum_bytes(n) bytes) that solve_spectrum starts from."""
+        import torch
+        n = S.shape[0]
+        if out is None:
+            out = torch.empty(spectrum_bytes(n), dtype=torch.uint8, device=S.device)
+        _check(lib.amber_source_spectrum(self._h, _ptr(S), n, _ptr(out), _stream(stream)), "amber_source_spectrum")
+        return out
+
+    def solve_spectrum(self, spec, mass, box: float, l_mfp: float, h: amber_history_t, out, order_out=None,
+                       mass_rank_out=None, J_out=None, stream=None):
+        """solve_ex from a kept source spectrum (l_mfp and history free to change)."""
+        p = params(mass.shape[0], box, l_mfp, h)
+        _check(lib.amber_solve_spectrum(self._h, _ptr(spec), _ptr(mass), C.byref(p), _ptr(out), _ptr(J_out),
+                                        _ptr(order_out), _ptr(mass_rank_out), _stream(stream)),
+               "amber_solve_spectrum")
         return out
 
     def assign_zre_ranked(self, order, mass_rank, h: amber_history_t, out, F=None, stream=None):

@@ -20,8 +20,12 @@ namespace amber {
 // krange: if not null, the intensities' key range is folded into it (the
 // sort's control block, reset beforehand) so the ranking needs no range pass.
 // variant: the FFT tile/radix variant (0 default; 1 for n >= 128).
+// spec_in: if not null, the x- and y-transformed source (source_spectrum_f32's
+// output), read by the z pass instead of transforming src.
 cudaError_t radiation_field_f32(int n, const float* src, float* J, void* H, const void* tw, double box, double l_mfp,
                                unsigned int* status, cudaStream_t s, FftProfile* prof, SortCtrl* krange,
+                               int variant, const void* spec_in = nullptr);
+cudaError_t source_spectrum_f32(int n, const float* src, void* H, const void* tw, cudaStream_t s, FftProfile* prof,
                                int variant);
 cudaError_t radiation_field_f64(int n, const double* src, double* J, void* H, const void* tw, double box,
                                double l_mfp, unsigned int* status, cudaStream_t s, FftProfile* prof,
@@ -648,7 +652,7 @@ static int solve_args(amber_ctx* c, const T* src, const float* mass, const amber
 // masses there for the caller; otherwise they stay in the workspace.
 static cudaError_t solve_f32_enqueue(amber_ctx* c, const float* d_src, const float* d_mass, const amber_params_t* p,
                                      const HistoryCoeffs& hc, float* d_zre, float* d_J_opt, uint32_t* order_out,
-                                     float* mass_rank_out, cudaStream_t s) {
+                                     float* mass_rank_out, cudaStream_t s, const void* spec_in = nullptr) {
   const Plan& pl = c->plan;
   const int n = p->n;
   const int64_t C = (int64_t)n * n * n;
@@ -657,7 +661,7 @@ static cudaError_t solve_f32_enqueue(amber_ctx* c, const float* d_src, const flo
   cudaError_t e = sort_ctrl_reset(c->sortw.ctrl, s);
   if (e == cudaSuccess)
     e = radiation_field_f32(n, d_src, J, c->ws + pl.off_spec, c->ws + pl.off_tw32 + pl.tw32_off[ilog2i(n)], p->box,
-                           p->l_mfp, c->status, s, &c->prof, c->sortw.ctrl, tu.fft_variant);
+                           p->l_mfp, c->status, s, &c->prof, c->sortw.ctrl, tu.fft_variant, spec_in);
   // the first sort pass sums each tile's masses; the thresholds kernel adds them
   unsigned long long* tile_mass = reinterpret_cast<unsigned long long*>(c->ws + pl.off_tilemass);
   if (e == cudaSuccess)
@@ -844,6 +848,43 @@ int amber_solve_ex(amber_ctx* c, const float* d_src, const float* d_mass, const 
   cudaStream_t s = (cudaStream_t)stream;
   c->last_stream = s;
   return cuda_status(solve_f32_enqueue(c, d_src, d_mass, p, hc, d_zre, d_J_opt, d_order_out, d_mass_rank_out, s));
+}
+
+int amber_spectrum_bytes(int n, size_t* out_bytes) {
+  if (!out_bytes || !is_pow2_in(n, 4, 1024)) return AMBER_ERR_INVALID_ARG;
+  *out_bytes = (size_t)n * n * (n / 2 + 2) * 8;
+  return AMBER_OK;
+}
+
+int amber_source_spectrum(amber_ctx* c, const float* d_src, int n, void* d_spec, void* stream) {
+  if (!c || !d_src || !d_spec || !is_pow2_in(n, 4, 1024) || !all_aligned(d_src) ||
+      (reinterpret_cast<uintptr_t>(d_spec) & 15) != 0)
+    return AMBER_ERR_INVALID_ARG;
+  if (n > c->plan.n32) return AMBER_ERR_CAPACITY;
+  std::lock_guard<std::mutex> lk(c->mu);
+  DeviceGuard g(c->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  c->last_stream = s;
+  const int l = ilog2i(n);
+  return cuda_status(source_spectrum_f32(n, d_src, d_spec, c->ws + c->plan.off_tw32 + c->plan.tw32_off[l], s,
+                                         &c->prof, c->tune[l].fft_variant));
+}
+
+int amber_solve_spectrum(amber_ctx* c, const void* d_spec, const float* d_mass, const amber_params_t* p, float* d_zre,
+                         float* d_J_opt, uint32_t* d_order_out, float* d_mass_rank_out, void* stream) {
+  if (!d_spec || (reinterpret_cast<uintptr_t>(d_spec) & 15) != 0) return AMBER_ERR_INVALID_ARG;
+  HistoryCoeffs hc;
+  // the spectrum stands in for the source field in the argument checks
+  int st = solve_args(c, static_cast<const float*>(d_spec), d_mass, p, d_zre, 32, c ? c->plan.n32 : 0, &hc);
+  if (st) return st;
+  if ((d_order_out == nullptr) != (d_mass_rank_out == nullptr) || !all_aligned(d_J_opt, d_order_out, d_mass_rank_out))
+    return AMBER_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(c->mu);
+  DeviceGuard g(c->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  c->last_stream = s;
+  return cuda_status(solve_f32_enqueue(c, nullptr, d_mass, p, hc, d_zre, d_J_opt, d_order_out, d_mass_rank_out, s,
+                                       d_spec));
 }
 
 int amber_assign_zre_ranked(amber_ctx* c, const uint32_t* d_order, const float* d_mass_rank, int64_t ncells,

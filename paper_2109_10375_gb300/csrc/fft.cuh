@@ -95,10 +95,13 @@ __device__ __forceinline__ int signed_freq(int m, int n) { return m < n / 2 ? m 
 // ---------------------------------------------------------------------------
 enum { PASS_FWD = 0, PASS_INV = 1, PASS_CONV = 2 };
 
-template <typename T, int N, int MODE, int V = 0>
+// OOP (z-pass only): the tile is read from Hin, a spectrum kept by the
+// caller, and the result written to H; otherwise H is read and written in place.
+template <typename T, int N, int MODE, int V = 0, bool OOP = false>
 __global__ void __launch_bounds__(strided_threads<N, V>(), 2)
 k_fft_strided(cpx<T>* __restrict__ H, int64_t elem_stride, int64_t outer_stride, int ncol,
-              int ntx, const cpx<T>* __restrict__ tw, T kf, T l_mfp, T norm) {
+              int ntx, const cpx<T>* __restrict__ tw, T kf, T l_mfp, T norm,
+              const cpx<T>* __restrict__ Hin = nullptr) {
   using C = FftCfg<N, V>;
   using L = StridedSmem<T, N, V>;
   constexpr int R0 = C::R0, R1 = C::R1, E = C::E, SB = C::SB, NT = strided_threads<N, V>();
@@ -110,6 +113,7 @@ k_fft_strided(cpx<T>* __restrict__ H, int64_t elem_stride, int64_t outer_stride,
   const int outer = blockIdx.x / ntx;
   const int kx0 = (blockIdx.x - outer * ntx) * SB;
   cpx<T>* base = H + (int64_t)outer * outer_stride + kx0;
+  const cpx<T>* ibase = OOP ? Hin + (int64_t)outer * outer_stride + kx0 : base;
 
   cpx<T> v[E];
   // ---- forward stage A: radix R0 over n = j + r N/R0, read from global
@@ -121,7 +125,7 @@ k_fft_strided(cpx<T>* __restrict__ H, int64_t elem_stride, int64_t outer_stride,
 #pragma unroll
     for (int r = 0; r < R0; ++r) {
       const int n = j + r * (N / R0);
-      v[q * R0 + r] = ok ? base[(int64_t)n * elem_stride + b] : mk<T>(0, 0);
+      v[q * R0 + r] = ok ? ibase[(int64_t)n * elem_stride + b] : mk<T>(0, 0);
     }
   }
   if constexpr (MODE == PASS_CONV) {
@@ -476,9 +480,13 @@ enum ProfKind {
   PK_SORT_HIST, PK_SORT_PASS, PK_MASS_REDUCE, PK_THRESHOLDS, PK_SCAN_ASSIGN, PK_SCATTER_BACK, PK_COUNT
 };
 
+// spec_in (optional): the x- and y-transformed source kept by the caller
+// (source_spectrum_n's output); the first two passes are skipped and the z
+// pass reads it, leaving it unchanged.
 template <typename T, int N, int V = 0>
 cudaError_t radiation_field_n(const T* src, T* J, cpx<T>* H, const cpx<T>* tw, double box, double l_mfp,
-                              unsigned int* status, cudaStream_t s, FftProfile* prof, SortCtrl* krange) {
+                              unsigned int* status, cudaStream_t s, FftProfile* prof, SortCtrl* krange,
+                              const cpx<T>* spec_in = nullptr) {
   using C = FftCfg<N, V>;
   const int RS = N / 2 + 2;
   const int ncol = N / 2 + 1;
@@ -496,23 +504,31 @@ cudaError_t radiation_field_n(const T* src, T* J, cpx<T>* H, const cpx<T>* tw, d
     cudaFuncSetAttribute(k_fft_strided<T, N, PASS_FWD, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss);
     cudaFuncSetAttribute(k_fft_strided<T, N, PASS_INV, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss);
     cudaFuncSetAttribute(k_fft_strided<T, N, PASS_CONV, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sc);
+    cudaFuncSetAttribute(k_fft_strided<T, N, PASS_CONV, V, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sc);
   }
   const int xgrid = (int)((nrows / 2 + C::XP - 1) / C::XP);
   const int ntx = (ncol + C::SB - 1) / C::SB;
   const int sgrid = N * ntx;
 
-  prof_begin(prof, PK_R2C_X, s);
-  k_fft_r2c_x<T, N, V><<<xgrid, xpass_threads<N, V>(), xs, s>>>(src, H, nrows, RS, tw);
-  prof_end(prof, PK_R2C_X, s);
-  // y-pass: lines (z, kx); element stride RS; outer (z) stride N*RS
-  prof_begin(prof, PK_FFT_Y_FWD, s);
-  k_fft_strided<T, N, PASS_FWD, V><<<sgrid, strided_threads<N, V>(), ss, s>>>(H, RS, (int64_t)N * RS, ncol, ntx, tw,
-                                                                       kf, (T)l_mfp, norm);
-  prof_end(prof, PK_FFT_Y_FWD, s);
+  if (!spec_in) {
+    prof_begin(prof, PK_R2C_X, s);
+    k_fft_r2c_x<T, N, V><<<xgrid, xpass_threads<N, V>(), xs, s>>>(src, H, nrows, RS, tw);
+    prof_end(prof, PK_R2C_X, s);
+    // y-pass: lines (z, kx); element stride RS; outer (z) stride N*RS
+    prof_begin(prof, PK_FFT_Y_FWD, s);
+    k_fft_strided<T, N, PASS_FWD, V><<<sgrid, strided_threads<N, V>(), ss, s>>>(H, RS, (int64_t)N * RS, ncol, ntx,
+                                                                             tw, kf, (T)l_mfp, norm);
+    prof_end(prof, PK_FFT_Y_FWD, s);
+  }
   // z-pass: lines (y, kx); element stride N*RS; outer (y) stride RS
   prof_begin(prof, PK_FFT_Z_CONV, s);
-  k_fft_strided<T, N, PASS_CONV, V><<<sgrid, strided_threads<N, V>(), sc, s>>>(H, (int64_t)N * RS, RS, ncol, ntx, tw,
-                                                                        kf, (T)l_mfp, norm);
+  if (spec_in)
+    k_fft_strided<T, N, PASS_CONV, V, true><<<sgrid, strided_threads<N, V>(), sc, s>>>(
+        H, (int64_t)N * RS, RS, ncol, ntx, tw, kf, (T)l_mfp, norm, spec_in);
+  else
+    k_fft_strided<T, N, PASS_CONV, V><<<sgrid, strided_threads<N, V>(), sc, s>>>(H, (int64_t)N * RS, RS, ncol, ntx,
+                                                                              tw, kf, (T)l_mfp, norm);
   prof_end(prof, PK_FFT_Z_CONV, s);
   prof_begin(prof, PK_FFT_Y_INV, s);
   k_fft_strided<T, N, PASS_INV, V><<<sgrid, strided_threads<N, V>(), ss, s>>>(H, RS, (int64_t)N * RS, ncol, ntx, tw,
@@ -549,6 +565,37 @@ cudaError_t forward_spectrum_n(const T* src, cpx<T>* H, const cpx<T>* tw, cudaSt
                                                                        zero, zero, zero);
   k_fft_strided<T, N, PASS_FWD><<<sgrid, strided_threads<N>(), ss, s>>>(H, (int64_t)N * RS, RS, ncol, ntx, tw,
                                                                        zero, zero, zero);
+  return cudaGetLastError();
+}
+
+// The first two passes of the radiation field: H = the x R2C and forward y
+// transforms of src (z not yet transformed), the spectrum radiation_field_n
+// takes as spec_in.  The tile variant must match the one that later consumes
+// it for bit-identical results (any variant gives the same layout).
+template <typename T, int N, int V = 0>
+cudaError_t source_spectrum_n(const T* src, cpx<T>* H, const cpx<T>* tw, cudaStream_t s, FftProfile* prof) {
+  using C = FftCfg<N, V>;
+  const int RS = N / 2 + 2;
+  const int ncol = N / 2 + 1;
+  const int64_t nrows = (int64_t)N * N;
+  const size_t xs = XSmem<T, N, V>::elems * sizeof(cpx<T>);
+  const size_t ss = StridedSmem<T, N, V>::elems * sizeof(cpx<T>);
+  static std::atomic<unsigned long long> attr_done{0};  // per instantiation and device
+  if (first_use_on_device(attr_done)) {
+    cudaFuncSetAttribute(k_fft_r2c_x<T, N, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xs);
+    cudaFuncSetAttribute(k_fft_strided<T, N, PASS_FWD, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss);
+  }
+  const int xgrid = (int)((nrows / 2 + C::XP - 1) / C::XP);
+  const int ntx = (ncol + C::SB - 1) / C::SB;
+  const int sgrid = N * ntx;
+  const T zero = (T)0;
+  prof_begin(prof, PK_R2C_X, s);
+  k_fft_r2c_x<T, N, V><<<xgrid, xpass_threads<N, V>(), xs, s>>>(src, H, nrows, RS, tw);
+  prof_end(prof, PK_R2C_X, s);
+  prof_begin(prof, PK_FFT_Y_FWD, s);
+  k_fft_strided<T, N, PASS_FWD, V><<<sgrid, strided_threads<N, V>(), ss, s>>>(H, RS, (int64_t)N * RS, ncol, ntx, tw,
+                                                                           zero, zero, zero);
+  prof_end(prof, PK_FFT_Y_FWD, s);
   return cudaGetLastError();
 }
 

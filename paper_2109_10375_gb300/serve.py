@@ -2,12 +2,20 @@
 
 Parameter studies (Sec. 5 of the paper varies z_mid, dz, Az, the source
 threshold and l_mfp over one realisation) reuse most of the work.  The server
-keeps, per realisation and grid, the density field on the device and, per
-(realisation, grid, l_mfp, delta_c), the rank order and the rank-order masses
-that amber_solve_ex leaves behind.  A request that changes only the history
-(z_mid, dz, Az) then runs only the abundance matching
-(amber_assign_zre_ranked); one that changes l_mfp or the threshold reruns the
-source field, the radiation field and the ranking.
+keeps, per realisation and grid, the density field on the device, and two
+levels of cached results:
+
+* per (realisation, grid, delta_c): the transformed source field
+  (amber_source_spectrum: the x and y passes of the forward transform) and
+  the cell masses;
+* per (realisation, grid, l_mfp, delta_c): the rank order and the rank-order
+  masses that the solve leaves behind.
+
+A request that changes only the history (z_mid, dz, Az) runs only the
+abundance matching (amber_assign_zre_ranked).  One that changes l_mfp starts
+from the cached spectrum (amber_solve_spectrum: the z pass with the new
+kernel, the inverse passes, ranking and matching).  One that changes the
+source threshold reruns the source field and both forward passes first.
 
 Continuous batching: each slot is a library context with its own CUDA
 stream.  Requests that arrive while others are on the GPU are admitted as
@@ -42,7 +50,8 @@ class Request:
     # filled by the server
     start: float = math.nan
     done: float = math.nan
-    hit: bool = False
+    hit: bool = False         # history-only: the rank order was cached
+    spec_hit: bool = False    # l_mfp change: the transformed source was cached
     z: torch.Tensor | None = None
 
     @property
@@ -83,27 +92,41 @@ class _Slot:
         self.stream = torch.cuda.Stream(device=device)
         self.event = torch.cuda.Event()
         self.req: Request | None = None
-        # per-slot source and mass scratch, so concurrent misses never share them
+        # per-slot source and output scratch, so concurrent requests never share them
         self.S = torch.empty(max_cells, device=f"cuda:{device}")
-        self.m = torch.empty(max_cells, device=f"cuda:{device}")
         self.z = torch.empty(max_cells, device=f"cuda:{device}")
+        self.held = []
 
 
 class Server:
-    """Continuous-batching server over n_slots contexts on one GPU."""
+    """Continuous-batching server over n_slots contexts on one GPU.
+
+    free_bytes: a callable returning the device's free bytes (default
+    torch.cuda.mem_get_info); admission keeps that above hbm_reserve after a
+    request's new cache entries, evicting unused entries (least recently used
+    first) and otherwise leaving the request queued until running ones end."""
 
     def __init__(self, n_slots: int = 6, max_n: int = 512, cache_bytes: float = 40e9, device: int = 0,
-                 hbm_reserve: float = 8e9, keep_outputs: bool = False):
+                 hbm_reserve: float = 8e9, keep_outputs: bool = False, free_bytes=None):
         self.device = device
         self.slots = [_Slot(max_n ** 3, device) for _ in range(n_slots)]
-        # key -> [order, mass_rank, bytes, running users, event recorded after it was written]
+        # key -> [tensors, bytes, running users, event recorded after it was written]
+        # ("order", r, n, l, dc): (order, mass_rank); ("spec", r, n, dc): (spectrum, mass)
         self.cache = collections.OrderedDict()
         self.cache_bytes = cache_bytes
         self.cached = 0
         self.fields = {}  # (realisation, n) -> density field on the device
         self.hbm_reserve = hbm_reserve
         self.keep_outputs = keep_outputs
-        self.waiting_hbm = 0
+        self.free_bytes = free_bytes or self._device_free_bytes
+        self.waited = set()  # requests that had to wait for HBM at least once
+        self.evictions = 0
+
+    def _device_free_bytes(self) -> int:
+        """Free device memory: the driver's free bytes plus what torch's caching
+        allocator holds reserved but unused (evicted entries return there)."""
+        free, _ = torch.cuda.mem_get_info(self.device)
+        return free + torch.cuda.memory_reserved(self.device) - torch.cuda.memory_allocated(self.device)
 
     # --- inputs ---------------------------------------------------------------
     def _field(self, r: int, n: int):
@@ -120,71 +143,111 @@ class Server:
         torch.cuda.synchronize()
 
     # --- admission --------------------------------------------------------------
-    def _entry_bytes(self, n):
+    @staticmethod
+    def _order_key(q: Request):
+        return ("order", q.realisation, q.n, q.l_mfp, q.delta_c)
+
+    @staticmethod
+    def _spec_key(q: Request):
+        return ("spec", q.realisation, q.n, q.delta_c)
+
+    @staticmethod
+    def _order_bytes(n):
         return 8 * n ** 3  # order + rank-order masses
 
+    @staticmethod
+    def _spec_bytes(n):
+        return B.spectrum_bytes(n) + 4 * n ** 3  # transformed source + masses
+
+    def _need(self, q: Request) -> int:
+        """Bytes of the cache entries q would add."""
+        if self._order_key(q) in self.cache:
+            return 0
+        need = self._order_bytes(q.n) + (4 * q.n ** 3 if self.keep_outputs else 0)
+        if self._spec_key(q) not in self.cache:
+            need += self._spec_bytes(q.n)
+        return need
+
     def _admissible(self, q: Request) -> bool:
-        key = (q.realisation, q.n, q.l_mfp, q.delta_c)
-        if key in self.cache:
+        need = self._need(q)
+        if need == 0:
             return True
-        need = self._entry_bytes(q.n) + 4 * q.n ** 3
-        free, _ = torch.cuda.mem_get_info(self.device)
-        while self.cached + need > self.cache_bytes or free - need < self.hbm_reserve:
-            if not self._evict_one():
+        protect = {self._order_key(q), self._spec_key(q)}
+        while self.cached + need > self.cache_bytes or self.free_bytes() - need < self.hbm_reserve:
+            if not self._evict_one(protect):
                 return False
-            free, _ = torch.cuda.mem_get_info(self.device)
         return True
 
-    def _evict_one(self) -> bool:
+    def _evict_one(self, protect=()) -> bool:
         for k, v in self.cache.items():
-            if v[3] == 0:  # not in use by a running request
+            if v[2] == 0 and k not in protect:  # not in use by a running request
                 self.cache.pop(k)
-                self.cached -= v[2]
+                self.cached -= v[1]
+                self.evictions += 1
                 return True
         return False
+
+    def _put(self, key, tensors, nbytes, stream):
+        ready = torch.cuda.Event()
+        ready.record(stream)
+        self.cache[key] = [tensors, nbytes, 1, ready]
+        self.cached += nbytes
+
+    def _use(self, key, stream):
+        ent = self.cache[key]
+        self.cache.move_to_end(key)
+        ent[2] += 1
+        stream.wait_event(ent[3])  # the entry may still be being written by another slot
+        return ent[0]
 
     # --- execution --------------------------------------------------------------
     def _launch(self, slot: _Slot, q: Request, now: float):
         n = q.n
         box = BOX_PER_CELL.get(n, 100.0 / 128) * n
         h = B.history(*q.history)
-        key = (q.realisation, n, q.l_mfp, q.delta_c)
-        d = self._field(q.realisation, n)
-        z = torch.empty((n, n, n), device=f"cuda:{self.device}") if self.keep_outputs else None
+        okey, skey = self._order_key(q), self._spec_key(q)
+        dev = f"cuda:{self.device}"
+        z = torch.empty((n, n, n), device=dev) if self.keep_outputs else None
         zbuf = z if z is not None else slot.z[: n ** 3].view(n, n, n)
+        held = []
         with torch.cuda.stream(slot.stream):
-            if key in self.cache:
-                ent = self.cache[key]
-                self.cache.move_to_end(key)
-                ent[3] += 1
-                slot.stream.wait_event(ent[4])  # the entry may still be being written by another slot
-                slot.ctx.assign_zre_ranked(ent[0], ent[1], h, zbuf.view(-1), stream=slot.stream)
+            if okey in self.cache:
+                # history only: the matching over the cached ranking
+                order, mrank = self._use(okey, slot.stream)
+                held.append(okey)
+                slot.ctx.assign_zre_ranked(order, mrank, h, zbuf.view(-1), stream=slot.stream)
                 q.hit = True
             else:
-                # a new l_mfp or threshold: source field, radiation field, rank
-                S = slot.S[: n ** 3].view(n, n, n)
-                m = slot.m[: n ** 3].view(n, n, n)
-                slot.ctx.source_field(d, q.delta_c, 0.7, out=S, mass_out=m, stream=slot.stream)
-                order = torch.empty(n ** 3, dtype=torch.int32, device=f"cuda:{self.device}")
-                mrank = torch.empty(n ** 3, device=f"cuda:{self.device}")
-                slot.ctx.solve_ex(S, m, box, q.l_mfp, h, zbuf, order, mrank, stream=slot.stream)
-                ready = torch.cuda.Event()
-                ready.record(slot.stream)
-                nbytes = self._entry_bytes(n)
-                self.cache[key] = [order, mrank, nbytes, 1, ready]
-                self.cached += nbytes
+                if skey in self.cache:
+                    # a new l_mfp: the z pass onward from the cached spectrum
+                    spec, m = self._use(skey, slot.stream)
+                    q.spec_hit = True
+                else:
+                    # a new threshold: source field and the two forward passes, kept
+                    S = slot.S[: n ** 3].view(n, n, n)
+                    m = torch.empty((n, n, n), device=dev)
+                    slot.ctx.source_field(self._field(q.realisation, n), q.delta_c, 0.7, out=S, mass_out=m,
+                                          stream=slot.stream)
+                    spec = slot.ctx.source_spectrum(S, stream=slot.stream)
+                    self._put(skey, (spec, m), self._spec_bytes(n), slot.stream)
+                held.append(skey)
+                order = torch.empty(n ** 3, dtype=torch.int32, device=dev)
+                mrank = torch.empty(n ** 3, device=dev)
+                slot.ctx.solve_spectrum(spec, m, box, q.l_mfp, h, zbuf, order, mrank, stream=slot.stream)
+                self._put(okey, (order, mrank), self._order_bytes(n), slot.stream)
+                held.append(okey)
             slot.event.record(slot.stream)
         q.start = now
         q.z = z
         slot.req = q
-        slot.key = key
+        slot.held = held
 
     def _finish(self, slot: _Slot, now: float):
         q = slot.req
         q.done = now
-        k = slot.key
-        if k in self.cache:
-            self.cache[k][3] = max(0, self.cache[k][3] - 1)
+        for k in slot.held:
+            if k in self.cache:
+                self.cache[k][2] = max(0, self.cache[k][2] - 1)
         slot.req = None
 
     def run(self, requests, realtime: bool = True):
@@ -202,7 +265,10 @@ class Server:
             for s in self.slots:
                 if s.req is None and queue:
                     if not self._admissible(queue[0]):
-                        self.waiting_hbm += 1
+                        if all(x.req is None for x in self.slots):
+                            raise RuntimeError(f"request {queue[0].rid} ({queue[0].n}^3) does not fit the HBM "
+                                               "budget even with every cache entry evicted")
+                        self.waited.add(queue[0].rid)  # queued until a running request ends
                         break
                     self._launch(s, queue.popleft(), time.perf_counter() - t0)
             if not queue and pending and realtime:
@@ -215,6 +281,10 @@ class Server:
             if st != 0:
                 raise RuntimeError(f"device status {B.status_string(st)}")
         return requests
+
+    @property
+    def waiting_hbm(self) -> int:
+        return len(self.waited)
 
     def close(self):
         for s in self.slots:
@@ -230,4 +300,5 @@ def summarize(requests) -> dict:
     return {"requests": len(requests), "p50_ms": float(np.percentile(lat, 50)),
             "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()),
             "cells_per_s": cells / span, "hit_rate": float(np.mean([q.hit for q in requests])),
+            "spectrum_hit_rate": float(np.mean([q.spec_hit for q in requests])),
             "makespan_s": span}

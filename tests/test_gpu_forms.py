@@ -133,3 +133,63 @@ def test_serving_results_same_alone_and_in_the_mix(B):
     So, mo = O.source_field(d, q.delta_c, 0.7)
     _, _, zo = O.solve(So, mo, box, q.l_mfp, *q.history)
     assert np.mean(np.abs(q.z.cpu().numpy().reshape(-1) - zo) > 1e-3) <= 1e-4
+
+
+@pytest.mark.parametrize("n,variant", [(32, 0), (64, 0), (128, 0), (128, 1)])
+def test_solve_from_a_kept_spectrum_equals_the_full_solve(B, n, variant):
+    # amber_source_spectrum + amber_solve_spectrum (two l_mfp values from one
+    # kept spectrum) against amber_solve_ex on the source field: bit-equal
+    box = 100.0 * n / 128
+    S, m = synth.realisation(n, box, 5, device="cuda")
+    h = B.history(7.5, 4.0, 3.0)
+    with B.Context(n ** 3) as ctx:
+        ctx.set_tuning(n, fft_variant=variant)
+        spec = ctx.source_spectrum(S)
+        assert spec.numel() == B.spectrum_bytes(n) == n * n * (n // 2 + 2) * 8
+        kept = spec.clone()
+        for l in (3.0, 11.0):
+            outs = []
+            for from_spec in (False, True):
+                z = torch.empty_like(S)
+                J = torch.empty_like(S)
+                order = torch.empty(n ** 3, dtype=torch.int32, device="cuda")
+                mr = torch.empty(n ** 3, device="cuda")
+                if from_spec:
+                    ctx.solve_spectrum(spec, m, box, l, h, z, order, mr, J_out=J)
+                else:
+                    ctx.solve_ex(S, m, box, l, h, z, order, mr, J_out=J)
+                outs.append((z, J, order, mr))
+            assert ctx.sync_status() == 0
+            for a, b in zip(*outs):
+                assert torch.equal(a, b)
+        assert torch.equal(spec, kept)  # read only
+
+
+def test_serving_admission_waits_and_evicts_with_the_same_results(B):
+    # a device-memory budget that holds the cache entries of only a couple of
+    # requests at a time: requests wait for running ones to end, entries are
+    # evicted, and every result is the one the request gets alone
+    from paper_2109_10375_gb300 import serve
+    reqs = serve.poisson_requests(30, rate=3000.0, seed=13, sizes=(32, 64), size_p=(0.4, 0.6), n_realisations=3)
+
+    def clone(qs):
+        return [serve.Request(q.rid, q.arrival, q.realisation, q.n, q.l_mfp, q.delta_c, q.history) for q in qs]
+
+    alone = clone(reqs)
+    srv = serve.Server(n_slots=1, max_n=64, cache_bytes=1e9, hbm_reserve=0, keep_outputs=True)
+    srv.prepare(alone)
+    for q in alone:
+        srv.run([q], realtime=False)
+    srv.close()
+    tight = clone(reqs)
+    srv = serve.Server(n_slots=4, max_n=64, cache_bytes=1e9, hbm_reserve=0, keep_outputs=True)
+    miss64 = srv._order_bytes(64) + srv._spec_bytes(64) + 4 * 64 ** 3
+    budget = int(2.5 * miss64)
+    srv.free_bytes = lambda: budget - srv.cached
+    srv.prepare(tight)
+    srv.run(tight, realtime=True)
+    waits, evictions = srv.waiting_hbm, srv.evictions
+    srv.close()
+    assert waits > 0 and evictions > 0, (waits, evictions)
+    for a, b in zip(alone, tight):
+        assert torch.equal(a.z, b.z), a.rid
