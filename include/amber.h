@@ -21,7 +21,8 @@
  *    such as J + 1 is fine).
  *  - `stream` is a cudaStream_t passed as void*; NULL means the legacy default
  *    stream.  All device work is asynchronous on that stream; no call
- *    allocates device memory after amber_create.
+ *    allocates device memory after amber_create (amber_batch_create
+ *    allocates its batch's own workspace).
  *  - Return values are amber_status codes.  Argument errors are detected on
  *    the host and returned immediately with nothing enqueued.  Errors found by
  *    kernels (non-finite intensity, invalid mass, a lookback wait that ran
@@ -276,17 +277,31 @@ int amber_set_tuning(amber_ctx *ctx, const amber_tuning_t *t);
 /* The current choices for size n. */
 int amber_get_tuning(amber_ctx *ctx, int n, amber_tuning_t *out);
 
-/* Batched solves: one captured CUDA graph replays many amber_solve calls.
- * Item i runs on ctxs[i % nctx], each context on its own stream forked from
- * and joined into one origin, so small realisations overlap on the GPU and
- * the whole batch costs one host launch.  Items are validated before the
- * capture (same rules as amber_solve, precision 32).  Before capturing, each
- * grid size not yet tuned on the first context is autotuned on the first item
- * of that size (amber_autotune), and the choices are copied to every context
- * of the batch; AMBER_AUTOTUNE=0 in the environment skips this.  The graph records the
- * given device pointers and parameters: buffers and contexts must stay
- * alive while the batch exists, and a context must not run other work while
- * the batch runs. */
+/* Batched solves: many realisations of mixed grid sizes, every stage of
+ * every item in one launch per stage, captured once into a CUDA graph.
+ *  - The transforms run one launch per pass and grid size (the items of a
+ *    size back to back), the ranking one histogram, one digit-offset and one
+ *    launch per digit pass per digit width, the matching one thresholds, one
+ *    scan per weighting form and one scatter launch for all items.  Inside a
+ *    launch each CTA finds its item from a prefix of the items' tile counts;
+ *    ticket-ordered kernels (digit passes, scan) take tiles from the item's
+ *    own ticket, so their look-backs stay within the item.  The graph's
+ *    kernel nodes number about 5 per grid size plus 6 per digit width plus
+ *    4, whatever the item count (amber_batch_kernel_nodes).
+ *  - The batch allocates its own workspace at creation (about 30 bytes per
+ *    cell of all items together, plus the items' arguments); amber_batch_create
+ *    and amber_create are the only calls that allocate.
+ *  - ctxs[0] gives the device, the FFT twiddles (its max_cells must hold the
+ *    largest grid), the status word that amber_sync_status(ctxs[0]) reads and
+ *    the tuning; each grid size not yet tuned on ctxs[0] is autotuned on its
+ *    first item (amber_autotune) unless AMBER_AUTOTUNE=0 is set, and the
+ *    choices are copied to every context given.  Other contexts do no work.
+ *  - Items are validated before anything runs (the rules of amber_solve,
+ *    precision 32, and n >= 8).  Results equal amber_solve's on ctxs[0] with
+ *    the same tuning, bit for bit.
+ *  - The graph records the given device pointers and parameters: the items'
+ *    buffers and ctxs[0] must stay alive while the batch exists, and ctxs[0]
+ *    must not run other work while the batch runs. */
 typedef struct {
   const float *d_src;
   const float *d_mass;
@@ -297,6 +312,8 @@ typedef struct amber_batch amber_batch;
 int amber_batch_create(amber_batch **batch, amber_ctx *const *ctxs, int nctx, const amber_batch_item *items,
                        int nitems);
 int amber_batch_launch(amber_batch *batch, void *stream);
+/* Kernel nodes in the batch's graph (host only). */
+int amber_batch_kernel_nodes(amber_batch *batch, int *out_nodes);
 int amber_batch_destroy(amber_batch *batch);
 
 /* FP64 intensity variant (p->precision == 64, n <= 256): d_src n^3 doubles,

@@ -34,7 +34,7 @@ EXPORTED = [
     "amber_lpt_displacement", "amber_mesh_density", "amber_esf_fcoll", "amber_sigma2_tophat",
     "amber_solve_tomographic", "amber_autotune", "amber_set_tuning", "amber_get_tuning",
     "amber_rank_noalloc", "amber_power_derived", "amber_spectrum_bytes", "amber_source_spectrum",
-    "amber_solve_spectrum",
+    "amber_solve_spectrum", "amber_batch_kernel_nodes",
 ]
 
 
@@ -108,6 +108,7 @@ def _load():
         "amber_batch_create": (i32, [C.POINTER(vp), C.POINTER(vp), i32, C.POINTER(amber_batch_item), i32]),
         "amber_batch_launch": (i32, [vp, vp]),
         "amber_batch_destroy": (i32, [vp]),
+        "amber_batch_kernel_nodes": (i32, [vp, C.POINTER(i32)]),
         "amber_delta_z": (i32, [vp, vp, i64, vp, vp, vp]),
         "amber_epsilon_z_pdf": (i32, [vp, vp, vp, i64, dbl, dbl, i32, vp, vp, vp]),
         "amber_power_bins": (i32, [i32, C.POINTER(i32)]),
@@ -224,7 +225,7 @@ def params(n: int, box: float, l_mfp: float, h: amber_history_t, precision: int 
 
 
 class Batch:
-    """One CUDA graph replaying many solves spread over several contexts."""
+    """Many solves in one captured CUDA graph of one launch per stage (see amber_batch_create)."""
 
     def __init__(self, ctxs, items):
         """items: (S, mass, box, l_mfp, history, z_out) tuples of device tensors."""
@@ -239,6 +240,11 @@ class Batch:
 
     def launch(self, stream=None):
         _check(lib.amber_batch_launch(self._h, _stream(stream)), "amber_batch_launch")
+
+    def kernel_nodes(self) -> int:
+        out = C.c_int()
+        _check(lib.amber_batch_kernel_nodes(self._h, C.byref(out)), "amber_batch_kernel_nodes")
+        return out.value
 
     def close(self):
         if self._h:

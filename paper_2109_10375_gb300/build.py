@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libamber.so")
-SOURCES = ["amber_host.cu", "fft_f32.cu", "fft_f64.cu", "sort.cu", "assign.cu", "source.cu", "spectra.cu", "lpt.cu", "noalloc.cu"]
+SOURCES = ["amber_host.cu", "fft_f32.cu", "fft_multi_f32.cu", "fft_f64.cu", "sort.cu", "assign.cu", "source.cu", "spectra.cu", "lpt.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

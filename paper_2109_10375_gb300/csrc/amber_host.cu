@@ -27,6 +27,9 @@ cudaError_t radiation_field_f32(int n, const float* src, float* J, void* H, cons
                                int variant, const void* spec_in = nullptr);
 cudaError_t source_spectrum_f32(int n, const float* src, void* H, const void* tw, cudaStream_t s, FftProfile* prof,
                                int variant);
+cudaError_t radiation_field_multi_f32(int n, int variant, const float* const* srcs, int M, float* J, void* H,
+                                      const void* tw, const float* kp, unsigned int* status, cudaStream_t s,
+                                      SortCtrl* kranges);
 cudaError_t radiation_field_f64(int n, const double* src, double* J, void* H, const void* tw, double box,
                                double l_mfp, unsigned int* status, cudaStream_t s, FftProfile* prof,
                                SortCtrl* krange);
@@ -270,6 +273,30 @@ int cuda_status(cudaError_t e) {
   if (e == cudaSuccess) return AMBER_OK;
   return AMBER_ERR_CUDA;
 }
+
+}  // namespace
+
+namespace {
+
+// Bump allocator over one device allocation (256-byte aligned pieces).
+struct Layout {
+  size_t total = 0;
+  size_t take(size_t bytes) {
+    const size_t at = total;
+    total += align256(bytes);
+    return at;
+  }
+};
+
+// Host copy of a device argument array, placed at `off` in the workspace.
+struct HostBlob {
+  size_t off = 0;
+  std::vector<unsigned char> bytes;
+  template <typename T> void set(const std::vector<T>& v) {
+    bytes.resize(v.size() * sizeof(T));
+    if (!v.empty()) std::memcpy(bytes.data(), v.data(), bytes.size());
+  }
+};
 
 }  // namespace
 
@@ -904,84 +931,343 @@ int amber_assign_zre_ranked(amber_ctx* c, const uint32_t* d_order, const float* 
 }
 
 // ---------------------------------------------------------------------------
-// Batched solves replayed from one captured CUDA graph.
+// Batched solves: every stage of every item in one launch per stage (per grid
+// size for the transforms, per digit width for the sort), captured once.
 // ---------------------------------------------------------------------------
 struct amber_batch {
   int device = 0;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   std::vector<amber_ctx*> ctxs;
+  unsigned char* ws = nullptr;    // the batch's own workspace (all items at once)
+  unsigned char* args = nullptr;  // the items' kernel arguments
+  int kernel_nodes = 0;
 };
+
 
 int amber_batch_create(amber_batch** out, amber_ctx* const* ctxs, int nctx, const amber_batch_item* items,
                        int nitems) {
   if (!out || !ctxs || nctx < 1 || !items || nitems < 1) return AMBER_ERR_INVALID_ARG;
   *out = nullptr;
-  std::vector<HistoryCoeffs> hcs(nitems);
-  const int dev = ctxs[0] ? ctxs[0]->device : -1;
+  amber_ctx* c0 = ctxs[0];
   for (int k = 0; k < nctx; ++k)
-    if (!ctxs[k] || ctxs[k]->device != dev) return AMBER_ERR_INVALID_ARG;
+    if (!ctxs[k] || ctxs[k]->device != (c0 ? c0->device : -1)) return AMBER_ERR_INVALID_ARG;
+  std::vector<HistoryCoeffs> hcs(nitems);
   for (int i = 0; i < nitems; ++i) {
-    amber_ctx* c = ctxs[i % nctx];
-    const int st = solve_args(c, items[i].d_src, items[i].d_mass, &items[i].params, items[i].d_zre, 32, c->plan.n32,
-                              &hcs[i]);
+    const int st = solve_args(c0, items[i].d_src, items[i].d_mass, &items[i].params, items[i].d_zre, 32,
+                              c0->plan.n32, &hcs[i]);
     if (st) return st;
+    if (items[i].params.n < 8) return AMBER_ERR_INVALID_ARG;  // x-pass tiles span whole items from 8^3 up
   }
-  std::vector<std::unique_lock<std::mutex>> locks;
-  for (int k = 0; k < nctx; ++k) locks.emplace_back(ctxs[k]->mu);
-  DeviceGuard g(dev);
-  // each size not yet tuned: autotune on its first item, then share the
-  // choices with every context of the batch
+  std::lock_guard<std::mutex> lk(c0->mu);
+  DeviceGuard g(c0->device);
+  // each size not yet tuned: autotune on its first item
   for (int i = 0; i < nitems && autotune_enabled(); ++i) {
     const int n = items[i].params.n, lg = ilog2i(n);
-    if (ctxs[0]->tune[lg].tuned) continue;
-    amber_ctx* c = ctxs[i % nctx];
-    const int st = autotune_locked(c, items[i].d_src, items[i].d_mass, n, items[i].params.box,
+    if (c0->tune[lg].tuned) continue;
+    const int st = autotune_locked(c0, items[i].d_src, items[i].d_mass, n, items[i].params.box,
                                    items[i].params.l_mfp, nullptr, nullptr);
     if (st) return st;
-    for (int k = 0; k < nctx; ++k) ctxs[k]->tune[lg] = c->tune[lg];
+  }
+  // every context of the batch carries the choices the batch runs with
+  for (int k = 1; k < nctx; ++k) {
+    if (ctxs[k] == c0) continue;
+    std::lock_guard<std::mutex> lk2(ctxs[k]->mu);
+    for (int i = 0; i < nitems; ++i) {
+      const int lg = ilog2i(items[i].params.n);
+      ctxs[k]->tune[lg] = c0->tune[lg];
+    }
+  }
+  // items ordered by grid size: one size's spectra and intensities lie back to back
+  std::vector<int> ord(nitems);
+  for (int i = 0; i < nitems; ++i) ord[i] = i;
+  std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return items[a].params.n < items[b].params.n; });
+
+  // ---- workspace plan
+  Layout L;
+  struct ItemWs {
+    int64_t C;
+    size_t J, kA, iA, iB, mA, mB, spec, lb, actrl, Xq, inv, lin, state, btab, tmass;
+    int64_t sort_tiles, scan_tiles;
+    int nbuckets;
+  };
+  std::vector<ItemWs> iw(nitems);
+  int64_t cells = 0;
+  for (int i : ord) cells += (int64_t)items[i].params.n * items[i].params.n * items[i].params.n;
+  // per-cell arrays: one run per kind, items in size order
+  const size_t offJ = L.take(cells * 4), offKA = L.take(cells * 4), offIA = L.take(cells * 4),
+               offIB = L.take(cells * 4), offMA = L.take(cells * 4), offMB = L.take(cells * 4);
+  size_t spec_total = 0;
+  for (int i : ord) {
+    const int n = items[i].params.n;
+    spec_total += (size_t)n * n * (n / 2 + 2) * 8;
+  }
+  const size_t offSpec = L.take(spec_total);
+  const size_t offCtrl = L.take((size_t)nitems * sizeof(SortCtrl));  // one control block per item, in size order
+  const size_t offACtrl = L.take((size_t)nitems * kAssignCtrlBytes);
+  {
+    int64_t co = 0;
+    size_t so = 0;
+    for (int i : ord) {
+      const int n = items[i].params.n;
+      ItemWs& w = iw[i];
+      w.C = (int64_t)n * n * n;
+      w.J = offJ + co * 4;
+      w.kA = offKA + co * 4;
+      w.iA = offIA + co * 4;
+      w.iB = offIB + co * 4;
+      w.mA = offMA + co * 4;
+      w.mB = offMB + co * 4;
+      w.spec = offSpec + so;
+      co += w.C;
+      so += (size_t)n * n * (n / 2 + 2) * 8;
+    }
+  }
+  size_t state_total = 0;
+  for (int i : ord) {
+    ItemWs& w = iw[i];
+    w.sort_tiles = sort_tiles(w.C);
+    w.scan_tiles = (w.C + kScanTile - 1) / kScanTile;
+    int shift;
+    bucket_plan(w.C, &w.nbuckets, &shift);
+    state_total += align256((size_t)w.scan_tiles * 8);
+  }
+  const size_t offState = L.take(state_total);  // scan look-back words of every item (one memset)
+  {
+    size_t so = 0;
+    for (int i : ord) {
+      ItemWs& w = iw[i];
+      w.state = offState + so;
+      so += align256((size_t)w.scan_tiles * 8);
+      w.lb = L.take(2 * sort_lookback_words(w.C) * 4);
+      w.Xq = L.take((size_t)hcs[i].n_table * 8);
+      w.inv = L.take((size_t)hcs[i].n_table * 4);
+      w.lin = L.take((size_t)4 * kMaxTable * 4);
+      w.btab = L.take((size_t)w.scan_tiles * (w.nbuckets + 1) * 2);
+      w.tmass = L.take((size_t)w.sort_tiles * 16);
+    }
+  }
+  // per-item argument arrays (device copies of host-built structs)
+  std::vector<int> sizes, rbs;
+  for (int i : ord) {
+    const int n = items[i].params.n;
+    if (sizes.empty() || sizes.back() != n) sizes.push_back(n);
+  }
+  for (int n : sizes) {
+    const int rb = c0->tune[ilog2i(n)].sort_digit_bits;
+    if (std::find(rbs.begin(), rbs.end(), rb) == rbs.end()) rbs.push_back(rb);
   }
   amber_batch* b = new (std::nothrow) amber_batch();
   if (!b) return AMBER_ERR_OOM;
-  b->device = dev;
+  b->device = c0->device;
   b->ctxs.assign(ctxs, ctxs + nctx);
-  std::vector<bool> prof_on(nctx);
-  for (int k = 0; k < nctx; ++k) { prof_on[k] = ctxs[k]->prof.on; ctxs[k]->prof.on = false; }
+  if (cudaMalloc(&b->ws, L.total) != cudaSuccess) {
+    cudaGetLastError();
+    delete b;
+    return AMBER_ERR_OOM;
+  }
+  unsigned char* W = b->ws;
+  // the argument arrays hold addresses in W; they are laid out here, then
+  // copied to a second allocation once complete
+  Layout A;
+  std::vector<HostBlob> blobs;
+  auto place = [&](auto vec) -> size_t {
+    HostBlob hb;
+    hb.set(vec);
+    hb.off = A.take(hb.bytes.size() ? hb.bytes.size() : 16);
+    blobs.push_back(std::move(hb));
+    return blobs.back().off;
+  };
+
+  SortCtrl* ctrl_base = reinterpret_cast<SortCtrl*>(W + offCtrl);
+  std::vector<SortWork> sw(nitems);
+  std::vector<AssignWork> aw(nitems);
+  std::vector<int> pos(nitems);  // position of item i in size order
+  for (int k = 0; k < nitems; ++k) pos[ord[k]] = k;
+  for (int i = 0; i < nitems; ++i) {
+    const ItemWs& w = iw[i];
+    SortWork& s = sw[i];
+    s.keysA = W + w.kA;
+    s.keysB = W + w.J;  // the intensity, dead after the first digit pass
+    s.idxA = reinterpret_cast<uint32_t*>(W + w.iA);
+    s.idxB = reinterpret_cast<uint32_t*>(W + w.iB);
+    s.massA = reinterpret_cast<float*>(W + w.mA);
+    s.massB = reinterpret_cast<float*>(W + w.mB);
+    s.lookback = reinterpret_cast<uint32_t*>(W + w.lb);
+    s.ctrl = ctrl_base + pos[i];
+    s.max_cells = w.C;
+    s.num_sms = c0->num_sms;
+    AssignWork& a = aw[i];
+    a.ctrl = W + offACtrl + (size_t)pos[i] * kAssignCtrlBytes;
+    a.Xq = reinterpret_cast<unsigned long long*>(W + w.Xq);
+    a.inv_dx = reinterpret_cast<float*>(W + w.inv);
+    a.lin = reinterpret_cast<float*>(W + w.lin);
+    a.state = reinterpret_cast<unsigned long long*>(W + w.state);
+    a.bcell = reinterpret_cast<uint32_t*>(s.keysA);
+    a.bz = reinterpret_cast<float*>(s.keysB);
+    a.btab = reinterpret_cast<uint16_t*>(W + w.btab);
+    a.num_sms = c0->num_sms;
+  }
+
+  // ---- transforms: per size, the sources, kf and l_mfp of its items
+  struct FftGroup { int n, M, first; size_t srcs, kp; };
+  std::vector<FftGroup> fg;
+  for (int n : sizes) {
+    FftGroup f{n, 0, -1, 0, 0};
+    std::vector<const float*> srcs;
+    std::vector<float> kp;
+    for (int k = 0; k < nitems; ++k) {
+      const int i = ord[k];
+      if (items[i].params.n != n) continue;
+      if (f.first < 0) f.first = i;
+      ++f.M;
+      srcs.push_back(items[i].d_src);
+      kp.push_back((float)(2.0 * 3.14159265358979323846 / items[i].params.box));
+      kp.push_back((float)items[i].params.l_mfp);
+    }
+    f.srcs = place(srcs);
+    f.kp = place(kp);
+    fg.push_back(f);
+  }
+  // ---- sort: per digit width, the items' histogram and pass arguments
+  struct SortGroup { int rb, match; RankMulti r; size_t hist, hpre, pass[4], tpre; };
+  std::vector<SortGroup> sg;
+  std::vector<unsigned long long*> tile_mass(nitems);
+  for (int i = 0; i < nitems; ++i) tile_mass[i] = reinterpret_cast<unsigned long long*>(W + iw[i].tmass);
+  for (int rb : rbs) {
+    SortGroup q{};
+    q.rb = rb;
+    std::vector<HistArgs> hist;
+    std::vector<uint32_t> hpre{0}, tpre{0};
+    std::vector<PassArgs> pass[4];
+    for (int k = 0; k < nitems; ++k) {
+      const int i = ord[k];
+      const amber_tuning_t& tu = c0->tune[ilog2i(items[i].params.n)];
+      if (tu.sort_digit_bits != rb) continue;
+      q.match = tu.sort_match;
+      HistArgs h;
+      uint32_t hb;
+      PassArgs pa[4];
+      const int P = rank_args<float>(sw[i], reinterpret_cast<const float*>(sw[i].keysB), iw[i].C, nullptr,
+                                     items[i].d_mass, nullptr, tile_mass[i], c0->status, kSpinLimit, rb, &h, &hb, pa);
+      for (int p = 0; p < 4; ++p) pass[p].push_back(pa[p < P ? p : P - 1]);
+      hist.push_back(h);
+      hpre.push_back(hpre.back() + hb);
+      tpre.push_back(tpre.back() + (uint32_t)iw[i].sort_tiles);
+    }
+    q.r.M = (int)hist.size();
+    q.r.hist_blocks = hpre.back();
+    q.r.tiles = tpre.back();
+    q.hist = place(hist);
+    q.hpre = place(hpre);
+    for (int p = 0; p < 4; ++p) q.pass[p] = place(pass[p]);
+    q.tpre = place(tpre);
+    sg.push_back(q);
+  }
+  // ---- matching: thresholds and scatter for every item, scans per weighting form
+  AssignMulti am{};
+  size_t o_thresh, o_scan[2], o_spre[2], o_scatter, o_xpre;
+  {
+    std::vector<ThreshArgs> th;
+    std::vector<ScanArgs> sc[2];
+    std::vector<uint32_t> spre[2] = {{0}, {0}}, xpre{0};
+    std::vector<ScatterArgs> xs;
+    for (int k = 0; k < nitems; ++k) {
+      const int i = ord[k];
+      ThreshArgs ta;
+      ScanArgs sa;
+      ScatterArgs xa;
+      assign_args(aw[i], sw[i].idxA, sw[i].massA, tile_mass[i], iw[i].C, hcs[i], items[i].d_zre, nullptr, c0->status,
+                  kSpinLimit, sw[i].idxB, sw[i].massB, &sw[i].ctrl->npasses, &ta, &sa, &xa);
+      th.push_back(ta);
+      const int f = hcs[i].weighting != AMBER_WEIGHT_MASS ? 1 : 0;
+      sc[f].push_back(sa);
+      spre[f].push_back(spre[f].back() + (uint32_t)iw[i].scan_tiles);
+      xs.push_back(xa);
+      xpre.push_back(xpre.back() + (uint32_t)(xa.groups * xa.nbuckets));
+    }
+    am.M = nitems;
+    for (int f = 0; f < 2; ++f) {
+      am.Mg[f] = (int)sc[f].size();
+      am.scan_tiles[f] = spre[f].back();
+      o_scan[f] = place(sc[f]);
+      o_spre[f] = place(spre[f]);
+    }
+    am.scatter_blocks = xpre.back();
+    o_thresh = place(th);
+    o_scatter = place(xs);
+    o_xpre = place(xpre);
+  }
+  cudaError_t e = cudaMalloc(&b->args, A.total);
+  unsigned char* G = b->args;
+  for (const HostBlob& hb : blobs)
+    if (e == cudaSuccess && !hb.bytes.empty()) e = cudaMemcpy(G + hb.off, hb.bytes.data(), hb.bytes.size(),
+                                                               cudaMemcpyHostToDevice);
+  am.thresh = reinterpret_cast<const ThreshArgs*>(G + o_thresh);
+  for (int f = 0; f < 2; ++f) {
+    am.scan[f] = reinterpret_cast<const ScanArgs*>(G + o_scan[f]);
+    am.scan_prefix[f] = reinterpret_cast<const uint32_t*>(G + o_spre[f]);
+  }
+  am.scatter = reinterpret_cast<const ScatterArgs*>(G + o_scatter);
+  am.scatter_prefix = reinterpret_cast<const uint32_t*>(G + o_xpre);
+  for (SortGroup& q : sg) {
+    q.r.hist = reinterpret_cast<const HistArgs*>(G + q.hist);
+    q.r.hist_prefix = reinterpret_cast<const uint32_t*>(G + q.hpre);
+    for (int p = 0; p < 4; ++p) q.r.pass[p] = reinterpret_cast<const PassArgs*>(G + q.pass[p]);
+    q.r.tile_prefix = reinterpret_cast<const uint32_t*>(G + q.tpre);
+  }
+
+  // ---- capture: every stage once
+  const bool prof_on = c0->prof.on;
+  c0->prof.on = false;
   cudaStream_t origin = nullptr;
-  std::vector<cudaStream_t> ws(nctx, nullptr);
-  std::vector<cudaEvent_t> ev(nctx + 1, nullptr);
-  cudaError_t e = cudaStreamCreateWithFlags(&origin, cudaStreamNonBlocking);
-  for (int k = 0; k < nctx && e == cudaSuccess; ++k) e = cudaStreamCreateWithFlags(&ws[k], cudaStreamNonBlocking);
-  for (int k = 0; k <= nctx && e == cudaSuccess; ++k) e = cudaEventCreateWithFlags(&ev[k], cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&origin, cudaStreamNonBlocking);
   bool capturing = false;
   if (e == cudaSuccess) {
     e = cudaStreamBeginCapture(origin, cudaStreamCaptureModeRelaxed);
     capturing = e == cudaSuccess;
   }
-  if (e == cudaSuccess) e = cudaEventRecord(ev[nctx], origin);
-  for (int k = 0; k < nctx && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(ws[k], ev[nctx], 0);
-  for (int i = 0; i < nitems && e == cudaSuccess; ++i) {
-    const int k = i % nctx;
-    e = solve_f32_enqueue(ctxs[k], items[i].d_src, items[i].d_mass, &items[i].params, hcs[i], items[i].d_zre, nullptr,
-                          nullptr, nullptr, ws[k]);
+  // sort control blocks: zero, key minimum at its largest value (the inverse
+  // x passes fold each item's key range in)
+  if (e == cudaSuccess) e = cudaMemsetAsync(W + offCtrl, 0, (size_t)nitems * sizeof(SortCtrl), origin);
+  if (e == cudaSuccess)
+    e = cudaMemset2DAsync(W + offCtrl, sizeof(SortCtrl), 0xff, sizeof(unsigned long long), nitems, origin);
+  for (const FftGroup& f : fg) {
+    if (e != cudaSuccess) break;
+    const int l = ilog2i(f.n);
+    e = radiation_field_multi_f32(f.n, c0->tune[l].fft_variant, reinterpret_cast<const float* const*>(G + f.srcs), f.M,
+                                  reinterpret_cast<float*>(W + iw[f.first].J), W + iw[f.first].spec,
+                                  c0->ws + c0->plan.off_tw32 + c0->plan.tw32_off[l],
+                                  reinterpret_cast<const float*>(G + f.kp), c0->status, origin, sw[f.first].ctrl);
   }
-  for (int k = 0; k < nctx && e == cudaSuccess; ++k) {
-    e = cudaEventRecord(ev[k], ws[k]);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(origin, ev[k], 0);
-  }
+  for (const SortGroup& q : sg)
+    if (e == cudaSuccess) e = rank_multi(q.r, q.rb, q.match == 1, origin);
+  if (e == cudaSuccess) e = cudaMemsetAsync(W + offACtrl, 0, (size_t)nitems * kAssignCtrlBytes, origin);
+  if (e == cudaSuccess) e = cudaMemsetAsync(W + offState, 0, state_total, origin);
+  if (e == cudaSuccess) e = assign_multi(am, origin);
   if (capturing) {
     const cudaError_t e2 = cudaStreamEndCapture(origin, &b->graph);
     if (e == cudaSuccess) e = e2;
   }
   if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
-  for (int k = 0; k < nctx; ++k) ctxs[k]->prof.on = prof_on[k];
-  for (auto x : ev) if (x) cudaEventDestroy(x);
-  for (auto x : ws) if (x) cudaStreamDestroy(x);
+  if (e == cudaSuccess) {
+    size_t nn = 0;
+    cudaGraphGetNodes(b->graph, nullptr, &nn);
+    std::vector<cudaGraphNode_t> nodes(nn);
+    cudaGraphGetNodes(b->graph, nodes.data(), &nn);
+    for (auto nd : nodes) {
+      cudaGraphNodeType t;
+      if (cudaGraphNodeGetType(nd, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++b->kernel_nodes;
+    }
+  }
+  c0->prof.on = prof_on;
   if (origin) cudaStreamDestroy(origin);
   if (e != cudaSuccess) {
     cudaGetLastError();
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
+    cudaFree(b->ws);
+    if (b->args) cudaFree(b->args);
     delete b;
     return AMBER_ERR_CUDA;
   }
@@ -996,12 +1282,21 @@ int amber_batch_launch(amber_batch* b, void* stream) {
   return cuda_status(cudaGraphLaunch(b->exec, (cudaStream_t)stream));
 }
 
+int amber_batch_kernel_nodes(amber_batch* b, int* out_nodes) {
+  if (!b || !out_nodes) return AMBER_ERR_INVALID_ARG;
+  *out_nodes = b->kernel_nodes;
+  return AMBER_OK;
+}
+
 int amber_batch_destroy(amber_batch* b) {
   if (!b) return AMBER_ERR_INVALID_ARG;
   {
     DeviceGuard g(b->device);
+    cudaDeviceSynchronize();
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
+    if (b->ws) cudaFree(b->ws);
+    if (b->args) cudaFree(b->args);
   }
   delete b;
   return AMBER_OK;

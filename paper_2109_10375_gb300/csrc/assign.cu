@@ -115,14 +115,20 @@ __device__ double growth_D(double a, double om) {
 // the kernel picks the scan's fixed-point shift s (total below 2^62), and
 // tabulates X_j = floor(x_j T 2^(s-64)) so "x_j >= F_n" is the integer test
 // "X_j >= M_n", plus 1/(X_j - X_j+1) for the interpolation weight.
-__global__ void __launch_bounds__(1024) k_thresholds(unsigned long long* __restrict__ total,
-                                                     const unsigned long long* __restrict__ tile_mass,
-                                                     int64_t ntiles, int M, double a_w, double b_w, double c_w,
-                                                     double z_lo, double z_hi, unsigned long long* __restrict__ Xq,
-                                                     float* __restrict__ inv_dx, int* __restrict__ qshift,
-                                                     unsigned long long* __restrict__ qtotal, int weighting,
-                                                     double omega_m, double z_mid, int64_t ncells,
-                                                     float* __restrict__ lin) {
+__device__ __forceinline__ void thresholds_body(const ThreshArgs& A) {
+  unsigned long long* __restrict__ total = A.total;
+  const unsigned long long* __restrict__ tile_mass = A.tile_mass;
+  const int64_t ntiles = A.ntiles;
+  const int M = A.M;
+  const double a_w = A.a_w, b_w = A.b_w, c_w = A.c_w, z_lo = A.z_lo, z_hi = A.z_hi;
+  unsigned long long* __restrict__ Xq = A.Xq;
+  float* __restrict__ inv_dx = A.inv_dx;
+  int* __restrict__ qshift = A.qshift;
+  unsigned long long* __restrict__ qtotal = A.qtotal;
+  const int weighting = A.weighting;
+  const double omega_m = A.omega_m, z_mid = A.z_mid;
+  const int64_t ncells = A.ncells;
+  float* __restrict__ lin = A.lin;
   __shared__ u128 ws[32];
   __shared__ u128 sT;
   __shared__ int s_shift;
@@ -195,6 +201,13 @@ __global__ void __launch_bounds__(1024) k_thresholds(unsigned long long* __restr
   }
 }
 
+__global__ void __launch_bounds__(1024) k_thresholds(const ThreshArgs A) { thresholds_body(A); }
+
+// One CTA per item.
+__global__ void __launch_bounds__(1024) k_thresholds_multi(const ThreshArgs* __restrict__ args) {
+  thresholds_body(args[blockIdx.x]);
+}
+
 // ---------------------------------------------------------------------------
 // Cell mass in the scan's 64-bit fixed point: floor(m 2^s), s chosen per call
 // by k_thresholds so the total stays below 2^62.  Each cell loses less than
@@ -255,7 +268,7 @@ constexpr int kLinCand = 256;  // table points a tile's cells may straddle (line
 // and each cell takes the largest point that ionizes it among
 // max{j : all ionized} and the straddling points above it.
 template <bool GATHER, bool WANT_F, bool LIN>
-__global__ void __launch_bounds__(kScanThreads, 2) k_scan_assign(const ScanArgs a) {
+__device__ __forceinline__ void scan_assign_body(const ScanArgs& a) {
   constexpr int NT = kScanThreads, IT = kScanItems, TILE = kScanTile;
   __shared__ int s_jall, s_ncand;
   __shared__ int s_cand[LIN ? kLinCand : 1];
@@ -618,6 +631,22 @@ __global__ void __launch_bounds__(kScanThreads, 2) k_scan_assign(const ScanArgs 
   }
 }
 
+template <bool GATHER, bool WANT_F, bool LIN>
+__global__ void __launch_bounds__(kScanThreads, 2) k_scan_assign(const ScanArgs a) {
+  scan_assign_body<GATHER, WANT_F, LIN>(a);
+}
+
+// Several matchings at once: CTA b works on item find_item(prefix, M, b) (the
+// prefix counts scan tiles), taking its tile from that item's own ticket.
+template <bool LIN>
+__global__ void __launch_bounds__(kScanThreads, 2)
+    k_scan_assign_multi(const ScanArgs* __restrict__ args, const uint32_t* __restrict__ prefix, int M) {
+  __shared__ ScanArgs sa;
+  if (threadIdx.x == 0) sa = args[find_item(prefix, M, blockIdx.x)];
+  __syncthreads();
+  scan_assign_body<false, false, LIN>(sa);
+}
+
 // z_re[cell] = z, bucket after bucket: CTA (bucket b, tile group g) copies
 // bucket b's run of every tile in its group (one tile per warp at the
 // default group size).  A warp takes its runs in rounds of four 32-pair
@@ -625,13 +654,12 @@ __global__ void __launch_bounds__(kScanThreads, 2) k_scan_assign(const ScanArgs 
 // stores, so the dependent load -> store chains overlap.  A
 // bucket's cells span a bounded region of z_re, so the permuted writes of
 // the CTAs working on it stay close together.
-__global__ void __launch_bounds__(256) k_scatter_back(const uint32_t* __restrict__ bcell,
-                                                      const float* __restrict__ bz,
-                                                      const uint16_t* __restrict__ btab, int nbuckets,
-                                                      int64_t tiles, int groups, float* __restrict__ zre) {
+__device__ __forceinline__ void scatter_back_body(const uint32_t* __restrict__ bcell, const float* __restrict__ bz,
+                                                  const uint16_t* __restrict__ btab, int nbuckets, int64_t tiles,
+                                                  int groups, float* __restrict__ zre, uint32_t blk) {
   constexpr int TPW = kBackTilesPerCta / 8;  // tiles per warp
-  const int b = blockIdx.x / groups;
-  const int64_t g = blockIdx.x - (int64_t)b * groups;
+  const int b = blk / groups;
+  const int64_t g = blk - (int64_t)b * groups;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const unsigned long long stream_pol = l2_evict_first(), keep_pol = l2_evict_last();
   const int64_t t0 = g * kBackTilesPerCta + warp * TPW;
@@ -674,6 +702,21 @@ __global__ void __launch_bounds__(256) k_scatter_back(const uint32_t* __restrict
     for (int q = 0; q < TPW * G; ++q)
       if (c[q] != 0xffffffffu) st_hint(zre + c[q], zz[q], keep_pol);
   }
+}
+
+__global__ void __launch_bounds__(256) k_scatter_back(const uint32_t* __restrict__ bcell,
+                                                      const float* __restrict__ bz,
+                                                      const uint16_t* __restrict__ btab, int nbuckets,
+                                                      int64_t tiles, int groups, float* __restrict__ zre) {
+  scatter_back_body(bcell, bz, btab, nbuckets, tiles, groups, zre, blockIdx.x);
+}
+
+// Several scatters at once: CTA b works on item find_item(prefix, M, b).
+__global__ void __launch_bounds__(256) k_scatter_back_multi(const ScatterArgs* __restrict__ args,
+                                                            const uint32_t* __restrict__ prefix, int M) {
+  const int it = find_item(prefix, M, blockIdx.x);
+  const ScatterArgs& a = args[it];
+  scatter_back_body(a.bcell, a.bz, a.btab, a.nbuckets, a.tiles, a.groups, a.zre, blockIdx.x - prefix[it]);
 }
 
 // ---------------------------------------------------------------------------
@@ -736,36 +779,36 @@ void bucket_plan(int64_t n, int* nbuckets, int* shift) {
   *nbuckets = (int)((n + ((int64_t)1 << kBucketShift) - 1) >> kBucketShift);
 }
 
-cudaError_t assign_impl(const AssignWork& w, const uint32_t* order, const float* mass, bool mass_in_rank_order,
-                        const unsigned long long* tile_mass, int64_t n, const HistoryCoeffs& hc, float* zre, double* F,
-                        unsigned int* status, cudaStream_t s, FftProfile* prof, unsigned int spin_limit,
-                        const uint32_t* order_b, const float* mass_b, const int* pick) {
+void assign_args(const AssignWork& w, const uint32_t* order, const float* mass, const unsigned long long* tile_mass,
+                 int64_t n, const HistoryCoeffs& hc, float* zre, double* F, unsigned int* status,
+                 unsigned int spin_limit, const uint32_t* order_b, const float* mass_b, const int* pick,
+                 ThreshArgs* ta, ScanArgs* sa, ScatterArgs* xa) {
   const int64_t tiles = (n + kScanTile - 1) / kScanTile;
-  cudaError_t e;
   unsigned long long* total = reinterpret_cast<unsigned long long*>(w.ctrl);
   uint32_t* ticket = reinterpret_cast<uint32_t*>(w.ctrl + 16);
-  e = cudaMemsetAsync(w.ctrl, 0, kAssignCtrlBytes, s);
-  if (e != cudaSuccess) return e;
-  e = cudaMemsetAsync(w.state, 0, (size_t)tiles * sizeof(unsigned long long), s);
-  if (e != cudaSuccess) return e;
-
-  if (!tile_mass) {  // masses in cell order: one exact reduction pass
-    prof_begin(prof, PK_MASS_REDUCE, s);
-    int grid = (int)std::min<int64_t>((n / 4 + 255) / 256, (int64_t)w.num_sms * 8);
-    if (grid < 1) grid = 1;
-    k_mass_reduce<<<grid, 256, 0, s>>>(mass, n, total, status);
-    prof_end(prof, PK_MASS_REDUCE, s);
-  }
-
-  prof_begin(prof, PK_THRESHOLDS, s);
   int* qshift = reinterpret_cast<int*>(w.ctrl + 32);
   unsigned long long* qtotal = reinterpret_cast<unsigned long long*>(w.ctrl + 40);
-  k_thresholds<<<1, 1024, 0, s>>>(total, tile_mass, tile_mass ? sort_tiles(n) : 0, hc.n_table, hc.a, hc.b, hc.c,
-                                   hc.z_lo, hc.z_hi, w.Xq, w.inv_dx, qshift, qtotal, hc.weighting, hc.omega_m,
-                                   hc.z_mid, n, w.lin);
-  prof_end(prof, PK_THRESHOLDS, s);
+  ThreshArgs& t = *ta;
+  t.total = total;
+  t.tile_mass = tile_mass;
+  t.ntiles = tile_mass ? sort_tiles(n) : 0;
+  t.M = hc.n_table;
+  t.a_w = hc.a;
+  t.b_w = hc.b;
+  t.c_w = hc.c;
+  t.z_lo = hc.z_lo;
+  t.z_hi = hc.z_hi;
+  t.Xq = w.Xq;
+  t.inv_dx = w.inv_dx;
+  t.qshift = qshift;
+  t.qtotal = qtotal;
+  t.weighting = hc.weighting;
+  t.omega_m = hc.omega_m;
+  t.z_mid = hc.z_mid;
+  t.ncells = n;
+  t.lin = w.lin;
 
-  ScanArgs a;
+  ScanArgs& a = *sa;
   a.order = order;
   a.mass = mass;
   a.order_b = order_b;
@@ -794,6 +837,43 @@ cudaError_t assign_impl(const AssignWork& w, const uint32_t* order, const float*
   a.linQ = w.lin + kMaxTable;
   a.lina = w.lin + 2 * kMaxTable;
   a.linb = w.lin + 3 * kMaxTable;
+
+  ScatterArgs& x = *xa;
+  x.bcell = w.bcell;
+  x.bz = w.bz;
+  x.btab = w.btab;
+  x.nbuckets = a.nbuckets;
+  x.tiles = tiles;
+  x.groups = (int)((tiles + kBackTilesPerCta - 1) / kBackTilesPerCta);
+  x.zre = zre;
+}
+
+cudaError_t assign_impl(const AssignWork& w, const uint32_t* order, const float* mass, bool mass_in_rank_order,
+                        const unsigned long long* tile_mass, int64_t n, const HistoryCoeffs& hc, float* zre, double* F,
+                        unsigned int* status, cudaStream_t s, FftProfile* prof, unsigned int spin_limit,
+                        const uint32_t* order_b, const float* mass_b, const int* pick) {
+  const int64_t tiles = (n + kScanTile - 1) / kScanTile;
+  ThreshArgs ta;
+  ScanArgs a;
+  ScatterArgs xa;
+  assign_args(w, order, mass, tile_mass, n, hc, zre, F, status, spin_limit, order_b, mass_b, pick, &ta, &a, &xa);
+  cudaError_t e = cudaMemsetAsync(w.ctrl, 0, kAssignCtrlBytes, s);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(w.state, 0, (size_t)tiles * sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return e;
+
+  if (!tile_mass) {  // masses in cell order: one exact reduction pass
+    prof_begin(prof, PK_MASS_REDUCE, s);
+    int grid = (int)std::min<int64_t>((n / 4 + 255) / 256, (int64_t)w.num_sms * 8);
+    if (grid < 1) grid = 1;
+    k_mass_reduce<<<grid, 256, 0, s>>>(mass, n, ta.total, status);
+    prof_end(prof, PK_MASS_REDUCE, s);
+  }
+
+  prof_begin(prof, PK_THRESHOLDS, s);
+  k_thresholds<<<1, 1024, 0, s>>>(ta);
+  prof_end(prof, PK_THRESHOLDS, s);
+
   prof_begin(prof, PK_SCAN_ASSIGN, s);
   const unsigned g = (unsigned)tiles;
   const bool gather = !mass_in_rank_order, lin = hc.weighting != AMBER_WEIGHT_MASS;
@@ -810,12 +890,17 @@ cudaError_t assign_impl(const AssignWork& w, const uint32_t* order, const float*
   }
   prof_end(prof, PK_SCAN_ASSIGN, s);
   prof_begin(prof, PK_SCATTER_BACK, s);
-  {
-    const int groups = (int)((tiles + kBackTilesPerCta - 1) / kBackTilesPerCta);
-    k_scatter_back<<<(unsigned)(groups * a.nbuckets), 256, 0, s>>>(w.bcell, w.bz, w.btab, a.nbuckets, tiles, groups,
-                                                                   zre);
-  }
+  k_scatter_back<<<(unsigned)(xa.groups * xa.nbuckets), 256, 0, s>>>(xa.bcell, xa.bz, xa.btab, xa.nbuckets, xa.tiles,
+                                                                     xa.groups, xa.zre);
   prof_end(prof, PK_SCATTER_BACK, s);
+  return cudaGetLastError();
+}
+
+cudaError_t assign_multi(const AssignMulti& m, cudaStream_t s) {
+  k_thresholds_multi<<<m.M, 1024, 0, s>>>(m.thresh);
+  if (m.scan_tiles[0]) k_scan_assign_multi<false><<<m.scan_tiles[0], kScanThreads, 0, s>>>(m.scan[0], m.scan_prefix[0], m.Mg[0]);
+  if (m.scan_tiles[1]) k_scan_assign_multi<true><<<m.scan_tiles[1], kScanThreads, 0, s>>>(m.scan[1], m.scan_prefix[1], m.Mg[1]);
+  k_scatter_back_multi<<<m.scatter_blocks, 256, 0, s>>>(m.scatter, m.scatter_prefix, m.M);
   return cudaGetLastError();
 }
 

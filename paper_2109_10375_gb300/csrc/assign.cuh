@@ -76,6 +76,59 @@ struct ScanArgs {
   const float* linb;
 };
 
+// Arguments of the thresholds kernel (one CTA per matching).
+struct ThreshArgs {
+  unsigned long long* total;             // exact mass total (2 x u64), formed here from tile_mass if given
+  const unsigned long long* tile_mass;   // per-sort-tile partial sums or null
+  int64_t ntiles;
+  int M;                                 // table points
+  double a_w, b_w, c_w, z_lo, z_hi;
+  unsigned long long* Xq;
+  float* inv_dx;
+  int* qshift;
+  unsigned long long* qtotal;
+  int weighting;
+  double omega_m, z_mid;
+  int64_t ncells;
+  float* lin;
+};
+
+// Arguments of the scatter back to cell order.
+struct ScatterArgs {
+  const uint32_t* bcell;
+  const float* bz;
+  const uint16_t* btab;
+  int nbuckets;
+  int64_t tiles;   // scan tiles
+  int groups;      // scatter CTAs per bucket
+  float* zre;
+};
+
+// Several matchings run together: one thresholds launch (a CTA per item),
+// one scan launch per weighting form (0: mass, 1: linear; items of each form
+// contiguous, scan[f] and scan_prefix[f] with Mg[f] entries), one scatter
+// launch.  All pointers are device arrays; the matchings' control words and
+// scan look-back states must be zeroed beforehand.
+struct AssignMulti {
+  int M;
+  const ThreshArgs* thresh;
+  const ScanArgs* scan[2];
+  const uint32_t* scan_prefix[2];
+  int Mg[2];
+  uint32_t scan_tiles[2];
+  const ScatterArgs* scatter;
+  const uint32_t* scatter_prefix;
+  uint32_t scatter_blocks;
+};
+
+// Host: the arguments of one matching as assign_impl runs it (the masses in
+// rank order and the total from tile_mass, no F).
+void assign_args(const AssignWork& w, const uint32_t* order, const float* mass, const unsigned long long* tile_mass,
+                 int64_t n, const HistoryCoeffs& hc, float* zre, double* F, unsigned int* status,
+                 unsigned int spin_limit, const uint32_t* order_b, const float* mass_b, const int* pick,
+                 ThreshArgs* ta, ScanArgs* sa, ScatterArgs* xa);
+cudaError_t assign_multi(const AssignMulti& m, cudaStream_t s);
+
 void bucket_plan(int64_t n, int* nbuckets, int* shift);
 
 // Tomographic matching: fill z with NaN (neutral); give cells with a redshift

@@ -161,6 +161,19 @@ __device__ __forceinline__ float ld_hint(const float* a, unsigned long long pol)
   return v;
 }
 
+// Launches that work on several items at once: item i owns blocks
+// [prefix[i], prefix[i+1]) of the grid.  The item of block b is the largest i
+// with prefix[i] <= b (an item with no blocks is skipped).
+__device__ __forceinline__ int find_item(const uint32_t* __restrict__ prefix, int M, uint32_t b) {
+  int lo = 0, hi = M - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (prefix[mid] <= b) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
 // ---------------------------------------------------------------------------
 // Status word (device-side errors latch here; no trap, no assert).
 // ---------------------------------------------------------------------------

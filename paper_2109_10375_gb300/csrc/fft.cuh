@@ -97,11 +97,15 @@ enum { PASS_FWD = 0, PASS_INV = 1, PASS_CONV = 2 };
 
 // OOP (z-pass only): the tile is read from Hin, a spectrum kept by the
 // caller, and the result written to H; otherwise H is read and written in place.
-template <typename T, int N, int MODE, int V = 0, bool OOP = false>
+// MULTI (z-pass only): several transforms of size N back to back, item_stride
+// elements apart; line family `outer` of the launch is line y = outer % N of
+// item outer / N, whose box and l_mfp give kp[2 item] = kf, kp[2 item + 1] = l.
+template <typename T, int N, int MODE, int V = 0, bool OOP = false, bool MULTI = false>
 __global__ void __launch_bounds__(strided_threads<N, V>(), 2)
 k_fft_strided(cpx<T>* __restrict__ H, int64_t elem_stride, int64_t outer_stride, int ncol,
               int ntx, const cpx<T>* __restrict__ tw, T kf, T l_mfp, T norm,
-              const cpx<T>* __restrict__ Hin = nullptr) {
+              const cpx<T>* __restrict__ Hin = nullptr, int64_t item_stride = 0,
+              const T* __restrict__ kp = nullptr) {
   using C = FftCfg<N, V>;
   using L = StridedSmem<T, N, V>;
   constexpr int R0 = C::R0, R1 = C::R1, E = C::E, SB = C::SB, NT = strided_threads<N, V>();
@@ -110,9 +114,17 @@ k_fft_strided(cpx<T>* __restrict__ H, int64_t elem_stride, int64_t outer_stride,
   cpx<T>* sm = reinterpret_cast<cpx<T>*>(smem_raw);
 
   const int tid = threadIdx.x;
-  const int outer = blockIdx.x / ntx;
+  int outer = blockIdx.x / ntx;
   const int kx0 = (blockIdx.x - outer * ntx) * SB;
-  cpx<T>* base = H + (int64_t)outer * outer_stride + kx0;
+  int64_t item_off = 0;
+  if constexpr (MULTI) {
+    const int item = outer / N;
+    outer -= item * N;
+    item_off = (int64_t)item * item_stride;
+    kf = kp[2 * item];
+    l_mfp = kp[2 * item + 1];
+  }
+  cpx<T>* base = H + item_off + (int64_t)outer * outer_stride + kx0;
   const cpx<T>* ibase = OOP ? Hin + (int64_t)outer * outer_stride + kx0 : base;
 
   cpx<T> v[E];
@@ -257,11 +269,14 @@ k_fft_strided(cpx<T>* __restrict__ H, int64_t elem_stride, int64_t outer_stride,
 // x-pass R2C: rows 2p and 2p+1 form z = a + i b; after the complex FFT
 // A_k = (Z_k + conj Z_{N-k})/2 and B_k = (Z_k - conj Z_{N-k})/(2i), k <= N/2.
 // ---------------------------------------------------------------------------
-template <typename T, int N, int V = 0>
+// MULTI: several transforms of size N back to back in H; the rows of item i
+// (rows [i rpi, (i+1) rpi), rpi = N^2) come from srcs[i].  A CTA's rows never
+// straddle two items (rpi is a multiple of 2 XP).
+template <typename T, int N, int V = 0, bool MULTI = false>
 // FP32: three CTAs per SM (measured faster for the forward x pass only)
 __global__ void __launch_bounds__(xpass_threads<N, V>(), sizeof(T) == 4 ? 3 : 1)
 k_fft_r2c_x(const T* __restrict__ src, cpx<T>* __restrict__ H, int64_t nrows, int RS,
-            const cpx<T>* __restrict__ tw) {
+            const cpx<T>* __restrict__ tw, const T* const* __restrict__ srcs = nullptr, int64_t rpi = 0) {
   using C = FftCfg<N, V>;
   using L = XSmem<T, N, V>;
   constexpr int R0 = C::R0, R1 = C::R1, E = C::E, XP = C::XP, NT = xpass_threads<N, V>();
@@ -270,12 +285,22 @@ k_fft_r2c_x(const T* __restrict__ src, cpx<T>* __restrict__ H, int64_t nrows, in
   cpx<T>* sm = reinterpret_cast<cpx<T>*>(smem_raw);
   const int tid = threadIdx.x;
   const int64_t row0 = (int64_t)blockIdx.x * 2 * XP;
+  // first element of row ra of the launch
+  auto row_ptr = [&](int64_t ra) -> const T* {
+    if constexpr (MULTI) {
+      const int64_t it = ra / rpi;
+      return srcs[it] + (ra - it * rpi) * N;
+    } else {
+      return src + ra * N;
+    }
+  };
   if (tid == 0) {
     // the rows of the CTA one SM count ahead into L2 (a third of the resident
     // wave: measured faster than a whole wave ahead, 1.63 vs 1.95 ms at 1024^3)
     const int64_t r2 = ((int64_t)blockIdx.x + sm_count()) * 2 * XP;
-    if (r2 < nrows) prefetch_l2_bulk(src + r2 * N, (uint32_t)(min((int64_t)2 * XP, nrows - r2) * N * sizeof(T)));
+    if (r2 < nrows) prefetch_l2_bulk(row_ptr(r2), (uint32_t)(min((int64_t)2 * XP, nrows - r2) * N * sizeof(T)));
   }
+  const T* rbase = row_ptr(row0);  // this CTA's rows, all of one item
 
   cpx<T> v[E];
 #pragma unroll
@@ -284,7 +309,7 @@ k_fft_r2c_x(const T* __restrict__ src, cpx<T>* __restrict__ H, int64_t nrows, in
     const int j = id % (N / R0), p = id / (N / R0);
     const int64_t ra = row0 + 2 * p;
     const bool ok = ra + 1 < nrows;
-    const T* a = src + ra * N;
+    const T* a = rbase + (int64_t)(2 * p) * N;
 #pragma unroll
     for (int r = 0; r < R0; ++r) {
       const int n = j + r * (N / R0);
@@ -344,10 +369,13 @@ k_fft_r2c_x(const T* __restrict__ src, cpx<T>* __restrict__ H, int64_t nrows, in
 // DC and Nyquist use the real parts only.  Re z -> row 2p, Im z -> row 2p+1.
 // The 1/n^3 normalisation was applied with the kernel in the z-pass.
 // ---------------------------------------------------------------------------
-template <typename T, int N, int V = 0>
+// MULTI: several transforms of size N back to back; the key range of item
+// row0 / rpi folds into krange[item] (one control block per item).
+template <typename T, int N, int V = 0, bool MULTI = false>
 __global__ void __launch_bounds__(xpass_threads<N, V>())
 k_fft_c2r_x(const cpx<T>* __restrict__ H, T* __restrict__ J, int64_t nrows, int RS,
-            const cpx<T>* __restrict__ tw, unsigned int* __restrict__ status, SortCtrl* __restrict__ krange) {
+            const cpx<T>* __restrict__ tw, unsigned int* __restrict__ status, SortCtrl* __restrict__ krange,
+            int64_t rpi = 0) {
   using C = FftCfg<N, V>;
   using L = XSmem<T, N, V>;
   using K = typename KeyOf<T>::K;
@@ -465,7 +493,8 @@ k_fft_c2r_x(const cpx<T>* __restrict__ H, T* __restrict__ J, int64_t nrows, int 
   }
   if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) raise_status(status, AMBER_ERR_NONFINITE);
   // fold the intensities' key range into the sort's control block
-  if (krange) key_range_commit(klo, khi, krange);
+  if constexpr (MULTI) key_range_commit(klo, khi, krange + row0 / rpi);
+  else if (krange) key_range_commit(klo, khi, krange);
 }
 
 // ---------------------------------------------------------------------------
@@ -537,6 +566,51 @@ cudaError_t radiation_field_n(const T* src, T* J, cpx<T>* H, const cpx<T>* tw, d
   prof_begin(prof, PK_C2R_X, s);
   k_fft_c2r_x<T, N, V><<<xgrid, xpass_threads<N, V>(), xs, s>>>(H, J, nrows, RS, tw, status, krange);
   prof_end(prof, PK_C2R_X, s);
+  return cudaGetLastError();
+}
+
+// Radiation fields of M same-size items in one launch per pass.  The items'
+// half spectra lie back to back in H (M n^2 (n/2 + 2) elements) and their
+// intensities back to back in J (M n^3); srcs (device array of M pointers)
+// holds the sources, kp (device, 2 M values) each item's kf = 2 pi / box and
+// l_mfp, kranges (device, M control blocks) the blocks the items' key ranges
+// fold into.  Requires n^2 to be a multiple of the x-pass tile (n >= 8).
+template <typename T, int N, int V = 0>
+cudaError_t radiation_field_multi_n(const T* const* srcs, int M, T* J, cpx<T>* H, const cpx<T>* tw, const T* kp,
+                                    unsigned int* status, cudaStream_t s, SortCtrl* kranges) {
+  using C = FftCfg<N, V>;
+  static_assert((N * N) % (2 * C::XP) == 0, "an x-pass tile must not straddle two items");
+  const int RS = N / 2 + 2;
+  const int ncol = N / 2 + 1;
+  const int64_t rpi = (int64_t)N * N;
+  const int64_t nrows = rpi * M;
+  const int64_t item_stride = rpi * RS;
+  const T norm = (T)(1.0 / ((double)N * N * N));
+  const size_t xs = XSmem<T, N, V>::elems * sizeof(cpx<T>);
+  const size_t ss = StridedSmem<T, N, V>::elems * sizeof(cpx<T>);
+  const size_t sc = ss + (size_t)(N / 2 + 1) * C::SB * sizeof(T);
+  static std::atomic<unsigned long long> attr_done{0};  // per instantiation and device
+  if (first_use_on_device(attr_done)) {
+    cudaFuncSetAttribute(k_fft_r2c_x<T, N, V, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xs);
+    cudaFuncSetAttribute(k_fft_c2r_x<T, N, V, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xs);
+    cudaFuncSetAttribute(k_fft_strided<T, N, PASS_FWD, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss);
+    cudaFuncSetAttribute(k_fft_strided<T, N, PASS_INV, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss);
+    cudaFuncSetAttribute(k_fft_strided<T, N, PASS_CONV, V, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sc);
+  }
+  const int xgrid = (int)((nrows / 2 + C::XP - 1) / C::XP);
+  const int ntx = (ncol + C::SB - 1) / C::SB;
+  const int sgrid = M * N * ntx;
+  const T zero = (T)0;
+  k_fft_r2c_x<T, N, V, true><<<xgrid, xpass_threads<N, V>(), xs, s>>>(nullptr, H, nrows, RS, tw, srcs, rpi);
+  // y passes: the z planes of all items are one run of M N planes
+  k_fft_strided<T, N, PASS_FWD, V><<<sgrid, strided_threads<N, V>(), ss, s>>>(H, RS, (int64_t)N * RS, ncol, ntx, tw,
+                                                                           zero, zero, zero);
+  k_fft_strided<T, N, PASS_CONV, V, false, true><<<sgrid, strided_threads<N, V>(), sc, s>>>(
+      H, (int64_t)N * RS, RS, ncol, ntx, tw, zero, zero, norm, nullptr, item_stride, kp);
+  k_fft_strided<T, N, PASS_INV, V><<<sgrid, strided_threads<N, V>(), ss, s>>>(H, RS, (int64_t)N * RS, ncol, ntx, tw,
+                                                                           zero, zero, zero);
+  k_fft_c2r_x<T, N, V, true><<<xgrid, xpass_threads<N, V>(), xs, s>>>(H, J, nrows, RS, tw, status, kranges, rpi);
   return cudaGetLastError();
 }
 

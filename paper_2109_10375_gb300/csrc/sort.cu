@@ -79,10 +79,11 @@ __global__ void __launch_bounds__(256) k_key_range(const SRC* __restrict__ J, in
   if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) raise_status(status, AMBER_ERR_NONFINITE);
 }
 
+// The histogram of one sort, run by CTA blk of nblk.
 template <typename SRC, int RB>
-__global__ void __launch_bounds__(256) k_sort_histogram(const SRC* __restrict__ J, int64_t n,
-                                                        SortCtrl* __restrict__ ctrl,
-                                                        uint32_t* __restrict__ lb0, int64_t lb0_words) {
+__device__ __forceinline__ void sort_histogram_body(const SRC* __restrict__ J, int64_t n, SortCtrl* __restrict__ ctrl,
+                                                    uint32_t* __restrict__ lb0, int64_t lb0_words, int64_t blk,
+                                                    int64_t nblk) {
   using K = typename KeyOf<SRC>::K;
   constexpr int R = 1 << RB, P = max_passes<SRC, RB>();
   constexpr int V = 16 / sizeof(SRC);  // elements per 16-byte load
@@ -98,8 +99,8 @@ __global__ void __launch_bounds__(256) k_sort_histogram(const SRC* __restrict__ 
     if (np < 1) np = 1;
   }
   bool bad = false;
-  const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
-  const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t nthreads = nblk * blockDim.x;
+  const int64_t gtid = blk * blockDim.x + threadIdx.x;
   // 16-byte loads only from a 16-byte aligned array (a caller's view may start
   // anywhere on its element size); otherwise every element takes the tail loop
   const bool vec = (reinterpret_cast<uintptr_t>(J) & 15) == 0;
@@ -141,9 +142,26 @@ __global__ void __launch_bounds__(256) k_sort_histogram(const SRC* __restrict__ 
   for (int64_t w = gtid; w < lb0_words; w += nthreads) lb0[w] = 0;  // look-back of the first pass
 }
 
+template <typename SRC, int RB>
+__global__ void __launch_bounds__(256) k_sort_histogram(const SRC* __restrict__ J, int64_t n,
+                                                        SortCtrl* __restrict__ ctrl,
+                                                        uint32_t* __restrict__ lb0, int64_t lb0_words) {
+  sort_histogram_body<SRC, RB>(J, n, ctrl, lb0, lb0_words, blockIdx.x, gridDim.x);
+}
+
+// Several sorts at once: CTA b works on item find_item(prefix, M, b).
+template <typename SRC, int RB>
+__global__ void __launch_bounds__(256) k_sort_histogram_multi(const HistArgs* __restrict__ args,
+                                                              const uint32_t* __restrict__ prefix, int M) {
+  const int it = find_item(prefix, M, blockIdx.x);
+  const HistArgs& a = args[it];
+  sort_histogram_body<SRC, RB>(reinterpret_cast<const SRC*>(a.J), a.n, a.ctrl, a.lb0, a.lb0_words,
+                               blockIdx.x - prefix[it], prefix[it + 1] - prefix[it]);
+}
+
 // One CTA: exclusive scan of each digit histogram, and the pass count.
 template <typename SRC, int RB>
-__global__ void __launch_bounds__(256) k_sort_offsets(SortCtrl* __restrict__ ctrl) {
+__device__ __forceinline__ void sort_offsets_body(SortCtrl* __restrict__ ctrl) {
   using K = typename KeyOf<SRC>::K;
   constexpr int R = 1 << RB, P = max_passes<SRC, RB>();
   __shared__ uint32_t wsum[8];
@@ -184,6 +202,17 @@ __global__ void __launch_bounds__(256) k_sort_offsets(SortCtrl* __restrict__ ctr
   }
 }
 
+template <typename SRC, int RB>
+__global__ void __launch_bounds__(256) k_sort_offsets(SortCtrl* __restrict__ ctrl) {
+  sort_offsets_body<SRC, RB>(ctrl);
+}
+
+// One CTA per item.
+template <typename SRC, int RB>
+__global__ void __launch_bounds__(256) k_sort_offsets_multi(const HistArgs* __restrict__ args) {
+  sort_offsets_body<SRC, RB>(args[blockIdx.x].ctrl);
+}
+
 // ---------------------------------------------------------------------------
 // One digit pass.  FIRST: keys come from the intensities (encoded, minus the
 // minimum key), payload = cell index, and (MASS) masses are read in cell
@@ -191,7 +220,7 @@ __global__ void __launch_bounds__(256) k_sort_offsets(SortCtrl* __restrict__ ctr
 // only the payloads (to the final arrays).
 // ---------------------------------------------------------------------------
 template <typename SRC, int RB, bool FIRST, bool MASS, bool MATCH>
-__global__ void __launch_bounds__(kSortThreads, AMBER_SORT_MINB) k_sort_pass(const PassArgs a) {
+__device__ __forceinline__ void sort_pass_body(const PassArgs& a) {
   using K = typename KeyOf<SRC>::K;
   constexpr int R = 1 << RB, DPT = R / kSortThreads;  // digits per thread
   static_assert(DPT >= 1 && R <= kMaxRadix, "digit width");
@@ -442,6 +471,22 @@ __global__ void __launch_bounds__(kSortThreads, AMBER_SORT_MINB) k_sort_pass(con
     raise_status(a.status, (FIRST && MASS) ? (AMBER_ERR_NONFINITE | AMBER_ERR_INVALID_MASS) : AMBER_ERR_NONFINITE);
 }
 
+template <typename SRC, int RB, bool FIRST, bool MASS, bool MATCH>
+__global__ void __launch_bounds__(kSortThreads, AMBER_SORT_MINB) k_sort_pass(const PassArgs a) {
+  sort_pass_body<SRC, RB, FIRST, MASS, MATCH>(a);
+}
+
+// Several sorts at once: CTA b works on item find_item(prefix, M, b) (the
+// prefix counts tiles), taking its tile from that item's own ticket.
+template <typename SRC, int RB, bool FIRST, bool MASS, bool MATCH>
+__global__ void __launch_bounds__(kSortThreads, AMBER_SORT_MINB)
+    k_sort_pass_multi(const PassArgs* __restrict__ args, const uint32_t* __restrict__ prefix, int M) {
+  __shared__ PassArgs sa;
+  if (threadIdx.x == 0) sa = args[find_item(prefix, M, blockIdx.x)];
+  __syncthreads();
+  sort_pass_body<SRC, RB, FIRST, MASS, MATCH>(sa);
+}
+
 // ---------------------------------------------------------------------------
 // Host side.
 // ---------------------------------------------------------------------------
@@ -579,6 +624,95 @@ cudaError_t rank_impl(const SortWork& w, const SRC* J, int64_t n, uint32_t* orde
   }
   return cudaErrorInvalidValue;
 }
+
+template <typename SRC>
+int rank_args(const SortWork& w, const SRC* J, int64_t n, uint32_t* order, const float* mass_in, float* mass_out,
+              unsigned long long* tile_mass, unsigned int* status, unsigned int spin_limit, int digit_bits,
+              HistArgs* hist, uint32_t* hist_blocks, PassArgs pass[4]) {
+  using K = typename KeyOf<SRC>::K;
+  const int RB = digit_bits ? digit_bits : KeyOf<SRC>::RB;
+  const int P = (8 * (int)sizeof(K) + RB - 1) / RB;
+  const int R = 1 << RB;
+  const int64_t tiles = sort_tiles(n);
+  uint32_t* lbA = w.lookback;
+  uint32_t* lbB = w.lookback + sort_lookback_words(w.max_cells);
+  hist->J = J;
+  hist->n = n;
+  hist->ctrl = w.ctrl;
+  hist->lb0 = lbA;
+  hist->lb0_words = tiles * R;
+  int grid = (int)std::min<int64_t>((n / (16 / (int)sizeof(SRC)) + 255) / 256, (int64_t)w.num_sms * 8);
+  *hist_blocks = (uint32_t)std::max(grid, 1);
+  K* kA = reinterpret_cast<K*>(w.keysA);
+  K* kB = reinterpret_cast<K*>(w.keysB);
+  const void* kin = nullptr;
+  const uint32_t* vin = nullptr;
+  const float* mcur = mass_in;
+  for (int p = 0; p < P; ++p) {
+    PassArgs& a = pass[p];
+    a.J = J;
+    a.kin = kin;
+    a.vin = vin;
+    a.min = mcur;
+    a.kout = (p & 1) ? (void*)kB : (void*)kA;
+    a.vout = (p & 1) ? w.idxB : w.idxA;
+    a.mout = mass_in ? ((p & 1) ? w.massB : w.massA) : nullptr;
+    a.vfinal = order;
+    a.mfinal = mass_out;
+    a.n = n;
+    a.pass = p;
+    a.lb = (p & 1) ? lbB : lbA;
+    a.lb_next = (p == P - 1) ? nullptr : ((p & 1) ? lbA : lbB);
+    a.ctrl = w.ctrl;
+    a.tile_mass = tile_mass;
+    a.status = status;
+    a.spin_limit = spin_limit;
+    a.ahead = (uint32_t)w.num_sms;
+    kin = a.kout;
+    vin = a.vout;
+    mcur = a.mout;
+  }
+  return P;
+}
+
+template <int RB, bool FIRST, bool MATCH>
+static void launch_pass_multi(const RankMulti& r, int p, cudaStream_t s) {
+  const size_t smem = pass_smem<float, RB>(true);
+  static std::atomic<unsigned long long> attr{0};  // per instantiation and device
+  if (first_use_on_device(attr))
+    cudaFuncSetAttribute(k_sort_pass_multi<float, RB, FIRST, true, MATCH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+  k_sort_pass_multi<float, RB, FIRST, true, MATCH><<<r.tiles, kSortThreads, smem, s>>>(r.pass[p], r.tile_prefix, r.M);
+}
+
+template <int RB>
+static cudaError_t rank_multi_rb(const RankMulti& r, bool match, cudaStream_t s) {
+  constexpr int P = max_passes<float, RB>();
+  k_sort_histogram_multi<float, RB><<<r.hist_blocks, 256, 0, s>>>(r.hist, r.hist_prefix, r.M);
+  k_sort_offsets_multi<float, RB><<<r.M, 256, 0, s>>>(r.hist);
+  for (int p = 0; p < P; ++p) {
+    if (p == 0) {
+      if (match) launch_pass_multi<RB, true, true>(r, p, s);
+      else launch_pass_multi<RB, true, false>(r, p, s);
+    } else {
+      if (match) launch_pass_multi<RB, false, true>(r, p, s);
+      else launch_pass_multi<RB, false, false>(r, p, s);
+    }
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t rank_multi(const RankMulti& r, int digit_bits, bool match, cudaStream_t s) {
+  const int env = rank_env();
+  const bool m = env >= 0 ? env == 1 : match;
+  if (digit_bits == 8) return rank_multi_rb<8>(r, m, s);
+  if (digit_bits == 9) return rank_multi_rb<9>(r, m, s);
+  return cudaErrorInvalidValue;
+}
+
+template int rank_args<float>(const SortWork&, const float*, int64_t, uint32_t*, const float*, float*,
+                              unsigned long long*, unsigned int*, unsigned int, int, HistArgs*, uint32_t*,
+                              PassArgs[4]);
 
 template cudaError_t rank_impl<float>(const SortWork&, const float*, int64_t, uint32_t*, const float*, float*,
                                       unsigned long long*, bool, unsigned int*, cudaStream_t, FftProfile*,

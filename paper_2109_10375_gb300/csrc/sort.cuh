@@ -61,6 +61,40 @@ struct PassArgs {
   uint32_t ahead;  // tiles ahead whose inputs are prefetched into L2 (0: none)
 };
 
+// Arguments of one sort's histogram and digit-offset kernels.
+struct HistArgs {
+  const void* J;  // intensities (float or double)
+  int64_t n;
+  SortCtrl* ctrl;
+  uint32_t* lb0;       // look-back region of the first pass (cleared here)
+  int64_t lb0_words;
+};
+
+// Several sorts run together: one histogram launch, one offset launch (a
+// CTA per item) and one launch per digit pass cover every item.  hist_prefix
+// and tile_prefix (device, M + 1 entries) give each item's histogram CTAs and
+// sort tiles; hist and pass[p] (device, M entries each) the items' arguments.
+struct RankMulti {
+  int M;
+  const HistArgs* hist;
+  const uint32_t* hist_prefix;
+  uint32_t hist_blocks;
+  const PassArgs* pass[4];
+  const uint32_t* tile_prefix;
+  uint32_t tiles;
+};
+
+// Host: the arguments of one sort of J (as rank_impl with the key range
+// already folded into w.ctrl) -- its histogram CTAs and the arguments of every
+// digit pass; returns the number of passes P (pass[0..P-1] filled).
+template <typename SRC>
+int rank_args(const SortWork& w, const SRC* J, int64_t n, uint32_t* order, const float* mass_in, float* mass_out,
+              unsigned long long* tile_mass, unsigned int* status, unsigned int spin_limit, int digit_bits,
+              HistArgs* hist, uint32_t* hist_blocks, PassArgs pass[4]);
+// Enqueue the histogram, offsets and digit passes of r's sorts (FP32 keys,
+// digit_bits 8 or 9, match: digit peers by warp match).
+cudaError_t rank_multi(const RankMulti& r, int digit_bits, bool match, cudaStream_t s);
+
 int64_t sort_tiles(int64_t n);
 size_t sort_lookback_words(int64_t n);
 cudaError_t sort_ctrl_reset(SortCtrl* ctrl, cudaStream_t s);

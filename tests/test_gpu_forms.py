@@ -193,3 +193,38 @@ def test_serving_admission_waits_and_evicts_with_the_same_results(B):
     assert waits > 0 and evictions > 0, (waits, evictions)
     for a, b in zip(alone, tight):
         assert torch.equal(a.z, b.z), a.rid
+
+
+def test_batch_is_one_launch_per_stage_with_mixed_tunings_and_weightings(B, monkeypatch):
+    # three grid sizes, two digit widths, FFT variant 1 on one size, mass and
+    # growth-rescaled weightings: bit-equal to individual solves with the same
+    # choices, and a graph whose kernel nodes do not grow with the item count
+    monkeypatch.setenv("AMBER_AUTOTUNE", "0")
+    rng = np.random.default_rng(9)
+    specs = [(16, 25.0)] * 3 + [(64, 100.0)] * 6 + [(128, 100.0)] * 4
+    ctx = B.Context(128 ** 3)
+    try:
+        ctx.set_tuning(16, sort_digit_bits=9)
+        ctx.set_tuning(64, sort_digit_bits=8)
+        ctx.set_tuning(128, fft_variant=1, sort_digit_bits=9)
+        items, ref = [], []
+        for i, (n, box) in enumerate(specs):
+            S, m = synth.realisation(n, box, 300 + i, device="cuda")
+            l = float(rng.uniform(1, 20))
+            w = B.AMBER_WEIGHT_MASS_GROWTH if i % 3 == 1 else B.AMBER_WEIGHT_MASS
+            h = B.history(float(rng.uniform(6.5, 9)), float(rng.uniform(2, 6)), float(rng.uniform(1.5, 5)), weighting=w)
+            items.append((S, m, box, l, h, torch.full_like(S, -1.0)))
+            ref.append(ctx.solve(S, m, box, l, h))
+        assert ctx.sync_status() == 0
+        batch = B.Batch([ctx], items)
+        # 5 transform passes x 3 sizes, (histogram + offsets + 4 digit passes)
+        # x 2 widths, thresholds + 2 scan forms + scatter
+        assert batch.kernel_nodes() == 5 * 3 + 6 * 2 + 4
+        batch.launch()
+        torch.cuda.synchronize()
+        assert ctx.sync_status() == 0
+        for it, r in zip(items, ref):
+            assert torch.equal(it[5], r)
+        batch.close()
+    finally:
+        ctx.close()
