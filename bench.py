@@ -298,7 +298,8 @@ def design_bytes(n: int, sort_passes: int) -> dict:
     """Algorithmic bytes per step of each kernel as this design moves them:
     the half spectrum at its true size, the mass riding through the sort as a
     second payload (+8 B/cell per pass), and the scan's (cell, z) pairs
-    written and read back by the scatter to cell order."""
+    regrouped by window (read 8, write 8 B/cell) before each window is written
+    whole (read 8, write 4 B/cell)."""
     C = n ** 3
     H = 8 * n * n * (n // 2 + 1)  # half spectrum, complex64
     if sort_passes == 1:
@@ -310,7 +311,7 @@ def design_bytes(n: int, sort_passes: int) -> dict:
         "fft_c2r_x": H + 4 * C,
         "sort_histogram": 4 * C,            # digit histograms (the key range comes with the inverse x pass)
         "sort_pass": sort,
-        "mass_reduce": 4 * C, "thresholds": 0, "scan_assign": 16 * C, "scatter_back": 12 * C,
+        "mass_reduce": 4 * C, "thresholds": 0, "scan_assign": 16 * C, "scatter_back": 28 * C,
     }
 
 
@@ -393,6 +394,8 @@ def run_amber(args):
     torch.cuda.empty_cache()
     h = B.history(*HIST)
     ctx = B.Context(C, device=local)
+    if args.fuse_histogram is not None:
+        ctx.set_tuning(n, fuse_histogram=args.fuse_histogram)
     z = torch.empty_like(S)
     stream = torch.cuda.current_stream()
 
@@ -426,6 +429,7 @@ def run_amber(args):
     prof = ctx.profile_read()
     ctx.profile(False)
     passes = ctx.sort_passes()  # digit passes of the timed solves' ranking
+    tuning = ctx.get_tuning(n)  # the choices the timed solves ran with
     st = ctx.sync_status()
     if st != 0:
         raise RuntimeError(f"device status after timed region: {B.status_string(st)}")
@@ -653,8 +657,12 @@ def run_amber(args):
     del S_d, m_d, z_d, z_h
 
     # each timed bracket is one kernel launch, except the histogram's, which
-    # also holds the one-CTA digit-offset scan (k_sort_offsets)
-    launches_per_step = (sum(v[1] for v in prof.values()) + prof["sort_histogram"][1]) / args.steps
+    # also holds the one-CTA digit-offset scan (k_sort_offsets) -- alone when
+    # the inverse x pass counted the digits -- and the scatter's, which holds
+    # the window split and the window write
+    fused = bool(tuning.get("fuse_histogram")) and tuning["sort_digit_bits"] == 8
+    launches_per_step = (sum(v[1] for v in prof.values()) + (0 if fused else prof["sort_histogram"][1]) +
+                         prof["scatter_back"][1]) / args.steps
     mb, db = model_bytes(n, passes), design_bytes(n, passes)
     kernels = {}
     for k, (ms_k, cnt) in prof.items():
@@ -716,6 +724,7 @@ def run_amber(args):
                                              "path": (path_design / (ms_max / 1e3) / 1e9) / peak},
                              "sort_passes": passes},
                 "kernels": kernels,
+                "tuning": {k: tuning[k] for k in ("fft_variant", "sort_digit_bits", "sort_match", "fuse_histogram")},
                 "clocks": clocks,
                 "cpu_baseline": cpu}
         if accuracy is not None:
@@ -866,6 +875,8 @@ def main():
     ap.add_argument("--cpu-sample-n", type=int, default=128)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--fuse-histogram", type=int, choices=[0, 1], default=None,
+                    help="override the size's choice of digit counts in the inverse x pass (8-bit digits)")
     ap.add_argument("--no-accuracy", action="store_true",
                     help="skip the oracle comparison of the workload's J and z_re (minutes of host time)")
     ap.add_argument("--no-extras", action="store_true", help="skip the batched and serving measurements")

@@ -243,7 +243,12 @@ int amber_solve_spectrum(amber_ctx *ctx, const void *d_spec, const float *d_mass
  *                    a 24-bit range takes 3 of either, the 8-bit ones cheaper);
  *   sort_match       0: digit peers by one warp ballot per digit bit;
  *                    1: by warp match (AMBER_SORT_RANK=ballot|match in the
- *                    environment overrides it).
+ *                    environment overrides it);
+ *   fuse_histogram   with 8-bit digits, 1: the solve's inverse x pass counts
+ *                    the intensities' digits as it writes them and the sort
+ *                    runs on the raw 32-bit keys (always four passes) with no
+ *                    histogram pass of its own; 0: a histogram pass of
+ *                    key - min(key) (a narrow key range may need fewer passes).
  * Every choice gives the same ranking (the stable descending order is
  * unique); the FFT variants differ only in FP32 rounding.  Defaults: 0, 8
  * for n >= 512 and 9 below, 0 (the tuner's picks on a synthetic field of the
@@ -259,6 +264,7 @@ typedef struct {
   int tuned;
   double fft_ms[2];
   double sort_ms[4];
+  int fuse_histogram;
 } amber_tuning_t;
 
 /* Measures every choice on the caller's own field (d_src, d_mass: n^3 floats
@@ -282,12 +288,13 @@ int amber_get_tuning(amber_ctx *ctx, int n, amber_tuning_t *out);
  *  - The transforms run one launch per pass and grid size (the items of a
  *    size back to back), the ranking one histogram, one digit-offset and one
  *    launch per digit pass per digit width, the matching one thresholds, one
- *    scan per weighting form and one scatter launch for all items.  Inside a
+ *    scan per weighting form and two scatter launches (window split, window
+ *    write) for all items.  Inside a
  *    launch each CTA finds its item from a prefix of the items' tile counts;
  *    ticket-ordered kernels (digit passes, scan) take tiles from the item's
  *    own ticket, so their look-backs stay within the item.  The graph's
- *    kernel nodes number about 5 per grid size plus 6 per digit width plus
- *    4, whatever the item count (amber_batch_kernel_nodes).
+ *    kernel nodes number 5 per grid size plus 6 per digit width plus 4 or 5,
+ *    whatever the item count (amber_batch_kernel_nodes).
  *  - The batch allocates its own workspace at creation (about 30 bytes per
  *    cell of all items together, plus the items' arguments); amber_batch_create
  *    and amber_create are the only calls that allocate.

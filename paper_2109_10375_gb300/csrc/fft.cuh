@@ -100,8 +100,16 @@ enum { PASS_FWD = 0, PASS_INV = 1, PASS_CONV = 2 };
 // MULTI (z-pass only): several transforms of size N back to back, item_stride
 // elements apart; line family `outer` of the launch is line y = outer % N of
 // item outer / N, whose box and l_mfp give kp[2 item] = kf, kp[2 item + 1] = l.
+// CTAs per SM the strided passes are compiled for (build-time tunables): two
+// keep 128 registers per thread at 256 threads.
+#ifndef AMBER_ZPASS_MINB
+#define AMBER_ZPASS_MINB 2
+#endif
+#ifndef AMBER_YPASS_MINB
+#define AMBER_YPASS_MINB 2
+#endif
 template <typename T, int N, int MODE, int V = 0, bool OOP = false, bool MULTI = false>
-__global__ void __launch_bounds__(strided_threads<N, V>(), 2)
+__global__ void __launch_bounds__(strided_threads<N, V>(), MODE == PASS_CONV ? AMBER_ZPASS_MINB : AMBER_YPASS_MINB)
 k_fft_strided(cpx<T>* __restrict__ H, int64_t elem_stride, int64_t outer_stride, int ncol,
               int ntx, const cpx<T>* __restrict__ tw, T kf, T l_mfp, T norm,
               const cpx<T>* __restrict__ Hin = nullptr, int64_t item_stride = 0,
@@ -371,7 +379,10 @@ k_fft_r2c_x(const T* __restrict__ src, cpx<T>* __restrict__ H, int64_t nrows, in
 // ---------------------------------------------------------------------------
 // MULTI: several transforms of size N back to back; the key range of item
 // row0 / rpi folds into krange[item] (one control block per item).
-template <typename T, int N, int V = 0, bool MULTI = false>
+// HIST (FP32): the intensities' raw 32-bit sort keys are also counted into
+// krange's histogram, four 8-bit digit positions, so a sort of raw keys with
+// 8-bit digits needs no histogram pass of its own.
+template <typename T, int N, int V = 0, bool MULTI = false, bool HIST = false>
 __global__ void __launch_bounds__(xpass_threads<N, V>())
 k_fft_c2r_x(const cpx<T>* __restrict__ H, T* __restrict__ J, int64_t nrows, int RS,
             const cpx<T>* __restrict__ tw, unsigned int* __restrict__ status, SortCtrl* __restrict__ krange,
@@ -435,11 +446,33 @@ k_fft_c2r_x(const cpx<T>* __restrict__ H, T* __restrict__ J, int64_t nrows, int 
   }
   bool bad = false, nan = false;
   K klo = ~K(0), khi = 0;
+  static_assert(!HIST || sizeof(K) == 4, "digit counts of 32-bit keys");
+  __shared__ uint32_t shist[HIST ? 4 * 256 : 1];
+  if constexpr (HIST) {
+    for (int i = tid; i < 4 * 256; i += NT) shist[i] = 0;
+    __syncthreads();
+  }
   auto track = [&](T x) {
     bad |= !isfinite(x);
     const K kk = enc_desc(x, nan);
     klo = kk < klo ? kk : klo;
     khi = kk > khi ? kk : khi;
+    if constexpr (HIST) {
+#pragma unroll
+      for (int p = 0; p < 4; ++p) {
+        const unsigned d = (unsigned)(kk >> (8 * p)) & 255u;
+        // neighbouring cells of a smooth field often share the upper digits:
+        // one add for the active lanes when they all agree
+        const unsigned am = __activemask();
+        const int leader = __ffs(am) - 1;
+        const unsigned d0 = __shfl_sync(am, d, leader);
+        if (p >= 2 && __all_sync(am, d == d0)) {
+          if ((int)(threadIdx.x & 31) == leader) atomicAdd(&shist[p * 256 + d0], (uint32_t)__popc(am));
+        } else {
+          atomicAdd(&shist[p * 256 + d], 1u);
+        }
+      }
+    }
   };
   if constexpr (R1 == 1) {
 #pragma unroll
@@ -495,6 +528,13 @@ k_fft_c2r_x(const cpx<T>* __restrict__ H, T* __restrict__ J, int64_t nrows, int 
   // fold the intensities' key range into the sort's control block
   if constexpr (MULTI) key_range_commit(klo, khi, krange + row0 / rpi);
   else if (krange) key_range_commit(klo, khi, krange);
+  if constexpr (HIST) {
+    __syncthreads();
+    for (int i = tid; i < 4 * 256; i += NT) {
+      const uint32_t c = shist[i];
+      if (c) atomicAdd(&krange->hist[i], c);
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -512,10 +552,12 @@ enum ProfKind {
 // spec_in (optional): the x- and y-transformed source kept by the caller
 // (source_spectrum_n's output); the first two passes are skipped and the z
 // pass reads it, leaving it unchanged.
+// hist8 (FP32, krange given): the inverse x pass also counts the raw keys'
+// four 8-bit digits into krange's histogram.
 template <typename T, int N, int V = 0>
 cudaError_t radiation_field_n(const T* src, T* J, cpx<T>* H, const cpx<T>* tw, double box, double l_mfp,
                               unsigned int* status, cudaStream_t s, FftProfile* prof, SortCtrl* krange,
-                              const cpx<T>* spec_in = nullptr) {
+                              const cpx<T>* spec_in = nullptr, bool hist8 = false) {
   using C = FftCfg<N, V>;
   const int RS = N / 2 + 2;
   const int ncol = N / 2 + 1;
@@ -535,6 +577,8 @@ cudaError_t radiation_field_n(const T* src, T* J, cpx<T>* H, const cpx<T>* tw, d
     cudaFuncSetAttribute(k_fft_strided<T, N, PASS_CONV, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sc);
     cudaFuncSetAttribute(k_fft_strided<T, N, PASS_CONV, V, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)sc);
+    if constexpr (sizeof(T) == 4)
+      cudaFuncSetAttribute(k_fft_c2r_x<T, N, V, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xs);
   }
   const int xgrid = (int)((nrows / 2 + C::XP - 1) / C::XP);
   const int ntx = (ncol + C::SB - 1) / C::SB;
@@ -564,7 +608,14 @@ cudaError_t radiation_field_n(const T* src, T* J, cpx<T>* H, const cpx<T>* tw, d
                                                                        kf, (T)l_mfp, norm);
   prof_end(prof, PK_FFT_Y_INV, s);
   prof_begin(prof, PK_C2R_X, s);
-  k_fft_c2r_x<T, N, V><<<xgrid, xpass_threads<N, V>(), xs, s>>>(H, J, nrows, RS, tw, status, krange);
+  if constexpr (sizeof(T) == 4) {
+    if (hist8 && krange)
+      k_fft_c2r_x<T, N, V, false, true><<<xgrid, xpass_threads<N, V>(), xs, s>>>(H, J, nrows, RS, tw, status, krange);
+    else
+      k_fft_c2r_x<T, N, V><<<xgrid, xpass_threads<N, V>(), xs, s>>>(H, J, nrows, RS, tw, status, krange);
+  } else {
+    k_fft_c2r_x<T, N, V><<<xgrid, xpass_threads<N, V>(), xs, s>>>(H, J, nrows, RS, tw, status, krange);
+  }
   prof_end(prof, PK_C2R_X, s);
   return cudaGetLastError();
 }

@@ -5,30 +5,30 @@ namespace amber {
 
 cudaError_t radiation_field_f32(int n, const float* src, float* J, void* H, const void* tw, double box, double l_mfp,
                                unsigned int* status, cudaStream_t s, FftProfile* prof,
-                               SortCtrl* krange, int variant, const void* spec_in) {
+                               SortCtrl* krange, int variant, const void* spec_in, bool hist8) {
   auto* h = reinterpret_cast<cpx<float>*>(H);
   auto* w = reinterpret_cast<const cpx<float>*>(tw);
   auto* si = reinterpret_cast<const cpx<float>*>(spec_in);
   if (variant == 1) {
     switch (n) {
-      case 128: return radiation_field_n<float, 128, 1>(src, J, h, w, box, l_mfp, status, s, prof, krange, si);
-      case 256: return radiation_field_n<float, 256, 1>(src, J, h, w, box, l_mfp, status, s, prof, krange, si);
-      case 512: return radiation_field_n<float, 512, 1>(src, J, h, w, box, l_mfp, status, s, prof, krange, si);
-      case 1024: return radiation_field_n<float, 1024, 1>(src, J, h, w, box, l_mfp, status, s, prof, krange, si);
+      case 128: return radiation_field_n<float, 128, 1>(src, J, h, w, box, l_mfp, status, s, prof, krange, si, hist8);
+      case 256: return radiation_field_n<float, 256, 1>(src, J, h, w, box, l_mfp, status, s, prof, krange, si, hist8);
+      case 512: return radiation_field_n<float, 512, 1>(src, J, h, w, box, l_mfp, status, s, prof, krange, si, hist8);
+      case 1024: return radiation_field_n<float, 1024, 1>(src, J, h, w, box, l_mfp, status, s, prof, krange, si, hist8);
       default: return cudaErrorInvalidValue;
     }
   }
   if (variant != 0) return cudaErrorInvalidValue;
   switch (n) {
-    case 4: return radiation_field_n<float, 4>(src, J, h, w, box, l_mfp, status, s, prof, krange, si);
-    case 8: return radiation_field_n<float, 8>(src, J, h, w, box, l_mfp, status, s, prof, krange, si);
-    case 16: return radiation_field_n<float, 16>(src, J, h, w, box, l_mfp, status, s, prof, krange, si);
-    case 32: return radiation_field_n<float, 32>(src, J, h, w, box, l_mfp, status, s, prof, krange, si);
-    case 64: return radiation_field_n<float, 64>(src, J, h, w, box, l_mfp, status, s, prof, krange, si);
-    case 128: return radiation_field_n<float, 128>(src, J, h, w, box, l_mfp, status, s, prof, krange, si);
-    case 256: return radiation_field_n<float, 256>(src, J, h, w, box, l_mfp, status, s, prof, krange, si);
-    case 512: return radiation_field_n<float, 512>(src, J, h, w, box, l_mfp, status, s, prof, krange, si);
-    case 1024: return radiation_field_n<float, 1024>(src, J, h, w, box, l_mfp, status, s, prof, krange, si);
+    case 4: return radiation_field_n<float, 4>(src, J, h, w, box, l_mfp, status, s, prof, krange, si, hist8);
+    case 8: return radiation_field_n<float, 8>(src, J, h, w, box, l_mfp, status, s, prof, krange, si, hist8);
+    case 16: return radiation_field_n<float, 16>(src, J, h, w, box, l_mfp, status, s, prof, krange, si, hist8);
+    case 32: return radiation_field_n<float, 32>(src, J, h, w, box, l_mfp, status, s, prof, krange, si, hist8);
+    case 64: return radiation_field_n<float, 64>(src, J, h, w, box, l_mfp, status, s, prof, krange, si, hist8);
+    case 128: return radiation_field_n<float, 128>(src, J, h, w, box, l_mfp, status, s, prof, krange, si, hist8);
+    case 256: return radiation_field_n<float, 256>(src, J, h, w, box, l_mfp, status, s, prof, krange, si, hist8);
+    case 512: return radiation_field_n<float, 512>(src, J, h, w, box, l_mfp, status, s, prof, krange, si, hist8);
+    case 1024: return radiation_field_n<float, 1024>(src, J, h, w, box, l_mfp, status, s, prof, krange, si, hist8);
     default: return cudaErrorInvalidValue;
   }
 }

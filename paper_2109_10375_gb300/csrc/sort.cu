@@ -160,8 +160,10 @@ __global__ void __launch_bounds__(256) k_sort_histogram_multi(const HistArgs* __
 }
 
 // One CTA: exclusive scan of each digit histogram, and the pass count.
+// raw: the histogram counted raw keys (the intensity kernel's digit counts):
+// the sort then runs on key - 0, so the key minimum is reset to 0.
 template <typename SRC, int RB>
-__device__ __forceinline__ void sort_offsets_body(SortCtrl* __restrict__ ctrl) {
+__device__ __forceinline__ void sort_offsets_body(SortCtrl* __restrict__ ctrl, bool raw = false) {
   using K = typename KeyOf<SRC>::K;
   constexpr int R = 1 << RB, P = max_passes<SRC, RB>();
   __shared__ uint32_t wsum[8];
@@ -194,6 +196,7 @@ __device__ __forceinline__ void sort_offsets_body(SortCtrl* __restrict__ ctrl) {
     }
   }
   if (threadIdx.x == 0) {
+    if (raw) ctrl->kmin = 0;
     const K range = (K)ctrl->kmax - (K)ctrl->kmin;
     int bits = 0;
     while (bits < (int)(8 * sizeof(K)) && (range >> bits) != 0) ++bits;
@@ -203,8 +206,8 @@ __device__ __forceinline__ void sort_offsets_body(SortCtrl* __restrict__ ctrl) {
 }
 
 template <typename SRC, int RB>
-__global__ void __launch_bounds__(256) k_sort_offsets(SortCtrl* __restrict__ ctrl) {
-  sort_offsets_body<SRC, RB>(ctrl);
+__global__ void __launch_bounds__(256) k_sort_offsets(SortCtrl* __restrict__ ctrl, bool raw) {
+  sort_offsets_body<SRC, RB>(ctrl, raw);
 }
 
 // One CTA per item.
@@ -537,7 +540,7 @@ template <typename SRC, int RB>
 static cudaError_t rank_impl_rb(const SortWork& w, const SRC* J, int64_t n, uint32_t* order, const float* mass_in,
                                 float* mass_out, unsigned long long* tile_mass, bool range_ready,
                                 unsigned int* status, cudaStream_t s, FftProfile* prof, unsigned int spin_limit,
-                                bool match) {
+                                bool match, bool hist_ready) {
   using K = typename KeyOf<SRC>::K;
   constexpr int R = 1 << RB, P = max_passes<SRC, RB>();
   const bool with_mass = mass_in != nullptr;
@@ -553,12 +556,18 @@ static cudaError_t rank_impl_rb(const SortWork& w, const SRC* J, int64_t n, uint
   uint32_t* lbB = w.lookback + sort_lookback_words(w.max_cells);
 
   prof_begin(prof, PK_SORT_HIST, s);
-  {
+  if (hist_ready && range_ready && sizeof(SRC) == 4 && RB == 8) {
+    // the intensity kernel counted the raw keys' digits: clear the first
+    // pass's look-back and form the offsets of a raw-key sort
+    e = cudaMemsetAsync(lbA, 0, (size_t)lbw * sizeof(uint32_t), s);
+    if (e != cudaSuccess) return e;
+    k_sort_offsets<SRC, RB><<<1, 256, 0, s>>>(ctrl, true);
+  } else {
     int grid = (int)std::min<int64_t>((n / (16 / (int)sizeof(SRC)) + 255) / 256, (int64_t)w.num_sms * 8);
     if (grid < 1) grid = 1;
     if (!range_ready) k_key_range<SRC><<<grid, 256, 0, s>>>(J, n, ctrl, status);
     k_sort_histogram<SRC, RB><<<grid, 256, 0, s>>>(J, n, ctrl, lbA, lbw);
-    k_sort_offsets<SRC, RB><<<1, 256, 0, s>>>(ctrl);
+    k_sort_offsets<SRC, RB><<<1, 256, 0, s>>>(ctrl, false);
   }
   prof_end(prof, PK_SORT_HIST, s);
 
@@ -606,21 +615,22 @@ static cudaError_t rank_impl_rb(const SortWork& w, const SRC* J, int64_t n, uint
 template <typename SRC>
 cudaError_t rank_impl(const SortWork& w, const SRC* J, int64_t n, uint32_t* order, const float* mass_in,
                       float* mass_out, unsigned long long* tile_mass, bool range_ready, unsigned int* status,
-                      cudaStream_t s, FftProfile* prof, unsigned int spin_limit, int digit_bits, int match) {
+                      cudaStream_t s, FftProfile* prof, unsigned int spin_limit, int digit_bits, int match,
+                      bool hist_ready) {
   const int env = rank_env();
   const bool m = env >= 0 ? env == 1 : match == 1;
   if (digit_bits == 0) digit_bits = KeyOf<SRC>::RB;
   if constexpr (sizeof(SRC) == 4) {
     if (digit_bits == 8)
       return rank_impl_rb<SRC, 8>(w, J, n, order, mass_in, mass_out, tile_mass, range_ready, status, s, prof,
-                                  spin_limit, m);
+                                  spin_limit, m, hist_ready);
     if (digit_bits == 9)
       return rank_impl_rb<SRC, 9>(w, J, n, order, mass_in, mass_out, tile_mass, range_ready, status, s, prof,
-                                  spin_limit, m);
+                                  spin_limit, m, hist_ready);
   } else {
     if (digit_bits == 8)
       return rank_impl_rb<SRC, 8>(w, J, n, order, mass_in, mass_out, tile_mass, range_ready, status, s, prof,
-                                  spin_limit, m);
+                                  spin_limit, m, hist_ready);
   }
   return cudaErrorInvalidValue;
 }
@@ -716,10 +726,10 @@ template int rank_args<float>(const SortWork&, const float*, int64_t, uint32_t*,
 
 template cudaError_t rank_impl<float>(const SortWork&, const float*, int64_t, uint32_t*, const float*, float*,
                                       unsigned long long*, bool, unsigned int*, cudaStream_t, FftProfile*,
-                                      unsigned int, int, int);
+                                      unsigned int, int, int, bool);
 template cudaError_t rank_impl<double>(const SortWork&, const double*, int64_t, uint32_t*, const float*, float*,
                                        unsigned long long*, bool, unsigned int*, cudaStream_t, FftProfile*,
-                                       unsigned int, int, int);
+                                       unsigned int, int, int, bool);
 
 // Failure-detection hook: the look-back wait on a word nothing publishes.
 __global__ void k_wait_never(const uint32_t* __restrict__ word, unsigned int* __restrict__ status,

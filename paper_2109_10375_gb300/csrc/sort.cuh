@@ -109,11 +109,14 @@ cudaError_t sort_ctrl_reset(SortCtrl* ctrl, cudaStream_t s);
 // kernel), so the range pass is skipped.  digit_bits: 9 or 8 for FP32 keys, 8
 // for FP64 (0: the default, 9 / 8); match: 1 digit peers by warp match, 0 by
 // ballots (default).  The environment variable AMBER_SORT_RANK=ballot|match
-// overrides match.
+// overrides match.  hist_ready (FP32 keys, 8-bit digits, range_ready): the
+// intensity kernel already counted the raw keys' digits into ctrl (hist8 of
+// the radiation field), so the sort runs on raw keys without a histogram pass.
 template <typename SRC>
 cudaError_t rank_impl(const SortWork& w, const SRC* J, int64_t n, uint32_t* order, const float* mass_in,
                       float* mass_out, unsigned long long* tile_mass, bool range_ready, unsigned int* status,
-                      cudaStream_t s, FftProfile* prof, unsigned int spin_limit, int digit_bits = 0, int match = 0);
+                      cudaStream_t s, FftProfile* prof, unsigned int spin_limit, int digit_bits = 0, int match = 0,
+                      bool hist_ready = false);
 
 cudaError_t wait_timeout_test(uint32_t* zero_word, unsigned int* status, unsigned int spin_limit, cudaStream_t s);
 

@@ -137,3 +137,33 @@ def test_batch_tunes_each_size_once(B, monkeypatch):
     finally:
         for c in ctxs:
             c.close()
+
+
+@pytest.mark.parametrize("n,variant", [(8, 0), (64, 0), (256, 0), (256, 1), (512, 0)])
+def test_fused_digit_counts_give_the_same_solve(B, n, variant):
+    # 8-bit digits with the digit counts taken in the inverse x pass (raw
+    # keys, no histogram pass) against the separate histogram of key - min:
+    # the stable order is unique and the prefix sums exact, so z_re, the
+    # order and the rank-order masses are bit-equal; the order is the stable
+    # descending order of the intensities
+    box, l = 100.0 * n / 128, 3.0
+    S, m = synth.realisation(n, box, 41, device="cuda")
+    h = B.history(8.0, 4.0, 3.0)
+    outs = []
+    with B.Context(n ** 3) as ctx:
+        for fuse in (0, 1):
+            ctx.set_tuning(n, fft_variant=variant, sort_digit_bits=8, fuse_histogram=fuse)
+            z = torch.empty_like(S)
+            J = torch.empty_like(S)
+            order = torch.empty(n ** 3, dtype=torch.int32, device="cuda")
+            mr = torch.empty(n ** 3, device="cuda")
+            ctx.solve_ex(S, m, box, l, h, z, order, mr, J_out=J)
+            assert ctx.sync_status() == 0
+            assert ctx.get_tuning(n)["fuse_histogram"] == fuse
+            if fuse:
+                assert ctx.sort_passes() == 4  # raw 32-bit keys
+            outs.append((z, J, order, mr))
+    for a, b in zip(*outs):
+        assert torch.equal(a, b)
+    Jn = outs[1][1].cpu().numpy().reshape(-1).astype(np.float64)
+    np.testing.assert_array_equal(outs[1][2].cpu().numpy(), np.argsort(-Jn, kind="stable"))
