@@ -298,8 +298,7 @@ def design_bytes(n: int, sort_passes: int) -> dict:
     """Algorithmic bytes per step of each kernel as this design moves them:
     the half spectrum at its true size, the mass riding through the sort as a
     second payload (+8 B/cell per pass), and the scan's (cell, z) pairs
-    regrouped by window (read 8, write 8 B/cell) before each window is written
-    whole (read 8, write 4 B/cell)."""
+    written and read back by the scatter to cell order."""
     C = n ** 3
     H = 8 * n * n * (n // 2 + 1)  # half spectrum, complex64
     if sort_passes == 1:
@@ -311,7 +310,7 @@ def design_bytes(n: int, sort_passes: int) -> dict:
         "fft_c2r_x": H + 4 * C,
         "sort_histogram": 4 * C,            # digit histograms (the key range comes with the inverse x pass)
         "sort_pass": sort,
-        "mass_reduce": 4 * C, "thresholds": 0, "scan_assign": 16 * C, "scatter_back": 28 * C,
+        "mass_reduce": 4 * C, "thresholds": 0, "scan_assign": 16 * C, "scatter_back": 12 * C,
     }
 
 
@@ -658,11 +657,9 @@ def run_amber(args):
 
     # each timed bracket is one kernel launch, except the histogram's, which
     # also holds the one-CTA digit-offset scan (k_sort_offsets) -- alone when
-    # the inverse x pass counted the digits -- and the scatter's, which holds
-    # the window split and the window write
+    # the inverse x pass counted the digits
     fused = bool(tuning.get("fuse_histogram")) and tuning["sort_digit_bits"] == 8
-    launches_per_step = (sum(v[1] for v in prof.values()) + (0 if fused else prof["sort_histogram"][1]) +
-                         prof["scatter_back"][1]) / args.steps
+    launches_per_step = (sum(v[1] for v in prof.values()) + (0 if fused else prof["sort_histogram"][1])) / args.steps
     mb, db = model_bytes(n, passes), design_bytes(n, passes)
     kernels = {}
     for k, (ms_k, cnt) in prof.items():

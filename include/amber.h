@@ -288,12 +288,11 @@ int amber_get_tuning(amber_ctx *ctx, int n, amber_tuning_t *out);
  *  - The transforms run one launch per pass and grid size (the items of a
  *    size back to back), the ranking one histogram, one digit-offset and one
  *    launch per digit pass per digit width, the matching one thresholds, one
- *    scan per weighting form and two scatter launches (window split, window
- *    write) for all items.  Inside a
+ *    scan per weighting form and one scatter launch for all items.  Inside a
  *    launch each CTA finds its item from a prefix of the items' tile counts;
  *    ticket-ordered kernels (digit passes, scan) take tiles from the item's
  *    own ticket, so their look-backs stay within the item.  The graph's
- *    kernel nodes number 5 per grid size plus 6 per digit width plus 4 or 5,
+ *    kernel nodes number 5 per grid size plus 6 per digit width plus 3 or 4,
  *    whatever the item count (amber_batch_kernel_nodes).
  *  - The batch allocates its own workspace at creation (about 30 bytes per
  *    cell of all items together, plus the items' arguments); amber_batch_create

@@ -175,7 +175,7 @@ struct Plan {
   int n32 = 0, n64 = 0;
   int64_t cells64 = 0;
   size_t off_spec, off_keysA, off_keysB, off_idxA, off_idxB, off_massA, off_massB, off_lb, off_sctrl, off_actrl, off_X, off_invdx, off_lin,
-      off_state, off_btab, off_fill, off_tilemass, off_status, off_srcsum, off_pow, off_tw32, off_tw64, total;
+      off_state, off_btab, off_tilemass, off_status, off_srcsum, off_pow, off_tw32, off_tw64, total;
   size_t tw32_off[11] = {}, tw64_off[11] = {};
 };
 
@@ -209,7 +209,6 @@ static Plan make_plan(int64_t max_cells) {
   p.off_lin = take((size_t)4 * kMaxTable * sizeof(float));
   p.off_state = take(stt);
   p.off_btab = take((size_t)((max_cells + kScanTile - 1) / kScanTile) * (kMaxBuckets + 1) * sizeof(uint16_t));
-  p.off_fill = take(window_fill_words(max_cells) * sizeof(uint32_t));
   p.off_tilemass = take((size_t)sort_tiles(max_cells) * 16);
   p.off_status = take(256);
   p.off_srcsum = take(256);
@@ -397,11 +396,6 @@ int amber_create(amber_ctx** out, int device, int64_t max_cells) {
   c->assw.bcell = reinterpret_cast<uint32_t*>(c->sortw.keysA);
   c->assw.bz = reinterpret_cast<float*>(c->sortw.keysB);
   c->assw.btab = reinterpret_cast<uint16_t*>(c->ws + p.off_btab);
-  // the pairs regrouped by window: the first index and mass arrays, free once
-  // the scan has read the rank order (from either side, or from the caller)
-  c->assw.wcell = c->sortw.idxA;
-  c->assw.wz = c->sortw.massA;
-  c->assw.fill = reinterpret_cast<uint32_t*>(c->ws + p.off_fill);
   c->assw.num_sms = c->num_sms;
   // twiddles w_n^m = exp(-2 pi i m / n), FP64 on the host, rounded for FP32
   for (int l = 6, n = 64; n <= p.n32; ++l, n *= 2) {
@@ -1000,7 +994,6 @@ int amber_batch_create(amber_batch** out, amber_ctx* const* ctxs, int nctx, cons
     size_t J, kA, iA, iB, mA, mB, spec, lb, actrl, Xq, inv, lin, state, btab, tmass;
     int64_t sort_tiles, scan_tiles;
     int nbuckets;
-    size_t fill;
   };
   std::vector<ItemWs> iw(nitems);
   int64_t cells = 0;
@@ -1044,15 +1037,10 @@ int amber_batch_create(amber_batch** out, amber_ctx* const* ctxs, int nctx, cons
     state_total += align256((size_t)w.scan_tiles * 8);
   }
   const size_t offState = L.take(state_total);  // scan look-back words of every item (one memset)
-  size_t fill_total = 0;
-  for (int i : ord) fill_total += window_fill_words(iw[i].C) * sizeof(uint32_t);
-  const size_t offFill = L.take(fill_total);  // window fill counts of every item (one memset)
   {
-    size_t so = 0, fo = 0;
+    size_t so = 0;
     for (int i : ord) {
       ItemWs& w = iw[i];
-      w.fill = offFill + fo;
-      fo += window_fill_words(w.C) * sizeof(uint32_t);
       w.state = offState + so;
       so += align256((size_t)w.scan_tiles * 8);
       w.lb = L.take(2 * sort_lookback_words(w.C) * 4);
@@ -1122,9 +1110,6 @@ int amber_batch_create(amber_batch** out, amber_ctx* const* ctxs, int nctx, cons
     a.bcell = reinterpret_cast<uint32_t*>(s.keysA);
     a.bz = reinterpret_cast<float*>(s.keysB);
     a.btab = reinterpret_cast<uint16_t*>(W + w.btab);
-    a.wcell = s.idxA;
-    a.wz = s.massA;
-    a.fill = reinterpret_cast<uint32_t*>(W + w.fill);
     a.num_sms = c0->num_sms;
   }
 
@@ -1185,11 +1170,11 @@ int amber_batch_create(amber_batch** out, amber_ctx* const* ctxs, int nctx, cons
   }
   // ---- matching: thresholds and scatter for every item, scans per weighting form
   AssignMulti am{};
-  size_t o_thresh, o_scan[2], o_spre[2], o_scatter, o_xpre, o_wpre;
+  size_t o_thresh, o_scan[2], o_spre[2], o_scatter, o_xpre;
   {
     std::vector<ThreshArgs> th;
     std::vector<ScanArgs> sc[2];
-    std::vector<uint32_t> spre[2] = {{0}, {0}}, xpre{0}, wpre{0};
+    std::vector<uint32_t> spre[2] = {{0}, {0}}, xpre{0};
     std::vector<ScatterArgs> xs;
     for (int k = 0; k < nitems; ++k) {
       const int i = ord[k];
@@ -1203,8 +1188,7 @@ int amber_batch_create(amber_batch** out, amber_ctx* const* ctxs, int nctx, cons
       sc[f].push_back(sa);
       spre[f].push_back(spre[f].back() + (uint32_t)iw[i].scan_tiles);
       xs.push_back(xa);
-      xpre.push_back(xpre.back() + (uint32_t)(xa.nchunks * xa.nbuckets));
-      wpre.push_back(wpre.back() + (uint32_t)xa.nwin);
+      xpre.push_back(xpre.back() + (uint32_t)(xa.groups * xa.nbuckets));
     }
     am.M = nitems;
     for (int f = 0; f < 2; ++f) {
@@ -1213,12 +1197,10 @@ int amber_batch_create(amber_batch** out, amber_ctx* const* ctxs, int nctx, cons
       o_scan[f] = place(sc[f]);
       o_spre[f] = place(spre[f]);
     }
-    am.split_blocks = xpre.back();
-    am.write_blocks = wpre.back();
+    am.scatter_blocks = xpre.back();
     o_thresh = place(th);
     o_scatter = place(xs);
     o_xpre = place(xpre);
-    o_wpre = place(wpre);
   }
   cudaError_t e = cudaMalloc(&b->args, A.total);
   unsigned char* G = b->args;
@@ -1231,8 +1213,7 @@ int amber_batch_create(amber_batch** out, amber_ctx* const* ctxs, int nctx, cons
     am.scan_prefix[f] = reinterpret_cast<const uint32_t*>(G + o_spre[f]);
   }
   am.scatter = reinterpret_cast<const ScatterArgs*>(G + o_scatter);
-  am.split_prefix = reinterpret_cast<const uint32_t*>(G + o_xpre);
-  am.write_prefix = reinterpret_cast<const uint32_t*>(G + o_wpre);
+  am.scatter_prefix = reinterpret_cast<const uint32_t*>(G + o_xpre);
   for (SortGroup& q : sg) {
     q.r.hist = reinterpret_cast<const HistArgs*>(G + q.hist);
     q.r.hist_prefix = reinterpret_cast<const uint32_t*>(G + q.hpre);
@@ -1267,7 +1248,6 @@ int amber_batch_create(amber_batch** out, amber_ctx* const* ctxs, int nctx, cons
     if (e == cudaSuccess) e = rank_multi(q.r, q.rb, q.match == 1, origin);
   if (e == cudaSuccess) e = cudaMemsetAsync(W + offACtrl, 0, (size_t)nitems * kAssignCtrlBytes, origin);
   if (e == cudaSuccess) e = cudaMemsetAsync(W + offState, 0, state_total, origin);
-  if (e == cudaSuccess) e = cudaMemsetAsync(W + offFill, 0, fill_total, origin);
   if (e == cudaSuccess) e = assign_multi(am, origin);
   if (capturing) {
     const cudaError_t e2 = cudaStreamEndCapture(origin, &b->graph);

@@ -647,170 +647,76 @@ __global__ void __launch_bounds__(kScanThreads, 2)
   scan_assign_body<false, false, LIN>(sa);
 }
 
-// Scatter back to cell order, level 2: CTA (bucket b, chunk c) takes bucket
-// b's runs of the scan tiles [c K, (c+1) K), K = a.chunk_tiles = min(nbuckets,
-// kSplitTiles) (about kSplitBatch pairs when cells fall evenly), up to
-// kSplitBatch pairs at a time, sorts them by window (2^14 cells) in shared
-// memory, reserves room in each window it touches with one atomic add, and
-// writes each window's pairs as one contiguous run.  Pairs land in a window
-// in any order; every cell of a window appears exactly once across the CTAs
-// (the ranking is a permutation), so window w ends up holding exactly its
-// cells at [w 2^14, w 2^14 + size).  A cell outside the grid or a window
-// overfilled (an order that is not a permutation) is dropped and latches
-// AMBER_ERR_INVALID_ARG.
-__device__ __forceinline__ void window_split_body(const ScatterArgs& a, uint32_t blk) {
-  constexpr int NT = kSplitThreads, IT = kSplitItems, BATCH = kSplitBatch, W = kWinPerBucket;
-  static_assert(W <= NT && kSplitTiles <= NT, "one thread per window and per run");
-  __shared__ uint32_t run_s[kSplitTiles];
-  __shared__ uint32_t run_off[kSplitTiles + 1];
-  __shared__ uint32_t hist[W], wstart[W], gbase[W];
-  __shared__ uint32_t wsum[NT / 32];
-  __shared__ uint32_t stage_c[BATCH];
-  __shared__ float stage_z[BATCH];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int b = (int)(blk / (uint32_t)a.nchunks);
-  const int K = a.chunk_tiles;
-  const int64_t t0 = (int64_t)(blk - (uint32_t)b * (uint32_t)a.nchunks) * K;
-  const int tcount = (int)(a.tiles - t0 < (int64_t)K ? a.tiles - t0 : (int64_t)K);
-  const uint32_t n = (uint32_t)a.n;  // n <= 2^30
-  const uint32_t gw0 = (uint32_t)b * W;  // first window of the bucket
-  bool bad = false;
-
-  // block-wide exclusive scan of one value per thread (returns the total)
-  auto block_scan = [&](uint32_t v, uint32_t& excl) -> uint32_t {
-    uint32_t x = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-      if (lane >= o) x += y;
-    }
-    if (lane == 31) wsum[warp] = x;
-    __syncthreads();
-    uint32_t pre = 0, tot = 0;
-#pragma unroll
-    for (int w = 0; w < NT / 32; ++w) {
-      pre += (w < warp) ? wsum[w] : 0u;
-      tot += wsum[w];
-    }
-    excl = pre + x - v;
-    __syncthreads();
-    return tot;
-  };
-
-  uint32_t len = 0;
-  if (tid < tcount) {
-    const uint16_t* row = a.btab + (t0 + tid) * (a.nbuckets + 1);
-    const uint32_t s0 = row[b], s1 = row[b + 1];
-    run_s[tid] = s0;
-    len = s1 - s0;
+// z_re[cell] = z, bucket after bucket: CTA (bucket b, tile group g) copies
+// bucket b's run of every tile in its group (one tile per warp at the
+// default group size).  A warp takes its runs in rounds of four 32-pair
+// chunks: all the round's loads (lanes read a run coalesced), then its
+// stores, so the dependent load -> store chains overlap.  A
+// bucket's cells span a bounded region of z_re, so the permuted writes of
+// the CTAs working on it stay close together.
+__device__ __forceinline__ void scatter_back_body(const uint32_t* __restrict__ bcell, const float* __restrict__ bz,
+                                                  const uint16_t* __restrict__ btab, int nbuckets, int64_t tiles,
+                                                  int groups, float* __restrict__ zre, uint32_t blk) {
+  constexpr int TPW = kBackTilesPerCta / 8;  // tiles per warp
+  const int b = blk / groups;
+  const int64_t g = blk - (int64_t)b * groups;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned long long stream_pol = l2_evict_first(), keep_pol = l2_evict_last();
+  const int64_t t0 = g * kBackTilesPerCta + warp * TPW;
+  // lane k < TPW fetches tile t0 + k's run bounds
+  int s_l = 0, e_l = 0;
+  if (lane < TPW && t0 + lane < tiles) {
+    const uint16_t* row = btab + (t0 + lane) * (nbuckets + 1);
+    s_l = row[b];
+    e_l = row[b + 1];
   }
-  uint32_t off;
-  const uint32_t total = block_scan(len, off);
-  if (tid < tcount) run_off[tid] = off;
-  if (tid == 0) run_off[tcount] = total;
-  __syncthreads();
-
-  for (uint32_t base = 0; base < total; base += BATCH) {
-    const uint32_t cnt = min(total - base, (uint32_t)BATCH);
-    if (tid < W) hist[tid] = 0;
-    __syncthreads();
-    uint32_t cc[IT], sl[IT];
-    float zz[IT];
+  // rounds of 4 x 32 pairs per run: the loads of all the warp's runs, then the stores
+  constexpr int G = 4;
+  int len = e_l - s_l;
 #pragma unroll
-    for (int k = 0; k < IT; ++k) {
-      const uint32_t jl = (uint32_t)(k * NT + tid);
-      cc[k] = 0xffffffffu;
-      if (jl < cnt) {
-        const uint32_t j = base + jl;
-        // the run holding pair j: the largest t with run_off[t] <= j
-        int lo = 0, hi = tcount - 1;
-        while (lo < hi) {
-          const int mid = (lo + hi + 1) >> 1;
-          if (run_off[mid] <= j) lo = mid;
-          else hi = mid - 1;
-        }
-        const int64_t at = (t0 + lo) * kScanTile + run_s[lo] + (j - run_off[lo]);
-        const uint32_t c = a.bcell[at];
-        zz[k] = a.bz[at];
-        const uint32_t w = (c >> kWinShift) - gw0;
-        if (c < n && w < (uint32_t)W) {
-          cc[k] = c;
-          sl[k] = atomicAdd(&hist[w], 1u);
-        } else {
-          bad = true;
+  for (int o = 16; o >= 1; o >>= 1) len = max(len, __shfl_xor_sync(0xffffffffu, len, o));
+  int s_k[TPW], e_k[TPW];
+#pragma unroll
+  for (int k = 0; k < TPW; ++k) {
+    s_k[k] = __shfl_sync(0xffffffffu, s_l, k);
+    e_k[k] = __shfl_sync(0xffffffffu, e_l, k);
+  }
+#pragma unroll 1
+  for (int j0 = 0; j0 < len; j0 += 32 * G) {
+    uint32_t c[TPW * G];
+    float zz[TPW * G];
+#pragma unroll
+    for (int k = 0; k < TPW; ++k) {
+#pragma unroll
+      for (int q = 0; q < G; ++q) {
+        const int i = s_k[k] + j0 + 32 * q + lane;
+        c[k * G + q] = 0xffffffffu;
+        if (i < e_k[k]) {
+          const int64_t at = (t0 + k) * kScanTile + i;
+          c[k * G + q] = ld_hint(bcell + at, stream_pol);
+          zz[k * G + q] = ld_hint(bz + at, stream_pol);
         }
       }
     }
-    __syncthreads();
-    // window starts inside the staging area, and each window's room in HBM
-    uint32_t ws;
-    const uint32_t h = tid < W ? hist[tid] : 0u;
-    const uint32_t staged = block_scan(h, ws);
-    if (tid < W) {
-      wstart[tid] = ws;
-      // counters window-major (bucket fastest): the CTAs of one bucket, which
-      // run together, spread their adds over many L2 lines
-      if (h) gbase[tid] = atomicAdd(&a.fill[(int64_t)tid * a.nbuckets + b], h);
-    }
-    __syncthreads();
 #pragma unroll
-    for (int k = 0; k < IT; ++k) {
-      if (cc[k] == 0xffffffffu) continue;
-      const uint32_t pos = wstart[(cc[k] >> kWinShift) - gw0] + sl[k];
-      stage_c[pos] = cc[k];
-      stage_z[pos] = zz[k];
-    }
-    __syncthreads();
-    // consecutive threads write consecutive slots of one window
-    for (uint32_t p = tid; p < staged; p += NT) {
-      const uint32_t c = stage_c[p];
-      const uint32_t gw = c >> kWinShift, w = gw - gw0;
-      const uint32_t slot = gbase[w] + (p - wstart[w]);
-      const uint32_t wsize = min((uint32_t)kWinCells, n - gw * (uint32_t)kWinCells);
-      if (slot < wsize) {
-        const int64_t P = (int64_t)gw * kWinCells + slot;
-        a.wcell[P] = c;
-        a.wz[P] = stage_z[p];
-      } else {
-        bad = true;
-      }
-    }
-    __syncthreads();  // the staging area and counters are reused by the next round
+    for (int q = 0; q < TPW * G; ++q)
+      if (c[q] != 0xffffffffu) st_hint(zre + c[q], zz[q], keep_pol);
   }
-  if (__any_sync(0xffffffffu, bad) && lane == 0) raise_status(a.status, AMBER_ERR_INVALID_ARG);
 }
 
-// Level 3: one CTA per window writes z_re of its 2^14 cells, staged in shared
-// memory from the window's pairs, as whole lines.
-__device__ __forceinline__ void window_write_body(const ScatterArgs& a, uint32_t gw) {
-  __shared__ float sz[kWinCells];
-  const int64_t base = (int64_t)gw * kWinCells;
-  const uint32_t wsize = (uint32_t)(a.n - base < (int64_t)kWinCells ? a.n - base : (int64_t)kWinCells);
-  const unsigned long long stream_pol = l2_evict_first();
-  for (uint32_t i = threadIdx.x; i < wsize; i += blockDim.x) {
-    const uint32_t lc = ld_hint(a.wcell + base + i, stream_pol) - (uint32_t)base;
-    const float z = ld_hint(a.wz + base + i, stream_pol);
-    if (lc < wsize) sz[lc] = z;  // a slot the split left empty (invalid order) holds anything
-  }
-  __syncthreads();
-  for (uint32_t i = threadIdx.x; i < wsize; i += blockDim.x) a.zre[base + i] = sz[i];
+__global__ void __launch_bounds__(256) k_scatter_back(const uint32_t* __restrict__ bcell,
+                                                      const float* __restrict__ bz,
+                                                      const uint16_t* __restrict__ btab, int nbuckets,
+                                                      int64_t tiles, int groups, float* __restrict__ zre) {
+  scatter_back_body(bcell, bz, btab, nbuckets, tiles, groups, zre, blockIdx.x);
 }
 
-__global__ void __launch_bounds__(kSplitThreads, 2) k_window_split(const ScatterArgs a) {
-  window_split_body(a, blockIdx.x);
-}
-__global__ void __launch_bounds__(512) k_window_write(const ScatterArgs a) { window_write_body(a, blockIdx.x); }
-
-// Several matchings at once: CTA b works on item find_item(prefix, M, b).
-__global__ void __launch_bounds__(kSplitThreads, 2) k_window_split_multi(const ScatterArgs* __restrict__ args,
-                                                                         const uint32_t* __restrict__ prefix, int M) {
-  const int it = find_item(prefix, M, blockIdx.x);
-  window_split_body(args[it], blockIdx.x - prefix[it]);
-}
-__global__ void __launch_bounds__(512) k_window_write_multi(const ScatterArgs* __restrict__ args,
+// Several scatters at once: CTA b works on item find_item(prefix, M, b).
+__global__ void __launch_bounds__(256) k_scatter_back_multi(const ScatterArgs* __restrict__ args,
                                                             const uint32_t* __restrict__ prefix, int M) {
   const int it = find_item(prefix, M, blockIdx.x);
-  window_write_body(args[it], blockIdx.x - prefix[it]);
+  const ScatterArgs& a = args[it];
+  scatter_back_body(a.bcell, a.bz, a.btab, a.nbuckets, a.tiles, a.groups, a.zre, blockIdx.x - prefix[it]);
 }
 
 // ---------------------------------------------------------------------------
@@ -938,21 +844,8 @@ void assign_args(const AssignWork& w, const uint32_t* order, const float* mass, 
   x.btab = w.btab;
   x.nbuckets = a.nbuckets;
   x.tiles = tiles;
-  x.chunk_tiles = a.nbuckets < kSplitTiles ? a.nbuckets : kSplitTiles;
-  x.nchunks = (int)((tiles + x.chunk_tiles - 1) / x.chunk_tiles);
-  x.fill = w.fill;
-  x.wcell = w.wcell;
-  x.wz = w.wz;
-  x.n = n;
-  x.nwin = (n + kWinCells - 1) / kWinCells;
+  x.groups = (int)((tiles + kBackTilesPerCta - 1) / kBackTilesPerCta);
   x.zre = zre;
-  x.status = status;
-}
-
-size_t window_fill_words(int64_t n) {
-  int nb, sh;
-  bucket_plan(n, &nb, &sh);
-  return (size_t)nb * kWinPerBucket;
 }
 
 cudaError_t assign_impl(const AssignWork& w, const uint32_t* order, const float* mass, bool mass_in_rank_order,
@@ -997,10 +890,8 @@ cudaError_t assign_impl(const AssignWork& w, const uint32_t* order, const float*
   }
   prof_end(prof, PK_SCAN_ASSIGN, s);
   prof_begin(prof, PK_SCATTER_BACK, s);
-  e = cudaMemsetAsync(xa.fill, 0, window_fill_words(n) * sizeof(uint32_t), s);
-  if (e != cudaSuccess) return e;
-  k_window_split<<<(unsigned)(xa.nbuckets * xa.nchunks), kSplitThreads, 0, s>>>(xa);
-  k_window_write<<<(unsigned)xa.nwin, 512, 0, s>>>(xa);
+  k_scatter_back<<<(unsigned)(xa.groups * xa.nbuckets), 256, 0, s>>>(xa.bcell, xa.bz, xa.btab, xa.nbuckets, xa.tiles,
+                                                                     xa.groups, xa.zre);
   prof_end(prof, PK_SCATTER_BACK, s);
   return cudaGetLastError();
 }
@@ -1009,8 +900,7 @@ cudaError_t assign_multi(const AssignMulti& m, cudaStream_t s) {
   k_thresholds_multi<<<m.M, 1024, 0, s>>>(m.thresh);
   if (m.scan_tiles[0]) k_scan_assign_multi<false><<<m.scan_tiles[0], kScanThreads, 0, s>>>(m.scan[0], m.scan_prefix[0], m.Mg[0]);
   if (m.scan_tiles[1]) k_scan_assign_multi<true><<<m.scan_tiles[1], kScanThreads, 0, s>>>(m.scan[1], m.scan_prefix[1], m.Mg[1]);
-  k_window_split_multi<<<m.split_blocks, kSplitThreads, 0, s>>>(m.scatter, m.split_prefix, m.M);
-  k_window_write_multi<<<m.write_blocks, 512, 0, s>>>(m.scatter, m.write_prefix, m.M);
+  k_scatter_back_multi<<<m.scatter_blocks, 256, 0, s>>>(m.scatter, m.scatter_prefix, m.M);
   return cudaGetLastError();
 }
 

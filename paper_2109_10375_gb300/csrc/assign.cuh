@@ -15,14 +15,8 @@ constexpr int kScanTile = kScanThreads * kScanItems;
 constexpr int kMaxTable = 1 << 16;
 constexpr int kMaxBuckets = 1024;
 
-constexpr int kBucketShift = 23;  // 2^23 cells (32 MB of z_re) per bucket
-constexpr int kWinShift = 14;     // 2^14 cells (64 KB of z_re) per window
-constexpr int kWinCells = 1 << kWinShift;
-constexpr int kWinPerBucket = 1 << (kBucketShift - kWinShift);
-constexpr int kSplitTiles = 128;   // scan tiles whose bucket runs one window-split CTA takes
-constexpr int kSplitThreads = 512;
-constexpr int kSplitItems = 16;
-constexpr int kSplitBatch = kSplitThreads * kSplitItems;  // pairs sorted by window per round
+constexpr int kBackTilesPerCta = 8;  // scan tiles one scatter-back CTA covers
+constexpr int kBucketShift = 23;  // 2^23 cells (32 MB of z_re) per bucket by default
 
 // ctrl: exact total mass (2 x u64) at 0, tile ticket (u32) at 16, scan
 // fixed-point shift (int) at 32, scan total (u64) at 40; zeroed per call
@@ -37,9 +31,6 @@ struct AssignWork {
   uint32_t* bcell;  // per scan tile, (cell, z) pairs grouped by bucket
   float* bz;
   uint16_t* btab;   // [tiles][nbuckets + 1] tile-local bucket starts
-  uint32_t* wcell;  // the pairs regrouped by window: window w's at [w 2^14, (w+1) 2^14)
-  float* wz;
-  uint32_t* fill;   // [kWinPerBucket][nbuckets] pairs placed per window (zeroed per call)
   int num_sms;
 };
 
@@ -102,32 +93,22 @@ struct ThreshArgs {
   float* lin;
 };
 
-// Arguments of the two-level scatter back to cell order: the scan's bucket
-// runs regrouped by window (k_window_split), then each window written whole
-// (k_window_write).
+// Arguments of the scatter back to cell order.
 struct ScatterArgs {
   const uint32_t* bcell;
   const float* bz;
   const uint16_t* btab;
   int nbuckets;
-  int64_t tiles;     // scan tiles
-  int chunk_tiles;   // scan tiles per window-split CTA: min(nbuckets, kSplitTiles)
-  int nchunks;       // window-split CTAs per bucket
-  uint32_t* fill;    // [kWinPerBucket][nbuckets] pairs placed per window
-  uint32_t* wcell;
-  float* wz;
-  int64_t n;
-  int64_t nwin;      // windows (window-write CTAs)
+  int64_t tiles;   // scan tiles
+  int groups;      // scatter CTAs per bucket
   float* zre;
-  unsigned int* status;
 };
 
 // Several matchings run together: one thresholds launch (a CTA per item),
 // one scan launch per weighting form (0: mass, 1: linear; items of each form
-// contiguous, scan[f] and scan_prefix[f] with Mg[f] entries), one window-split
-// and one window-write launch.  All pointers are device arrays; the
-// matchings' control words, scan look-back states and window fill counts must
-// be zeroed beforehand.
+// contiguous, scan[f] and scan_prefix[f] with Mg[f] entries), one scatter
+// launch.  All pointers are device arrays; the matchings' control words and
+// scan look-back states must be zeroed beforehand.
 struct AssignMulti {
   int M;
   const ThreshArgs* thresh;
@@ -136,10 +117,8 @@ struct AssignMulti {
   int Mg[2];
   uint32_t scan_tiles[2];
   const ScatterArgs* scatter;
-  const uint32_t* split_prefix;   // window-split CTAs per item
-  uint32_t split_blocks;
-  const uint32_t* write_prefix;   // window-write CTAs per item
-  uint32_t write_blocks;
+  const uint32_t* scatter_prefix;
+  uint32_t scatter_blocks;
 };
 
 // Host: the arguments of one matching as assign_impl runs it (the masses in
@@ -151,8 +130,6 @@ void assign_args(const AssignWork& w, const uint32_t* order, const float* mass, 
 cudaError_t assign_multi(const AssignMulti& m, cudaStream_t s);
 
 void bucket_plan(int64_t n, int* nbuckets, int* shift);
-// Window fill counters one matching of n cells needs (AssignWork::fill).
-size_t window_fill_words(int64_t n);
 
 // Tomographic matching: fill z with NaN (neutral); give cells with a redshift
 // intensity +inf (rank first); take the interval's redshift for neutral cells

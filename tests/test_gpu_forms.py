@@ -230,8 +230,8 @@ def test_batch_is_one_launch_per_stage_with_mixed_tunings_and_weightings(B, monk
         assert ctx.sync_status() == 0
         batch = B.Batch([ctx], items)
         # 5 transform passes x 3 sizes, (histogram + offsets + 4 digit passes)
-        # x 2 widths, thresholds + 2 scan forms + window split + window write
-        assert batch.kernel_nodes() == 5 * 3 + 6 * 2 + 5
+        # x 2 widths, thresholds + 2 scan forms + scatter
+        assert batch.kernel_nodes() == 5 * 3 + 6 * 2 + 4
         batch.launch()
         torch.cuda.synchronize()
         assert ctx.sync_status() == 0
