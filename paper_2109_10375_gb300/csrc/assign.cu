@@ -654,21 +654,26 @@ __global__ void __launch_bounds__(kScanThreads, 2)
 // stores, so the dependent load -> store chains overlap.  A
 // bucket's cells span a bounded region of z_re, so the permuted writes of
 // the CTAs working on it stay close together.
+// wpt (1, 2, 4 or 8) warps share one tile's run, each taking a contiguous
+// part: with few buckets (small grids) a run holds most of a tile's 8192
+// pairs, and one warp copying it alone would wait through dozens of rounds.
 __device__ __forceinline__ void scatter_back_body(const uint32_t* __restrict__ bcell, const float* __restrict__ bz,
                                                   const uint16_t* __restrict__ btab, int nbuckets, int64_t tiles,
-                                                  int groups, float* __restrict__ zre, uint32_t blk) {
-  constexpr int TPW = kBackTilesPerCta / 8;  // tiles per warp
+                                                  int groups, int wpt, float* __restrict__ zre, uint32_t blk) {
+  constexpr int TPW = 1;  // tiles per warp
   const int b = blk / groups;
   const int64_t g = blk - (int64_t)b * groups;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const unsigned long long stream_pol = l2_evict_first(), keep_pol = l2_evict_last();
-  const int64_t t0 = g * kBackTilesPerCta + warp * TPW;
-  // lane k < TPW fetches tile t0 + k's run bounds
+  const int tiles_per_cta = kBackTilesPerCta / wpt, part = warp % wpt;
+  const int64_t t0 = g * tiles_per_cta + warp / wpt;
+  // lane 0 fetches the tile's run bounds and keeps this warp's part of it
   int s_l = 0, e_l = 0;
   if (lane < TPW && t0 + lane < tiles) {
     const uint16_t* row = btab + (t0 + lane) * (nbuckets + 1);
-    s_l = row[b];
-    e_l = row[b + 1];
+    const int s = row[b], e = row[b + 1];
+    s_l = s + ((e - s) * part) / wpt;
+    e_l = s + ((e - s) * (part + 1)) / wpt;
   }
   // rounds of 4 x 32 pairs per run: the loads of all the warp's runs, then the stores
   constexpr int G = 4;
@@ -707,8 +712,8 @@ __device__ __forceinline__ void scatter_back_body(const uint32_t* __restrict__ b
 __global__ void __launch_bounds__(256) k_scatter_back(const uint32_t* __restrict__ bcell,
                                                       const float* __restrict__ bz,
                                                       const uint16_t* __restrict__ btab, int nbuckets,
-                                                      int64_t tiles, int groups, float* __restrict__ zre) {
-  scatter_back_body(bcell, bz, btab, nbuckets, tiles, groups, zre, blockIdx.x);
+                                                      int64_t tiles, int groups, int wpt, float* __restrict__ zre) {
+  scatter_back_body(bcell, bz, btab, nbuckets, tiles, groups, wpt, zre, blockIdx.x);
 }
 
 // Several scatters at once: CTA b works on item find_item(prefix, M, b).
@@ -716,7 +721,7 @@ __global__ void __launch_bounds__(256) k_scatter_back_multi(const ScatterArgs* _
                                                             const uint32_t* __restrict__ prefix, int M) {
   const int it = find_item(prefix, M, blockIdx.x);
   const ScatterArgs& a = args[it];
-  scatter_back_body(a.bcell, a.bz, a.btab, a.nbuckets, a.tiles, a.groups, a.zre, blockIdx.x - prefix[it]);
+  scatter_back_body(a.bcell, a.bz, a.btab, a.nbuckets, a.tiles, a.groups, a.wpt, a.zre, blockIdx.x - prefix[it]);
 }
 
 // ---------------------------------------------------------------------------
@@ -844,7 +849,12 @@ void assign_args(const AssignWork& w, const uint32_t* order, const float* mass, 
   x.btab = w.btab;
   x.nbuckets = a.nbuckets;
   x.tiles = tiles;
-  x.groups = (int)((tiles + kBackTilesPerCta - 1) / kBackTilesPerCta);
+  // warps per tile run: about 128 pairs each on average (a tile's 8192 pairs
+  // spread over the buckets)
+  x.wpt = 1;
+  while (x.wpt < 8 && kScanTile / a.nbuckets >= 256 * x.wpt) x.wpt *= 2;
+  const int tiles_per_cta = kBackTilesPerCta / x.wpt;
+  x.groups = (int)((tiles + tiles_per_cta - 1) / tiles_per_cta);
   x.zre = zre;
 }
 
@@ -891,7 +901,7 @@ cudaError_t assign_impl(const AssignWork& w, const uint32_t* order, const float*
   prof_end(prof, PK_SCAN_ASSIGN, s);
   prof_begin(prof, PK_SCATTER_BACK, s);
   k_scatter_back<<<(unsigned)(xa.groups * xa.nbuckets), 256, 0, s>>>(xa.bcell, xa.bz, xa.btab, xa.nbuckets, xa.tiles,
-                                                                     xa.groups, xa.zre);
+                                                                     xa.groups, xa.wpt, xa.zre);
   prof_end(prof, PK_SCATTER_BACK, s);
   return cudaGetLastError();
 }

@@ -101,6 +101,7 @@ struct ScatterArgs {
   int nbuckets;
   int64_t tiles;   // scan tiles
   int groups;      // scatter CTAs per bucket
+  int wpt;         // warps sharing one tile's run (1, 2, 4, 8); a CTA covers 8 / wpt tiles
   float* zre;
 };
 
