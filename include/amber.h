@@ -191,6 +191,19 @@ int amber_source_field(amber_ctx *ctx, const float *d_delta, int64_t ncells, dou
  * n^3 floats out with the intensity.  p->precision must be 32 here. */
 int amber_solve(amber_ctx *ctx, const float *d_src, const float *d_mass, const amber_params_t *p,
                 float *d_zre, float *d_J_opt, void *stream);
+/* amber_solve from and to HOST memory: h_src and h_mass (n^3 floats each,
+ * host) are copied to the device, solved as by amber_solve, and z_re (n^3
+ * floats) copied back to h_zre, all in order on `stream`; the call returns
+ * once the work is enqueued, and h_zre holds the result after the stream has
+ * reached it (synchronise the stream or an event).  Host buffers allocated
+ * pinned (cudaMallocHost, cudaHostRegister) copy at the link's full rate and
+ * asynchronously; pageable ones are copied through the driver's staging.
+ * No device memory beyond the context's workspace: the copies live in
+ * workspace that is free while they are needed.  To overlap one step's
+ * copies with another's solve, alternate two contexts on two streams. */
+int amber_solve_host(amber_ctx *ctx, const float *h_src, const float *h_mass, const amber_params_t *p,
+                     float *h_zre, void *stream);
+
 /* amber_solve that also hands back what a parameter study reuses: the rank
  * order (d_order_out, n^3 uint32) and the masses in rank order
  * (d_mass_rank_out, n^3 floats), both caller-owned device buffers.  A later

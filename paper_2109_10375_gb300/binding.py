@@ -34,7 +34,7 @@ EXPORTED = [
     "amber_lpt_displacement", "amber_mesh_density", "amber_esf_fcoll", "amber_sigma2_tophat",
     "amber_solve_tomographic", "amber_autotune", "amber_set_tuning", "amber_get_tuning",
     "amber_rank_noalloc", "amber_power_derived", "amber_spectrum_bytes", "amber_source_spectrum",
-    "amber_solve_spectrum", "amber_batch_kernel_nodes",
+    "amber_solve_spectrum", "amber_batch_kernel_nodes", "amber_solve_host",
 ]
 
 
@@ -110,6 +110,7 @@ def _load():
         "amber_batch_launch": (i32, [vp, vp]),
         "amber_batch_destroy": (i32, [vp]),
         "amber_batch_kernel_nodes": (i32, [vp, C.POINTER(i32)]),
+        "amber_solve_host": (i32, [vp, vp, vp, C.POINTER(amber_params_t), vp, vp]),
         "amber_delta_z": (i32, [vp, vp, i64, vp, vp, vp]),
         "amber_epsilon_z_pdf": (i32, [vp, vp, vp, i64, dbl, dbl, i32, vp, vp, vp]),
         "amber_power_bins": (i32, [i32, C.POINTER(i32)]),
@@ -334,6 +335,14 @@ class Context:
             out = torch.empty(S.shape, dtype=torch.float32, device=S.device)
         fn = lib.amber_solve_f64 if f64 else lib.amber_solve
         _check(fn(self._h, _ptr(S), _ptr(mass), C.byref(p), _ptr(out), _ptr(J_out), _stream(stream)), "amber_solve")
+        return out
+
+    def solve_host(self, S, mass, box: float, l_mfp: float, h: amber_history_t, out, stream=None):
+        """The whole path from host tensors (S, mass; pinned for full speed) into
+        the host tensor out, enqueued on the stream (synchronise before reading out)."""
+        p = params(S.shape[0], box, l_mfp, h)
+        _check(lib.amber_solve_host(self._h, _ptr(S), _ptr(mass), C.byref(p), _ptr(out), _stream(stream)),
+               "amber_solve_host")
         return out
 
     def solve_ex(self, S, mass, box: float, l_mfp: float, h: amber_history_t, out, order_out, mass_rank_out,

@@ -797,6 +797,32 @@ int amber_solve(amber_ctx* c, const float* d_src, const float* d_mass, const amb
   return cuda_status(solve_f32_enqueue(c, d_src, d_mass, p, hc, d_zre, d_J_opt, nullptr, nullptr, s));
 }
 
+int amber_solve_host(amber_ctx* c, const float* h_src, const float* h_mass, const amber_params_t* p, float* h_zre,
+                     void* stream) {
+  HistoryCoeffs hc;
+  int st = solve_args(c, h_src, h_mass, p, h_zre, 32, c ? c->plan.n32 : 0, &hc);
+  if (st) return st;
+  std::lock_guard<std::mutex> lk(c->mu);
+  DeviceGuard g(c->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  c->last_stream = s;
+  const size_t bytes = (size_t)p->n * p->n * p->n * sizeof(float);
+  // device copies in workspace that is free when they are live: the source in
+  // the second index array (read by the forward x pass, first written by the
+  // second digit pass), the masses in the second mass array (read by the
+  // first digit pass, first written by the second), z_re in the transform
+  // buffer (free once the inverse x pass has run)
+  float* dS = reinterpret_cast<float*>(c->sortw.idxB);
+  float* dM = c->sortw.massB;
+  float* dZ = reinterpret_cast<float*>(c->ws + c->plan.off_spec);
+  cudaError_t e = cudaMemcpyAsync(dS, h_src, bytes, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dM, h_mass, bytes, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = solve_f32_enqueue(c, dS, dM, p, hc, dZ, nullptr, nullptr, nullptr, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h_zre, dZ, bytes, cudaMemcpyDeviceToHost, s);
+  if (e != cudaSuccess) cudaGetLastError();
+  return cuda_status(e);
+}
+
 int amber_autotune(amber_ctx* c, const float* d_src, const float* d_mass, int n, double box, double l_mfp,
                    amber_tuning_t* out, void* stream) {
   const int st = rf_args_ok(c, d_src, n, box, l_mfp, d_src, c ? c->plan.n32 : 0);

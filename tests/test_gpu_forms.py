@@ -240,3 +240,21 @@ def test_batch_is_one_launch_per_stage_with_mixed_tunings_and_weightings(B, monk
         batch.close()
     finally:
         ctx.close()
+
+
+@pytest.mark.parametrize("n,pinned", [(32, False), (64, True), (128, True)])
+def test_solve_from_host_buffers_equals_the_device_solve(B, n, pinned):
+    # amber_solve_host: host inputs copied in, solved, z_re copied out on the
+    # stream; the result is the device solve's, bit for bit, call after call
+    box, l = 100.0 * n / 128, 4.0
+    S, m = synth.realisation(n, box, 7)
+    h = B.history(7.8, 3.5, 2.5)
+    with B.Context(n ** 3) as ctx:
+        ref = ctx.solve(S.cuda(), m.cuda(), box, l, h).cpu()
+        Sh, mh = (S.pin_memory(), m.pin_memory()) if pinned else (S.contiguous(), m.contiguous())
+        for rep in range(2):
+            zh = torch.full(S.shape, -1.0, pin_memory=pinned)
+            ctx.solve_host(Sh, mh, box, l, h, zh)
+            torch.cuda.synchronize()
+            assert ctx.sync_status() == 0
+            assert torch.equal(zh, ref)
