@@ -356,9 +356,27 @@ __device__ __forceinline__ void scan_assign_body(const ScanArgs& a) {
     lbw = (lbt - lane >= 0) ? ld_relaxed_u64(a.state + lbt - lane) : kScanInc;
   }
   uint32_t slot[IT];
+  if (a.nbuckets <= 16) {
+    // few buckets (small grids: one below 2^23 cells): most lanes share one,
+    // and one shared add per lane would serialise on its counter; the lanes
+    // of a bucket take their slots with one add for the warp
+    const unsigned lt = (1u << lane) - 1u;
 #pragma unroll
-  for (int i = 0; i < IT; ++i)
-    slot[i] = (tid * IT + i < cnt) ? atomicAdd(&scnt[cell[i] >> a.bucket_shift], 1u) : 0xffffffffu;
+    for (int i = 0; i < IT; ++i) {
+      const bool ok = tid * IT + i < cnt;
+      const unsigned bk = ok ? cell[i] >> a.bucket_shift : 0xffffu;
+      const unsigned peers = __match_any_sync(0xffffffffu, bk);
+      const int leader = __ffs(peers) - 1;
+      uint32_t base = 0;
+      if (ok && lane == leader) base = atomicAdd(&scnt[bk], (uint32_t)__popc(peers));
+      base = __shfl_sync(0xffffffffu, base, leader);
+      slot[i] = ok ? base + (uint32_t)__popc(peers & lt) : 0xffffffffu;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < IT; ++i)
+      slot[i] = (tid * IT + i < cnt) ? atomicAdd(&scnt[cell[i] >> a.bucket_shift], 1u) : 0xffffffffu;
+  }
   __syncthreads();
 
   if (warp == 0) {
