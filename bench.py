@@ -562,15 +562,17 @@ def run_amber(args):
 
     # --- end to end through the C ABI with host buffers: amber_solve_host
     # copies the step's inputs in from pinned host memory, solves and copies
-    # z_re out, all on its stream.  Two contexts alternate on two streams, so
-    # one step's copies overlap the neighbouring step's solve.
+    # z_re out, all on its stream.  Each call runs its copies and its solve in
+    # order, so the contexts take turns on their own streams: while one
+    # solves, the others copy.
     del S, m
     torch.cuda.empty_cache()
-    ctx2 = B.Context(C, device=local)
+    ctxs2 = [ctx] + [B.Context(C, device=local) for _ in range(args.e2e_contexts - 1)]
     if args.fuse_histogram is not None:
-        ctx2.set_tuning(n, fuse_histogram=args.fuse_histogram)
-    ctxs2 = [ctx, ctx2]
-    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+        for cx in ctxs2[1:]:
+            cx.set_tuning(n, fuse_histogram=args.fuse_histogram)
+    streams = [torch.cuda.Stream() for _ in ctxs2]
+    z_h = z_h + [torch.empty(z.shape, dtype=torch.float32, pin_memory=True) for _ in range(len(ctxs2) - len(z_h))]
     e_steps = max(2, args.steps)  # the same K as the device-timed steps
 
     def pipeline(steps):
@@ -581,7 +583,7 @@ def run_amber(args):
         for st_ in streams:
             st_.wait_event(f0)
         for i in range(steps):
-            b = i & 1
+            b = i % len(ctxs2)
             ctxs2[b].solve_host(S_h, m_h, box, L_MFP, h, z_h[b], stream=streams[b])
         for st_ in streams:
             ev = torch.cuda.Event()
@@ -591,7 +593,7 @@ def run_amber(args):
         barrier()
         return f0.elapsed_time(f1) / steps
 
-    pipeline(2)  # warm-up: the second context's first use
+    pipeline(len(ctxs2))  # warm-up: every context's first use
     # three timed trials; the median one is reported (the host side of the
     # copies is shared with the rest of the machine)
     trials = [pipeline(e_steps) for _ in range(3)]
@@ -616,7 +618,8 @@ def run_amber(args):
         st = cx.sync_status()
         if st != 0:
             raise RuntimeError(f"device status after end-to-end steps: {B.status_string(st)}")
-    ctx2.close()
+    for cx in ctxs2[1:]:
+        cx.close()
     # the autotuner needs device copies of the workload's fields
     S_d = [torch.empty(z.shape, device="cuda")]
     m_d = [torch.empty(z.shape, device="cuda")]
@@ -681,8 +684,8 @@ def run_amber(args):
                 "e2e": {"value": whole_job_rate(C, ws, e2e_ms), "unit": "cells/s", "h2d_bytes_per_step": 8 * C,
                         "d2h_bytes_per_step": 4 * C, "ms_per_step": e2e_ms, "steps": e_steps,
                         "call": "amber_solve_host (pinned host buffers in and out, copies on the call's stream)",
-                        "overlap": "two contexts alternate on two streams: one step's copies overlap the "
-                                   "neighbouring step's solve",
+                        "overlap": f"{len(ctxs2)} contexts take turns on their own streams: while one solves, "
+                                   "the others copy",
                         "h2d_GBps_alone": h2d_gbps, "d2h_GBps_alone": d2h_gbps,
                         "trials_ms": trials, "reported": "median of 3 timed trials"},
                 "gpu_launches": int(round(launches_per_step * args.steps)),
@@ -852,6 +855,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fuse-histogram", type=int, choices=[0, 1], default=None,
                     help="override the size's choice of digit counts in the inverse x pass (8-bit digits)")
+    ap.add_argument("--e2e-contexts", type=int, default=3,
+                    help="contexts (each with its own stream) the end-to-end steps rotate over")
     ap.add_argument("--no-accuracy", action="store_true",
                     help="skip the oracle comparison of the workload's J and z_re (minutes of host time)")
     ap.add_argument("--no-extras", action="store_true", help="skip the batched and serving measurements")

@@ -200,7 +200,11 @@ int amber_solve(amber_ctx *ctx, const float *d_src, const float *d_mass, const a
  * asynchronously; pageable ones are copied through the driver's staging.
  * No device memory beyond the context's workspace: the copies live in
  * workspace that is free while they are needed.  To overlap one step's
- * copies with another's solve, alternate two contexts on two streams. */
+ * copies with another's solve, alternate two or more contexts, each on its
+ * own stream: host-buffer solves on one device take turns in call order (a
+ * call's solve waits for the previous call's solve, on whichever context, but
+ * its copies in do not), so the copies of one call run while another solves
+ * and no two of these solves share the GPU. */
 int amber_solve_host(amber_ctx *ctx, const float *h_src, const float *h_mass, const amber_params_t *p,
                      float *h_zre, void *stream);
 

@@ -243,8 +243,17 @@ struct amber_ctx {
   FftProfile prof;
   cudaStream_t last_stream = nullptr;
   amber_tuning_t tune[11] = {};  // per log2 n: FFT variant, digit width and peers of the FP32 solve path
+  cudaEvent_t host_solve_done = nullptr;  // recorded after each amber_solve_host's solve
   std::mutex mu;
 };
+
+namespace {
+// Host-buffer solves on one device take turns in call order: each waits for
+// the previous one's solve (not its copies), so contexts used in turn overlap
+// one call's copies with another's solve without two solves sharing the GPU.
+std::mutex g_host_solve_mu;
+amber_ctx* g_last_host_solve[64] = {};
+}  // namespace
 
 namespace {
 
@@ -374,6 +383,13 @@ int amber_create(amber_ctx** out, int device, int64_t max_cells) {
     delete c;
     return AMBER_ERR_CUDA;
   }
+  if (cudaEventCreateWithFlags(&c->host_solve_done, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFreeHost(c->h_status);
+    cudaFree(c->ws);
+    delete c;
+    return AMBER_ERR_CUDA;
+  }
   const Plan& p = c->plan;
   c->status = reinterpret_cast<unsigned int*>(c->ws + p.off_status);
   cudaMemset(c->ws + p.off_status, 0, 256);
@@ -425,8 +441,13 @@ int amber_create(amber_ctx** out, int device, int64_t max_cells) {
 int amber_destroy(amber_ctx* c) {
   if (!c) return AMBER_ERR_INVALID_ARG;
   {
+    std::lock_guard<std::mutex> lk(g_host_solve_mu);
+    if (c->device >= 0 && c->device < 64 && g_last_host_solve[c->device] == c) g_last_host_solve[c->device] = nullptr;
+  }
+  {
     DeviceGuard g(c->device);
     cudaDeviceSynchronize();
+    if (c->host_solve_done) cudaEventDestroy(c->host_solve_done);
     for (auto e : c->prof.pool) cudaEventDestroy(e);
     if (c->h_status) cudaFreeHost(c->h_status);
     if (c->ws) cudaFree(c->ws);
@@ -817,7 +838,16 @@ int amber_solve_host(amber_ctx* c, const float* h_src, const float* h_mass, cons
   float* dZ = reinterpret_cast<float*>(c->ws + c->plan.off_spec);
   cudaError_t e = cudaMemcpyAsync(dS, h_src, bytes, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(dM, h_mass, bytes, cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) e = solve_f32_enqueue(c, dS, dM, p, hc, dZ, nullptr, nullptr, nullptr, s);
+  {
+    // the solve waits for the previous host-buffer solve on this device
+    // (enqueued after this call's copies in, which need not wait)
+    std::lock_guard<std::mutex> glk(g_host_solve_mu);
+    amber_ctx*& last = g_last_host_solve[c->device < 64 ? c->device : 63];
+    if (e == cudaSuccess && last && last != c) e = cudaStreamWaitEvent(s, last->host_solve_done, 0);
+    if (e == cudaSuccess) e = solve_f32_enqueue(c, dS, dM, p, hc, dZ, nullptr, nullptr, nullptr, s);
+    if (e == cudaSuccess) e = cudaEventRecord(c->host_solve_done, s);
+    if (e == cudaSuccess) last = c;
+  }
   if (e == cudaSuccess) e = cudaMemcpyAsync(h_zre, dZ, bytes, cudaMemcpyDeviceToHost, s);
   if (e != cudaSuccess) cudaGetLastError();
   return cuda_status(e);

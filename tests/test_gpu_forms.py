@@ -258,3 +258,29 @@ def test_solve_from_host_buffers_equals_the_device_solve(B, n, pinned):
             torch.cuda.synchronize()
             assert ctx.sync_status() == 0
             assert torch.equal(zh, ref)
+
+
+def test_host_buffer_solves_on_contexts_in_turn(B):
+    # contexts used in turn on their own streams: each call's solve waits for
+    # the previous call's (copies in do not), and every result is the device
+    # solve's
+    n, box, l = 64, 50.0, 4.0
+    S, m = synth.realisation(n, box, 8)
+    h = B.history(8.0, 4.0, 3.0)
+    ctxs = [B.Context(n ** 3) for _ in range(3)]
+    try:
+        ref = ctxs[0].solve(S.cuda(), m.cuda(), box, l, h).cpu()
+        Sh, mh = S.pin_memory(), m.pin_memory()
+        streams = [torch.cuda.Stream() for _ in ctxs]
+        outs = [torch.full(S.shape, -1.0, pin_memory=True) for _ in range(7)]
+        for i, zh in enumerate(outs):
+            k = i % len(ctxs)
+            ctxs[k].solve_host(Sh, mh, box, l, h, zh, stream=streams[k])
+        torch.cuda.synchronize()
+        for c in ctxs:
+            assert c.sync_status() == 0
+        for zh in outs:
+            assert torch.equal(zh, ref)
+    finally:
+        for c in ctxs:
+            c.close()
