@@ -302,12 +302,13 @@ __device__ __forceinline__ void sort_pass_body(const PassArgs& a) {
         peers = __match_any_sync(0xffffffffu, ok ? d : 0x10000u);
       } else {
         // the same set from one ballot per digit bit: keep the lanes whose bit
-        // agrees (bit - 1 is all ones exactly when the bit is clear)
+        // agrees.  m is the bit sign-extended (all ones when set), so the lanes
+        // that agree with this one are ~(ballot ^ m)
         peers = FULL ? 0xffffffffu : __ballot_sync(0xffffffffu, ok);
 #pragma unroll
         for (int b = 0; b < RB; ++b) {
-          const unsigned bit = (d >> b) & 1u;
-          peers &= __ballot_sync(0xffffffffu, bit) ^ (bit - 1u);
+          const unsigned m = (unsigned)((int)(d << (31 - b)) >> 31);
+          peers &= ~(__ballot_sync(0xffffffffu, m != 0u) ^ m);
         }
       }
       uint32_t base = 0;
