@@ -702,7 +702,8 @@ def run_amber(args):
                                              "path": (path_design / (ms_max / 1e3) / 1e9) / peak},
                              "sort_passes": passes},
                 "kernels": kernels,
-                "tuning": {k: tuning[k] for k in ("fft_variant", "sort_digit_bits", "sort_match", "fuse_histogram")},
+                "tuning": {k: tuning[k] for k in ("fft_variant", "sort_digit_bits", "sort_match", "fuse_histogram",
+                                                 "zpass_tma")},
                 "clocks": clocks,
                 "cpu_baseline": cpu}
         if accuracy is not None:

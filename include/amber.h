@@ -265,14 +265,21 @@ int amber_solve_spectrum(amber_ctx *ctx, const void *d_spec, const float *d_mass
  *                    the intensities' digits as it writes them and the sort
  *                    runs on the raw 32-bit keys (always four passes) with no
  *                    histogram pass of its own; 0: a histogram pass of
- *                    key - min(key) (a narrow key range may need fewer passes).
+ *                    key - min(key) (a narrow key range may need fewer passes);
+ *   zpass_tma        1: the fused z pass (n >= 64) is a persistent kernel whose
+ *                    tiles arrive in shared memory by TMA (cp.async.bulk.tensor
+ *                    under a 3D tensor map of the half spectrum), the next
+ *                    tile's copy overlapping the current tile's stores;
+ *                    0: each CTA loads its tile with ordinary loads.  The
+ *                    arithmetic is the same, so are the results, bit for bit.
  * Every choice gives the same ranking (the stable descending order is
  * unique); the FFT variants differ only in FP32 rounding.  Defaults: 0, 8
- * for n >= 512 and 9 below, 0 (the tuner's picks on a synthetic field of the
- * paper's kind).
+ * for n >= 512 and 9 below, 0, 0 but 1 for n = 512 (the tuner's picks on a
+ * synthetic field of the paper's kind).
  * tuned: 1 once amber_autotune measured this size; fft_ms[v] and sort_ms[k]
  * hold the median times it measured (k: (9, ballot), (9, match), (8,
- * ballot), (8, match); 0 where not applicable). */
+ * ballot), (8, match); 0 where not applicable), fft_tma_ms the radiation
+ * field's with the chosen variant and the TMA z pass (0 below n = 64). */
 typedef struct {
   int n;
   int fft_variant;
@@ -282,6 +289,8 @@ typedef struct {
   double fft_ms[2];
   double sort_ms[4];
   int fuse_histogram;
+  int zpass_tma;
+  double fft_tma_ms;
 } amber_tuning_t;
 
 /* Measures every choice on the caller's own field (d_src, d_mass: n^3 floats

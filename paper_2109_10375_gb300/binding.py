@@ -58,12 +58,13 @@ class amber_params_t(C.Structure):
 class amber_tuning_t(C.Structure):
     _fields_ = [("n", C.c_int), ("fft_variant", C.c_int), ("sort_digit_bits", C.c_int), ("sort_match", C.c_int),
                 ("tuned", C.c_int), ("fft_ms", C.c_double * 2), ("sort_ms", C.c_double * 4),
-                ("fuse_histogram", C.c_int)]
+                ("fuse_histogram", C.c_int), ("zpass_tma", C.c_int), ("fft_tma_ms", C.c_double)]
 
     def as_dict(self) -> dict:
         return {"n": self.n, "fft_variant": self.fft_variant, "sort_digit_bits": self.sort_digit_bits,
                 "sort_match": self.sort_match, "tuned": self.tuned, "fft_ms": list(self.fft_ms),
-                "sort_ms": list(self.sort_ms), "fuse_histogram": self.fuse_histogram}
+                "sort_ms": list(self.sort_ms), "fuse_histogram": self.fuse_histogram,
+                "zpass_tma": self.zpass_tma, "fft_tma_ms": self.fft_tma_ms}
 
 
 class amber_batch_item(C.Structure):
@@ -411,13 +412,15 @@ class Context:
                "amber_autotune")
         return t.as_dict()
 
-    def set_tuning(self, n: int, fft_variant=None, sort_digit_bits=None, sort_match=None, fuse_histogram=None):
+    def set_tuning(self, n: int, fft_variant=None, sort_digit_bits=None, sort_match=None, fuse_histogram=None,
+                   zpass_tma=None):
         """Set the choices for size n; a choice left as None keeps its current value."""
         cur = self.get_tuning(n)
         t = amber_tuning_t(n, cur["fft_variant"] if fft_variant is None else fft_variant,
                            cur["sort_digit_bits"] if sort_digit_bits is None else sort_digit_bits,
                            cur["sort_match"] if sort_match is None else sort_match, 0)
         t.fuse_histogram = cur["fuse_histogram"] if fuse_histogram is None else fuse_histogram
+        t.zpass_tma = cur["zpass_tma"] if zpass_tma is None else zpass_tma
         _check(lib.amber_set_tuning(self._h, C.byref(t)), "amber_set_tuning")
 
     def get_tuning(self, n: int) -> dict:

@@ -23,9 +23,11 @@ namespace amber {
 // spec_in: if not null, the x- and y-transformed source (source_spectrum_f32's
 // output), read by the z pass instead of transforming src.
 // hist8: the inverse x pass also counts the raw keys' 8-bit digits into krange.
+// tma: the z pass stages its tiles with the tensor-memory accelerator
+// (k_fft_zconv_tma; two-stage sizes n >= 64, same results bit for bit).
 cudaError_t radiation_field_f32(int n, const float* src, float* J, void* H, const void* tw, double box, double l_mfp,
                                unsigned int* status, cudaStream_t s, FftProfile* prof, SortCtrl* krange,
-                               int variant, const void* spec_in = nullptr, bool hist8 = false);
+                               int variant, const void* spec_in = nullptr, bool hist8 = false, bool tma = false);
 cudaError_t source_spectrum_f32(int n, const float* src, void* H, const void* tw, cudaStream_t s, FftProfile* prof,
                                int variant);
 cudaError_t radiation_field_multi_f32(int n, int variant, const float* const* srcs, int M, float* J, void* H,
@@ -366,7 +368,8 @@ int amber_create(amber_ctx** out, int device, int64_t max_cells) {
   // 32.1 ms per ranking at 1024^3), 9-bit below, default FFT tiles, ballots
   if (c)
     for (int l = 0; l < 11; ++l)
-      c->tune[l] = amber_tuning_t{1 << l, 0, l >= 9 ? 8 : 9, 0, 0, {0.0, 0.0}, {0.0, 0.0, 0.0, 0.0}, 0};
+      c->tune[l] = amber_tuning_t{1 << l, 0, l >= 9 ? 8 : 9, 0, 0, {0.0, 0.0}, {0.0, 0.0, 0.0, 0.0}, 0, l == 9 ? 1 : 0,
+                                  0.0};
   if (!c) return AMBER_ERR_OOM;
   c->device = device;
   c->max_cells = max_cells;
@@ -478,7 +481,8 @@ int amber_radiation_field(amber_ctx* c, const float* d_src, int n, double box, d
   const Plan& p = c->plan;
   const int l = ilog2i(n);
   return cuda_status(radiation_field_f32(n, d_src, d_J, c->ws + p.off_spec, c->ws + p.off_tw32 + p.tw32_off[l], box,
-                                         l_mfp, c->status, s, &c->prof, nullptr, c->tune[l].fft_variant));
+                                         l_mfp, c->status, s, &c->prof, nullptr, c->tune[l].fft_variant, nullptr,
+                                         false, c->tune[l].zpass_tma != 0));
 }
 
 int amber_radiation_field_f64(amber_ctx* c, const double* d_src, int n, double box, double l_mfp, double* d_J,
@@ -712,7 +716,8 @@ static cudaError_t solve_f32_enqueue(amber_ctx* c, const float* d_src, const flo
   cudaError_t e = sort_ctrl_reset(c->sortw.ctrl, s);
   if (e == cudaSuccess)
     e = radiation_field_f32(n, d_src, J, c->ws + pl.off_spec, c->ws + pl.off_tw32 + pl.tw32_off[ilog2i(n)], p->box,
-                           p->l_mfp, c->status, s, &c->prof, c->sortw.ctrl, tu.fft_variant, spec_in, fuse);
+                           p->l_mfp, c->status, s, &c->prof, c->sortw.ctrl, tu.fft_variant, spec_in, fuse,
+                           tu.zpass_tma != 0);
   // the first sort pass sums each tile's masses; the thresholds kernel adds them
   unsigned long long* tile_mass = reinterpret_cast<unsigned long long*>(c->ws + pl.off_tilemass);
   if (e == cudaSuccess)
@@ -774,9 +779,17 @@ static int autotune_locked(amber_ctx* c, const float* d_src, const float* d_mass
     timed([&] { return radiation_field_f32(n, d_src, J, c->ws + pl.off_spec, tw, box, l_mfp, c->status, s, nullptr,
                                            nullptr, v); }, &t.fft_ms[v]);
   t.fft_variant = (nv == 2 && t.fft_ms[1] < t.fft_ms[0]) ? 1 : 0;
+  // the chosen tiles once more with the TMA-staged z pass
+  t.fft_tma_ms = 0.0;
+  t.zpass_tma = 0;
+  if (n >= 64 && e == cudaSuccess) {
+    timed([&] { return radiation_field_f32(n, d_src, J, c->ws + pl.off_spec, tw, box, l_mfp, c->status, s, nullptr,
+                                           nullptr, t.fft_variant, nullptr, false, true); }, &t.fft_tma_ms);
+    t.zpass_tma = t.fft_tma_ms < 0.98 * t.fft_ms[t.fft_variant] ? 1 : 0;  // a clear win only
+  }
   if (e == cudaSuccess)
     e = radiation_field_f32(n, d_src, J, c->ws + pl.off_spec, tw, box, l_mfp, c->status, s, nullptr, nullptr,
-                            t.fft_variant);
+                            t.fft_variant, nullptr, false, t.zpass_tma != 0);
   if (e == cudaSuccess) e = cudaMemcpyAsync(Jkeep, J, (size_t)C * sizeof(float), cudaMemcpyDeviceToDevice, s);
   static const int cand[4][2] = {{9, 0}, {9, 1}, {8, 0}, {8, 1}};
   int best = 0;
@@ -868,7 +881,7 @@ int amber_set_tuning(amber_ctx* c, const amber_tuning_t* t) {
   if (!c || !t || !is_pow2_in(t->n, 4, 1024) || t->n > c->plan.n32) return AMBER_ERR_INVALID_ARG;
   if (t->fft_variant < 0 || t->fft_variant > (t->n >= 128 ? 1 : 0)) return AMBER_ERR_INVALID_ARG;
   if ((t->sort_digit_bits != 8 && t->sort_digit_bits != 9) || (t->sort_match != 0 && t->sort_match != 1) ||
-      (t->fuse_histogram != 0 && t->fuse_histogram != 1))
+      (t->fuse_histogram != 0 && t->fuse_histogram != 1) || (t->zpass_tma != 0 && t->zpass_tma != 1))
     return AMBER_ERR_INVALID_ARG;
   std::lock_guard<std::mutex> lk(c->mu);
   c->tune[ilog2i(t->n)] = *t;
@@ -910,7 +923,7 @@ int amber_solve_tomographic(amber_ctx* c, const float* const* d_src_list, int ni
     if (e == cudaSuccess)
       e = radiation_field_f32(n, d_src_list[k], J, c->ws + pl.off_spec, c->ws + pl.off_tw32 + pl.tw32_off[ilog2i(n)],
                               p->box, p->l_mfp, c->status, s, &c->prof, c->sortw.ctrl,
-                              c->tune[ilog2i(n)].fft_variant);
+                              c->tune[ilog2i(n)].fft_variant, nullptr, false, c->tune[ilog2i(n)].zpass_tma != 0);
     if (e == cudaSuccess && k > 0) e = tomo_mask(J, d_zre, C, c->sortw.ctrl, c->num_sms, s);
     if (e == cudaSuccess)
       e = rank_impl<float>(c->sortw, J, C, nullptr, d_mass, nullptr, tile_mass, true, c->status, s, &c->prof,

@@ -17,6 +17,8 @@
 // the same register set, so the kernel multiply happens in registers.
 #pragma once
 
+#include <cuda.h>  // CUtensorMap (the z pass's TMA descriptor)
+
 #include "common.cuh"
 #include "keys.cuh"
 
@@ -88,6 +90,18 @@ __device__ __forceinline__ int sm_count() {
 
 __device__ __forceinline__ int signed_freq(int m, int n) { return m < n / 2 ? m : m - n; }
 
+// K(|k|)/n^3 of one tile's columns kx0 .. kx0 + SB - 1 at ky for |kz| = 0..n/2
+// into Kt (row |kz|, column b).  Evaluated per tile while the tile's loads
+// are in flight: a table over |k|^2 read from L2 was measured slower.
+template <typename T, int N, int SB, int NT>
+__device__ __forceinline__ void tile_kernel(T* Kt, int kx0, int ky, int tid, T kf, T l_mfp, T norm) {
+#pragma unroll 1
+  for (int i = tid; i < (N / 2 + 1) * SB; i += NT) {
+    const int kza = i / SB, kx = kx0 + (i - kza * SB);
+    Kt[i] = kernel_K<T>((T)(kx * kx + ky * ky + kza * kza), l_mfp, kf, norm);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Strided passes (y forward, y inverse, z convolution).  A CTA owns SB
 // consecutive kx columns of one line family; lane mapping is column-fastest
@@ -151,13 +165,8 @@ k_fft_strided(cpx<T>* __restrict__ H, int64_t elem_stride, int64_t outer_stride,
   if constexpr (MODE == PASS_CONV) {
     // K(|k|)/n^3 of this tile's columns for |kz| = 0..N/2, into shared memory
     // after the tile, while the loads are in flight
-    const int ky = signed_freq(outer, N);
-    T* Kt = reinterpret_cast<T*>(sm + L::elems);
-#pragma unroll 1
-    for (int i = tid; i < (N / 2 + 1) * SB; i += NT) {
-      const int kza = i / SB, kx = kx0 + (i - kza * SB);
-      Kt[i] = kernel_K<T>((T)(kx * kx + ky * ky + kza * kza), l_mfp, kf, norm);
-    }
+    tile_kernel<T, N, SB, NT>(reinterpret_cast<T*>(sm + L::elems), kx0, signed_freq(outer, N), tid, kf, l_mfp,
+                              norm);
     if constexpr (R1 == 1) __syncthreads();
   }
 #pragma unroll
@@ -272,6 +281,200 @@ k_fft_strided(cpx<T>* __restrict__ H, int64_t elem_stride, int64_t outer_stride,
     }
   }
 }
+
+// ---------------------------------------------------------------------------
+// z pass with TMA-staged tiles (FP32, two-stage sizes): a persistent CTA
+// walks tiles (outer = ky line, SB columns); each tile -- N rows of SB
+// complex values, one 8*SB-byte segment per row -- arrives in shared memory
+// by cp.async.bulk.tensor (N/ZBOX boxes of SB x 1 x ZBOX elements of a 3D
+// tensor map over H: x = kx, y, z), completion counted by an mbarrier.  The
+// arithmetic is the z pass's (forward stage A from the staged tile, forward
+// stage B, K multiply, inverse stages), so the results equal it bit for bit.
+// The next tile's copy is issued once the current tile's shared-memory reads
+// are done, overlapping its global stores and the other CTA's work.  Every
+// mbarrier wait is bounded: a wait that runs out latches
+// AMBER_ERR_DEVICE_TIMEOUT, waits once more (bounded) for the copy in flight
+// and ends the kernel.
+// ---------------------------------------------------------------------------
+constexpr int kZBox = 256;  // rows per TMA box (a box dimension is at most 256)
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+// true when the phase with this parity has completed; up to `limit` tries
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar, uint32_t parity, unsigned limit) {
+  for (unsigned i = 0; i < limit; ++i) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(mbar), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+// bytes of k_fft_zconv_tma's dynamic shared memory before its mbarrier, and in all
+template <int N, int V>
+constexpr size_t zpass_tma_mbar_offset() {
+  return ((size_t)StridedSmem<float, N, V>::elems * 8 + (size_t)(N / 2 + 1) * FftCfg<N, V>::SB * 4 + 7) & ~(size_t)7;
+}
+template <int N, int V>
+constexpr size_t zpass_tma_smem() { return zpass_tma_mbar_offset<N, V>() + 8; }
+
+template <int N, int V>
+__device__ __forceinline__ void zpass_tma_issue(const CUtensorMap* tmap, uint32_t dst, uint32_t mbar, int kx0,
+                                                int y) {
+  constexpr int SB = FftCfg<N, V>::SB;
+  constexpr int ZB = N < kZBox ? N : kZBox;
+  constexpr uint32_t bytes = (uint32_t)N * SB * 8u;
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
+#pragma unroll
+  for (int k = 0; k < N / ZB; ++k) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+        ::"r"(dst + (uint32_t)(k * ZB * SB * 8)), "l"(reinterpret_cast<unsigned long long>(tmap)), "r"(kx0), "r"(y),
+          "r"(k * ZB), "r"(mbar)
+        : "memory");
+  }
+}
+
+template <int N, int V = 0>
+__global__ void __launch_bounds__(strided_threads<N, V>(), 2)
+k_fft_zconv_tma(const __grid_constant__ CUtensorMap tmap, cpx<float>* __restrict__ H, int ncol, int ntx, int ntiles,
+                const cpx<float>* __restrict__ tw, float kf, float l_mfp, float norm,
+                unsigned int* __restrict__ status) {
+  using T = float;
+  using C = FftCfg<N, V>;
+  using L = StridedSmem<T, N, V>;
+  constexpr int R0 = C::R0, R1 = C::R1, E = C::E, SB = C::SB, NT = strided_threads<N, V>();
+  constexpr int QA = E / R0, QB = E / R1;
+  static_assert(R1 > 1, "two-stage sizes only");
+  const int64_t elem_stride = (int64_t)N * (N / 2 + 2), outer_stride = N / 2 + 2;
+  // dynamic shared memory only (its base is 1024-byte aligned): the staged
+  // tile / exchange area, the K table, the mbarrier
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  cpx<T>* sm = reinterpret_cast<cpx<T>*>(smem_raw);
+  T* Kt = reinterpret_cast<T*>(sm + L::elems);  // K over |kz| = 0..N/2 for the tile's columns
+  const uint32_t buf = smem_u32(sm), mbar = buf + (uint32_t)zpass_tma_mbar_offset<N, V>();
+  const int tid = threadIdx.x;
+  constexpr unsigned kLimit = 1u << 22;
+
+  int tile = blockIdx.x;
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    if (tile < ntiles) zpass_tma_issue<N, V>(&tmap, buf, mbar, (tile % ntx) * SB, tile / ntx);
+  }
+  __syncthreads();
+  uint32_t parity = 0;
+  for (; tile < ntiles; tile += gridDim.x) {
+    {
+      // K(|k|)/n^3 for this tile while its rows are in flight
+      const int outer = tile / ntx;
+      tile_kernel<T, N, SB, NT>(Kt, (tile - outer * ntx) * SB, signed_freq(outer, N), tid, kf, l_mfp, norm);
+    }
+    const bool ok = mbar_wait_bounded(mbar, parity, kLimit);
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0) {
+        raise_status(status, AMBER_ERR_DEVICE_TIMEOUT);
+        mbar_wait_bounded(mbar, parity, kLimit);  // let the copy in flight land before leaving
+      }
+      return;
+    }
+    parity ^= 1u;
+    cpx<T> v[E];
+    // ---- forward stage A from the staged tile (row n, column b at n SB + b)
+#pragma unroll
+    for (int q = 0; q < QA; ++q) {
+      const int id = tid + q * NT;
+      const int b = id % SB, j = id / SB;
+#pragma unroll
+      for (int r = 0; r < R0; ++r) v[q * R0 + r] = sm[(j + r * (N / R0)) * SB + b];
+    }
+#pragma unroll
+    for (int q = 0; q < QA; ++q) dft<R0, false>(v + q * R0);
+    __syncthreads();  // the staged tile is read: its space becomes the exchange area
+#pragma unroll
+    for (int q = 0; q < QA; ++q) {
+      const int id = tid + q * NT;
+      const int b = id % SB, j = id / SB;
+#pragma unroll
+      for (int r = 0; r < R0; ++r) sm[L::pos(j * R0 + r, b)] = v[q * R0 + r];
+    }
+    __syncthreads();
+    // ---- forward stage B, the kernel multiply, inverse stage A (registers)
+#pragma unroll
+    for (int q = 0; q < QB; ++q) {
+      const int id = tid + q * NT;
+      const int b = id % SB, j = id / SB;
+#pragma unroll
+      for (int r = 0; r < R1; ++r) {
+        cpx<T> x = sm[L::pos(j + r * R0, b)];
+        if (r > 0) x = cmul(x, tw[j * r]);
+        v[q * R1 + r] = x;
+      }
+      dft<R1, false>(v + q * R1);
+#pragma unroll
+      for (int r = 0; r < R1; ++r) {
+        const int n = j + r * R0;
+        const int kza = n <= N / 2 ? n : N - n;
+        v[q * R1 + r] = scale(v[q * R1 + r], Kt[kza * SB + b]);
+      }
+      dft<R1, true>(v + q * R1);
+    }
+    __syncthreads();  // all forward stage-B reads of the exchange area are done
+#pragma unroll
+    for (int q = 0; q < QB; ++q) {
+      const int id = tid + q * NT;
+      const int b = id % SB, j = id / SB;
+#pragma unroll
+      for (int r = 0; r < R1; ++r) sm[L::pos(j * R1 + r, b)] = v[q * R1 + r];
+    }
+    __syncthreads();
+    // ---- inverse stage B: radix R0 over n = j + r R1, twiddle conj(w_N^(j r))
+#pragma unroll
+    for (int q = 0; q < QA; ++q) {
+      const int id = tid + q * NT;
+      const int b = id % SB, j = id / SB;
+#pragma unroll
+      for (int r = 0; r < R0; ++r) {
+        cpx<T> x = sm[L::pos(j + r * R1, b)];
+        if (r > 0) x = cmulc(x, tw[j * r]);
+        v[q * R0 + r] = x;
+      }
+      dft<R0, true>(v + q * R0);
+    }
+    __syncthreads();  // the exchange area is read: the next tile may land in it
+    if (tid == 0 && tile + (int)gridDim.x < ntiles) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      const int nt = tile + (int)gridDim.x;
+      zpass_tma_issue<N, V>(&tmap, buf, mbar, (nt % ntx) * SB, nt / ntx);
+    }
+#pragma unroll
+    for (int q = 0; q < QA; ++q) {
+      const int id = tid + q * NT;
+      const int b = id % SB, j = id / SB;
+      // the store base is recomputed here from the tile index: kept live
+      // across the stages it would spill
+      int t;
+      asm volatile("mov.b32 %0, %1;" : "=r"(t) : "r"(tile));
+      const int o = t / ntx, c0 = (t - o * ntx) * SB;
+      if (c0 + b < ncol) {
+        cpx<T>* ob = H + (int64_t)o * outer_stride + c0 + b;
+#pragma unroll
+        for (int r = 0; r < R0; ++r) ob[(int64_t)(j + r * R1) * elem_stride] = v[q * R0 + r];
+      }
+    }
+  }
+}
+
+// Host: the 3D tensor map of the half spectrum H (x = kx over n/2 + 2
+// columns of which the first n/2 + 1 are read, y, z; 8-byte elements) with boxes of SB x 1 x min(n, 256), for
+// k_fft_zconv_tma.  False when the driver's encoder is unavailable or refuses.
+bool zpass_tensor_map(CUtensorMap* map, const void* H, int n, int SB);
 
 // ---------------------------------------------------------------------------
 // x-pass R2C: rows 2p and 2p+1 form z = a + i b; after the complex FFT
@@ -557,7 +760,7 @@ enum ProfKind {
 template <typename T, int N, int V = 0>
 cudaError_t radiation_field_n(const T* src, T* J, cpx<T>* H, const cpx<T>* tw, double box, double l_mfp,
                               unsigned int* status, cudaStream_t s, FftProfile* prof, SortCtrl* krange,
-                              const cpx<T>* spec_in = nullptr, bool hist8 = false) {
+                              const cpx<T>* spec_in = nullptr, bool hist8 = false, bool tma = false) {
   using C = FftCfg<N, V>;
   const int RS = N / 2 + 2;
   const int ncol = N / 2 + 1;
@@ -596,12 +799,30 @@ cudaError_t radiation_field_n(const T* src, T* J, cpx<T>* H, const cpx<T>* tw, d
   }
   // z-pass: lines (y, kx); element stride N*RS; outer (y) stride RS
   prof_begin(prof, PK_FFT_Z_CONV, s);
-  if (spec_in)
+  bool z_done = false;
+  if constexpr (sizeof(T) == 4 && C::R1 > 1) {
+    CUtensorMap map;
+    if (tma && zpass_tensor_map(&map, spec_in ? (const void*)spec_in : (const void*)H, N, C::SB)) {
+      static std::atomic<unsigned long long> tma_attr{0};
+      if (first_use_on_device(tma_attr))
+        cudaFuncSetAttribute(k_fft_zconv_tma<N, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)zpass_tma_smem<N, V>());
+      int dev = 0, sms = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      const int grid = sgrid < 2 * sms ? sgrid : 2 * sms;
+      k_fft_zconv_tma<N, V><<<grid, strided_threads<N, V>(), zpass_tma_smem<N, V>(), s>>>(
+          map, H, ncol, ntx, sgrid, tw, kf, (T)l_mfp, norm, status);
+      z_done = true;
+    }
+  }
+  if (z_done) {
+  } else if (spec_in)
     k_fft_strided<T, N, PASS_CONV, V, true><<<sgrid, strided_threads<N, V>(), sc, s>>>(
         H, (int64_t)N * RS, RS, ncol, ntx, tw, kf, (T)l_mfp, norm, spec_in);
   else
-    k_fft_strided<T, N, PASS_CONV, V><<<sgrid, strided_threads<N, V>(), sc, s>>>(H, (int64_t)N * RS, RS, ncol, ntx,
-                                                                              tw, kf, (T)l_mfp, norm);
+    k_fft_strided<T, N, PASS_CONV, V><<<sgrid, strided_threads<N, V>(), sc, s>>>(
+        H, (int64_t)N * RS, RS, ncol, ntx, tw, kf, (T)l_mfp, norm);
   prof_end(prof, PK_FFT_Z_CONV, s);
   prof_begin(prof, PK_FFT_Y_INV, s);
   k_fft_strided<T, N, PASS_INV, V><<<sgrid, strided_threads<N, V>(), ss, s>>>(H, RS, (int64_t)N * RS, ncol, ntx, tw,

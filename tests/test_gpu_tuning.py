@@ -63,6 +63,38 @@ def test_fft_variant_1_plane_wave(B, n):
     assert float((J - K * S).abs().max()) <= 1e-5 * K
 
 
+@pytest.mark.parametrize("n,variant", [(64, 0), (128, 0), (128, 1), (256, 1), (512, 0), (512, 1), (1024, 0)])
+def test_tma_z_pass_gives_the_same_solve(B, n, variant):
+    # the z pass with TMA-staged tiles (one to four boxes of up to 256 rows
+    # per tile; the last column tile holds one column, the rest zero fill)
+    # does the plain z pass's arithmetic: intensities, z_re, order and masses
+    # bit-equal, from the source and from a kept spectrum
+    box, l = 100.0 * n / 128, 3.0
+    S, m = synth.realisation(n, box, 43, device="cuda")
+    h = B.history(8.0, 4.0, 3.0)
+    outs = []
+    with B.Context(n ** 3) as ctx:
+        ctx.set_tuning(n, fft_variant=variant)
+        spec = ctx.source_spectrum(S)  # the x and y passes of this variant's tiles
+        for tma in (0, 1):
+            ctx.set_tuning(n, zpass_tma=tma)
+            assert ctx.get_tuning(n)["zpass_tma"] == tma
+            z = torch.empty_like(S)
+            J = torch.empty_like(S)
+            order = torch.empty(n ** 3, dtype=torch.int32, device="cuda")
+            mr = torch.empty(n ** 3, device="cuda")
+            ctx.solve_ex(S, m, box, l, h, z, order, mr, J_out=J)
+            z2 = torch.empty_like(S)
+            ctx.solve_spectrum(spec, m, box, l, h, z2)
+            Jr = ctx.radiation_field(S, box, l)
+            assert ctx.sync_status() == 0
+            assert torch.equal(z2, z) and torch.equal(Jr, J)
+            outs.append((z, J, order, mr))
+            del z2, Jr
+    for a, b in zip(*outs):
+        assert torch.equal(a, b)
+
+
 @pytest.mark.parametrize("bits,match", [(8, 0), (8, 1), (9, 1)])
 @pytest.mark.parametrize("n", [4, 8, 64, 128])
 def test_ranking_choices_bit_exact(B, n, bits, match):
@@ -90,6 +122,9 @@ def test_set_tuning_rejects_bad_choices(B):
         for args in [(64, 1, 9, 0), (64, 0, 7, 0), (64, 0, 9, 2), (256, 0, 9, 0), (48, 0, 9, 0)]:
             with pytest.raises(B.AmberError):
                 ctx.set_tuning(*args)
+        for kw in [{"fuse_histogram": 2}, {"zpass_tma": 2}, {"zpass_tma": -1}]:
+            with pytest.raises(B.AmberError):
+                ctx.set_tuning(64, **kw)
 
 
 def test_autotune_keeps_the_fastest_choice(B):
@@ -101,6 +136,8 @@ def test_autotune_keeps_the_fastest_choice(B):
         assert t["tuned"] == 1 and t["n"] == n
         assert min(t["fft_ms"]) > 0 and min(t["sort_ms"]) > 0
         assert t["fft_variant"] == int(np.argmin(t["fft_ms"]))
+        assert t["fft_tma_ms"] > 0
+        assert t["zpass_tma"] == int(t["fft_tma_ms"] < 0.98 * t["fft_ms"][t["fft_variant"]])
         k = int(np.argmin(t["sort_ms"]))
         assert (t["sort_digit_bits"], t["sort_match"]) == [(9, 0), (9, 1), (8, 0), (8, 1)][k]
         assert ctx.get_tuning(n) == t
