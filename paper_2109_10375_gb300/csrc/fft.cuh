@@ -354,8 +354,8 @@ k_fft_zconv_tma(const __grid_constant__ CUtensorMap tmap, cpx<float>* __restrict
   const int64_t elem_stride = (int64_t)N * (N / 2 + 2), outer_stride = N / 2 + 2;
   // dynamic shared memory only (its base is 1024-byte aligned): the staged
   // tile / exchange area, the K table, the mbarrier
-  extern __shared__ __align__(1024) unsigned char smem_raw[];
-  cpx<T>* sm = reinterpret_cast<cpx<T>*>(smem_raw);
+  extern __shared__ __align__(1024) unsigned char smem_tma[];
+  cpx<T>* sm = reinterpret_cast<cpx<T>*>(smem_tma);
   T* Kt = reinterpret_cast<T*>(sm + L::elems);  // K over |kz| = 0..N/2 for the tile's columns
   const uint32_t buf = smem_u32(sm), mbar = buf + (uint32_t)zpass_tma_mbar_offset<N, V>();
   const int tid = threadIdx.x;

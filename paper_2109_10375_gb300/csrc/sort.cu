@@ -105,26 +105,49 @@ __device__ __forceinline__ void sort_histogram_body(const SRC* __restrict__ J, i
   // anywhere on its element size); otherwise every element takes the tail loop
   const bool vec = (reinterpret_cast<uintptr_t>(J) & 15) == 0;
   const int64_t nvec = vec ? n / V : 0;
-  const int64_t vec_iters = (nvec + nthreads - 1) / nthreads;
-  for (int64_t it = 0; it < vec_iters; ++it) {  // the same trip count on every lane
-    const int64_t v = it * nthreads + gtid;
-    const bool ok = v < nvec;
-    SRC x[V];
-    if (ok) {
-      const uint4 raw = reinterpret_cast<const uint4*>(J)[v];
-      memcpy(x, &raw, 16);
-    }
-    const bool all_ok = __all_sync(0xffffffffu, ok);
+  // two 16-byte loads in flight per thread and round
+  constexpr int U = 2;
+  const int64_t rounds = (nvec + U * nthreads - 1) / (U * nthreads);
+  for (int64_t it = 0; it < rounds; ++it) {  // the same trip count on every lane
+    K key[U][V];
+    bool ok[U];
+    {
+      SRC x[U][V];
 #pragma unroll
-    for (int e = 0; e < V; ++e) {
-      const K key = ok ? K(enc_desc(x[e], bad) - kmin) : K(0);
+      for (int u = 0; u < U; ++u) {
+        const int64_t v = (it * U + u) * nthreads + gtid;
+        ok[u] = v < nvec;
+        if (ok[u]) {
+          const uint4 raw = reinterpret_cast<const uint4*>(J)[v];
+          memcpy(x[u], &raw, 16);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+#pragma unroll
+        for (int e = 0; e < V; ++e) key[u][e] = ok[u] ? K(enc_desc(x[u][e], bad) - kmin) : K(0);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const bool all_ok = __all_sync(0xffffffffu, ok[u]);
+      // digit position by digit position (warp-uniform tests, once per V
+      // keys): one shared add per key below the top digit; the top digit of
+      // a smooth field tends to agree across a warp, which then adds once
 #pragma unroll
       for (int p = 0; p < P; ++p) {
-        if (p >= np) break;
-        const unsigned d = (unsigned)(key >> (RB * p)) & (R - 1);
-        // only the top digit of a smooth field tends to agree across a warp
-        if (all_ok && p == np - 1) hist_add(h[p], d);
-        else if (ok) atomicAdd(&h[p][d], 1u);
+        if (p < np - 1) {
+          if (ok[u]) {
+#pragma unroll
+            for (int e = 0; e < V; ++e) atomicAdd(&h[p][(unsigned)(key[u][e] >> (RB * p)) & (R - 1)], 1u);
+          }
+        } else if (p == np - 1) {
+#pragma unroll
+          for (int e = 0; e < V; ++e) {
+            const unsigned d = (unsigned)(key[u][e] >> (RB * p)) & (R - 1);
+            if (all_ok) hist_add(h[p], d);
+            else if (ok[u]) atomicAdd(&h[p][d], 1u);
+          }
+        }
       }
     }
   }
