@@ -650,14 +650,14 @@ __device__ __forceinline__ void scan_assign_body(const ScanArgs& a) {
 }
 
 template <bool GATHER, bool WANT_F, bool LIN>
-__global__ void __launch_bounds__(kScanThreads, 2) k_scan_assign(const ScanArgs a) {
+__global__ void __launch_bounds__(kScanThreads, AMBER_SCAN_MINB) k_scan_assign(const ScanArgs a) {
   scan_assign_body<GATHER, WANT_F, LIN>(a);
 }
 
 // Several matchings at once: CTA b works on item find_item(prefix, M, b) (the
 // prefix counts scan tiles), taking its tile from that item's own ticket.
 template <bool LIN>
-__global__ void __launch_bounds__(kScanThreads, 2)
+__global__ void __launch_bounds__(kScanThreads, AMBER_SCAN_MINB)
     k_scan_assign_multi(const ScanArgs* __restrict__ args, const uint32_t* __restrict__ prefix, int M) {
   __shared__ ScanArgs sa;
   if (threadIdx.x == 0) sa = args[find_item(prefix, M, blockIdx.x)];

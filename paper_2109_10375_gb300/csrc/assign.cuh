@@ -9,8 +9,18 @@
 
 namespace amber {
 
-constexpr int kScanThreads = 512;
-constexpr int kScanItems = 16;
+// Scan tile shape and CTAs per SM (build-time tunables).
+#ifndef AMBER_SCAN_THREADS
+#define AMBER_SCAN_THREADS 512
+#endif
+#ifndef AMBER_SCAN_ITEMS
+#define AMBER_SCAN_ITEMS 16
+#endif
+#ifndef AMBER_SCAN_MINB
+#define AMBER_SCAN_MINB 2
+#endif
+constexpr int kScanThreads = AMBER_SCAN_THREADS;
+constexpr int kScanItems = AMBER_SCAN_ITEMS;
 constexpr int kScanTile = kScanThreads * kScanItems;
 constexpr int kMaxTable = 1 << 16;
 constexpr int kMaxBuckets = 1024;
