@@ -395,6 +395,8 @@ def run_amber(args):
     ctx = B.Context(C, device=local)
     if args.fuse_histogram is not None:
         ctx.set_tuning(n, fuse_histogram=args.fuse_histogram)
+    if args.zpass_tma is not None:
+        ctx.set_tuning(n, zpass_tma=args.zpass_tma)
     z = torch.empty_like(S)
     stream = torch.cuda.current_stream()
 
@@ -568,9 +570,11 @@ def run_amber(args):
     del S, m
     torch.cuda.empty_cache()
     ctxs2 = [ctx] + [B.Context(C, device=local) for _ in range(args.e2e_contexts - 1)]
-    if args.fuse_histogram is not None:
-        for cx in ctxs2[1:]:
+    for cx in ctxs2[1:]:
+        if args.fuse_histogram is not None:
             cx.set_tuning(n, fuse_histogram=args.fuse_histogram)
+        if args.zpass_tma is not None:
+            cx.set_tuning(n, zpass_tma=args.zpass_tma)
     streams = [torch.cuda.Stream() for _ in ctxs2]
     z_h = z_h + [torch.empty(z.shape, dtype=torch.float32, pin_memory=True) for _ in range(len(ctxs2) - len(z_h))]
     e_steps = max(2, args.steps)  # the same K as the device-timed steps
@@ -856,6 +860,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fuse-histogram", type=int, choices=[0, 1], default=None,
                     help="override the size's choice of digit counts in the inverse x pass (8-bit digits)")
+    ap.add_argument("--zpass-tma", type=int, choices=[0, 1], default=None,
+                    help="override the size's choice of the TMA-staged z pass")
     ap.add_argument("--e2e-contexts", type=int, default=3,
                     help="contexts (each with its own stream) the end-to-end steps rotate over")
     ap.add_argument("--no-accuracy", action="store_true",
