@@ -360,6 +360,15 @@ int amber_sync_status(amber_ctx *ctx, void *stream);
 /* Human-readable name of a status code (static string). */
 const char *amber_status_string(int code);
 
+/* The layout of a public struct as this library was compiled, so a binding
+ * in another language can check its own copy: which = 0 amber_history_t,
+ * 1 amber_params_t, 2 amber_tuning_t, 3 amber_batch_item.  Writes sizeof to
+ * *size and the byte offset of each member, in declaration order, to
+ * offsets[0 .. *count - 1] (at most max_offsets of them; *count is the
+ * member count).  Host only: no CUDA call, no context.  AMBER_ERR_INVALID_ARG
+ * for another `which` or a NULL size or count. */
+int amber_struct_layout(int which, size_t *size, size_t *offsets, int max_offsets, int *count);
+
 /* Per-kernel timing with CUDA events on the launching stream.  When enabled,
  * every kernel launch is bracketed by events and the totals accumulate until
  * amber_profile_reset.  amber_profile_read synchronises the context's last

@@ -34,7 +34,7 @@ EXPORTED = [
     "amber_lpt_displacement", "amber_mesh_density", "amber_esf_fcoll", "amber_sigma2_tophat",
     "amber_solve_tomographic", "amber_autotune", "amber_set_tuning", "amber_get_tuning",
     "amber_rank_noalloc", "amber_power_derived", "amber_spectrum_bytes", "amber_source_spectrum",
-    "amber_solve_spectrum", "amber_batch_kernel_nodes", "amber_solve_host",
+    "amber_solve_spectrum", "amber_batch_kernel_nodes", "amber_solve_host", "amber_struct_layout",
 ]
 
 
@@ -102,6 +102,7 @@ def _load():
         "amber_profile_enable": (i32, [vp, i32]),
         "amber_profile_reset": (i32, [vp]),
         "amber_profile_kinds": (i32, []),
+        "amber_struct_layout": (i32, [i32, C.POINTER(C.c_size_t), C.POINTER(C.c_size_t), i32, C.POINTER(i32)]),
         "amber_profile_read": (i32, [vp, i32, C.POINTER(C.c_char_p), C.POINTER(dbl), C.POINTER(i64)]),
         "amber_sort_passes": (i32, [vp, C.POINTER(i32)]),
         "amber_source_field": (i32, [vp, vp, i64, dbl, dbl, vp, vp, vp]),

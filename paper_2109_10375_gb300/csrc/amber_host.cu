@@ -1457,6 +1457,49 @@ int amber_profile_reset(amber_ctx* c) {
 
 int amber_profile_kinds(void) { return PK_COUNT; }
 
+int amber_struct_layout(int which, size_t* size, size_t* offsets, int max_offsets, int* count) {
+  if (!size || !count) return AMBER_ERR_INVALID_ARG;
+  size_t off[16];
+  int k = 0;
+  switch (which) {
+    case 0:
+      *size = sizeof(amber_history_t);
+      for (size_t o : {offsetof(amber_history_t, z_mid), offsetof(amber_history_t, dz), offsetof(amber_history_t, Az),
+                       offsetof(amber_history_t, x_ear), offsetof(amber_history_t, x_mid),
+                       offsetof(amber_history_t, x_lat), offsetof(amber_history_t, z_lo),
+                       offsetof(amber_history_t, z_hi), offsetof(amber_history_t, n_table),
+                       offsetof(amber_history_t, weighting), offsetof(amber_history_t, omega_m)})
+        off[k++] = o;
+      break;
+    case 1:
+      *size = sizeof(amber_params_t);
+      for (size_t o : {offsetof(amber_params_t, n), offsetof(amber_params_t, box), offsetof(amber_params_t, l_mfp),
+                       offsetof(amber_params_t, hist), offsetof(amber_params_t, precision)})
+        off[k++] = o;
+      break;
+    case 2:
+      *size = sizeof(amber_tuning_t);
+      for (size_t o : {offsetof(amber_tuning_t, n), offsetof(amber_tuning_t, fft_variant),
+                       offsetof(amber_tuning_t, sort_digit_bits), offsetof(amber_tuning_t, sort_match),
+                       offsetof(amber_tuning_t, tuned), offsetof(amber_tuning_t, fft_ms),
+                       offsetof(amber_tuning_t, sort_ms), offsetof(amber_tuning_t, fuse_histogram),
+                       offsetof(amber_tuning_t, zpass_tma), offsetof(amber_tuning_t, fft_tma_ms)})
+        off[k++] = o;
+      break;
+    case 3:
+      *size = sizeof(amber_batch_item);
+      for (size_t o : {offsetof(amber_batch_item, d_src), offsetof(amber_batch_item, d_mass),
+                       offsetof(amber_batch_item, params), offsetof(amber_batch_item, d_zre)})
+        off[k++] = o;
+      break;
+    default:
+      return AMBER_ERR_INVALID_ARG;
+  }
+  *count = k;
+  for (int i = 0; i < k && i < max_offsets && offsets; ++i) offsets[i] = off[i];
+  return AMBER_OK;
+}
+
 int amber_profile_read(amber_ctx* c, int kind, const char** name, double* total_ms, int64_t* launches) {
   if (!c || kind < 0 || kind >= PK_COUNT) return AMBER_ERR_INVALID_ARG;
   std::lock_guard<std::mutex> lk(c->mu);

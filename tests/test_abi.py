@@ -114,3 +114,20 @@ def test_binding_rejects_non_contiguous_tensors(B):
     with pytest.raises(ValueError):
         B._ptr(t)
     assert B._ptr(torch.zeros(4)) is not None and B._ptr(None) is None
+
+
+def test_ctypes_structs_match_the_compiled_layout(B):
+    # the binding's copies of the public structs against sizeof and offsetof
+    # as the library was compiled (host-only call: no CUDA, no context)
+    import ctypes as C
+    for which, cls in enumerate([B.amber_history_t, B.amber_params_t, B.amber_tuning_t, B.amber_batch_item]):
+        size, count = C.c_size_t(), C.c_int()
+        offs = (C.c_size_t * 16)()
+        assert B.lib.amber_struct_layout(which, C.byref(size), offs, 16, C.byref(count)) == 0
+        fields = [f[0] for f in cls._fields_]
+        assert size.value == C.sizeof(cls), cls.__name__
+        assert count.value == len(fields), cls.__name__
+        assert list(offs[:count.value]) == [getattr(cls, f).offset for f in fields], cls.__name__
+    size, count = C.c_size_t(), C.c_int()
+    assert B.lib.amber_struct_layout(4, C.byref(size), None, 0, C.byref(count)) != 0
+    assert B.lib.amber_struct_layout(0, None, None, 0, C.byref(count)) != 0
