@@ -89,6 +89,36 @@ def test_mesh_density_vs_oracle(ctx, B, order, interlace, weighted):
     _close(got.cpu().numpy(), ref, 2e-5)
 
 
+@pytest.mark.parametrize("order,interlace", [(2, False), (3, True)])
+def test_mesh_density_blocks_vs_oracle_64(ctx, B, order, interlace):
+    # 64^3: particles whose windows cross the periodic edge and overlap their
+    # neighbours' (displacements up to 2.5 cells)
+    n, box = 64, 64.0
+    g = np.random.default_rng(order + 40)
+    psi = [g.uniform(-2.5, 2.5, (n, n, n)).astype(np.float32) for _ in range(3)]
+    got = ctx.mesh_density(tuple(_t(p) for p in psi), box, order, interlace)
+    assert ctx.sync_status() == 0
+    p64 = [p.astype(np.float64) for p in psi]
+    r1 = O.mesh_assign(p64, None, box, order)
+    ref = O.interlace_deconvolve(r1, O.mesh_assign(p64, None, box, order, 0.5), box, order) if interlace else r1
+    _close(got.cpu().numpy(), ref, 2e-5)
+
+
+@pytest.mark.parametrize("order", [2, 3])
+def test_mesh_density_wide_spread_vs_oracle(ctx, B, order):
+    # displacements up to 7.5 cells: particles far from their lattice points,
+    # windows wrapping the periodic edge, weighted
+    n, box = 16, 24.0
+    g = np.random.default_rng(order + 50)
+    dx = box / n
+    psi = [(g.uniform(-7.5, 7.5, (n, n, n)) * dx).astype(np.float32) for _ in range(3)]
+    mass = g.uniform(0.2, 3.0, (n, n, n)).astype(np.float32)
+    got = ctx.mesh_density(tuple(_t(p) for p in psi), box, order, False, mass=_t(mass))
+    assert ctx.sync_status() == 0
+    ref = O.mesh_assign([p.astype(np.float64) for p in psi], mass.astype(np.float64), box, order)
+    _close(got.cpu().numpy(), ref, 2e-5)
+
+
 @pytest.mark.parametrize("order", [1, 2, 3])
 def test_mesh_density_uniform_lattice_256(B, order):
     # no displacement: every window, with or without interlacing, gives 1
