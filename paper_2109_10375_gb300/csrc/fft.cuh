@@ -661,15 +661,18 @@ k_fft_c2r_x(const cpx<T>* __restrict__ H, T* __restrict__ J, int64_t nrows, int 
     klo = kk < klo ? kk : klo;
     khi = kk > khi ? kk : khi;
     if constexpr (HIST) {
+      // the two low digits: one add per key
+      atomicAdd(&shist[kk & 255u], 1u);
+      atomicAdd(&shist[256 + ((kk >> 8) & 255u)], 1u);
+      // neighbouring cells of a smooth field often share the upper digits:
+      // one add for the active lanes when they all agree
+      const unsigned am = __activemask();
+      const int leader = __ffs(am) - 1;
 #pragma unroll
-      for (int p = 0; p < 4; ++p) {
+      for (int p = 2; p < 4; ++p) {
         const unsigned d = (unsigned)(kk >> (8 * p)) & 255u;
-        // neighbouring cells of a smooth field often share the upper digits:
-        // one add for the active lanes when they all agree
-        const unsigned am = __activemask();
-        const int leader = __ffs(am) - 1;
         const unsigned d0 = __shfl_sync(am, d, leader);
-        if (p >= 2 && __all_sync(am, d == d0)) {
+        if (__all_sync(am, d == d0)) {
           if ((int)(threadIdx.x & 31) == leader) atomicAdd(&shist[p * 256 + d0], (uint32_t)__popc(am));
         } else {
           atomicAdd(&shist[p * 256 + d], 1u);
